@@ -1,0 +1,389 @@
+#!/usr/bin/env python3
+"""Benchmark of the exact k-NN DTW retrieval cascade (LB_Keogh -> LB_Improved
+-> band DTW_p with early abandoning) on one or more GB300s.
+
+Workload (default): 100,000 seeded random walks x_1 = 0, x_t = x_{t-1} + N(0,1)
+of length n = 256 (fp32, resident in HBM), band w = 25 (10 %), 1,000 fresh
+queries per step from a distinct seed stream, 1-NN under DTW_1 (the measure
+of the paper's experiments, Sec. 10).  A step is one knn_search call over the
+whole query batch: envelopes, LB_Keogh of every pair, seed DTWs,
+LB_Improved of the LB_Keogh survivors, DTW of the LB_Improved survivors and
+the ordered top-k.  The same step under DTW_2 is reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank holds the whole database and runs its own batch of
+queries (weak scaling; the only collectives are the timing barrier and the
+max-over-ranks of the elapsed time).  `--impl reference` times the FP64 CPU
+oracle (the paper's Algorithm 3 scan, in C, on all host cores) on a bounded
+sample of the same workload.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "exact 1-NN DTW queries/s (LB_Improved cascade)"
+L2_BYTES = 129 * 2**20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--N", type=int, default=100_000)
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--w", type=int, default=25)
+    ap.add_argument("--Q", type=int, default=1000)
+    ap.add_argument("--k", type=int, default=1)
+    ap.add_argument("--p", type=int, default=1)
+    ap.add_argument("--seed", type=int, default=2)
+    ap.add_argument("--no-p2", action="store_true", help="skip the DTW_2 side measurement")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU baseline sample")
+    return ap.parse_args()
+
+
+def workload_config(a, world):
+    return {
+        "workload": "random-walk 1-NN retrieval: N=%d series, n=%d, w=%d, %d queries/step/GPU, DTW_%d, k=%d"
+        % (a.N, a.n, a.w, a.Q, a.p, a.k),
+        "N": a.N, "n": a.n, "w": a.w, "queries_per_step_per_gpu": a.Q, "p": a.p, "k": a.k,
+        "data": "seeded synthetic random walks (fp32)", "seed": a.seed,
+        "l2": "flushed between timed steps (256 MiB write)",
+        "parallelism": "queries sharded over %d GPU(s), database replicated" % world,
+    }
+
+
+def cpu_info():
+    model = ""
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    return os.cpu_count() or 1, model
+
+
+def oracle_rate(db, queries, w, p, k, budget_s):
+    """Oracle (Algorithm 3 scan, fp64 C) on all host cores over a bounded query sample."""
+    import oracle
+
+    cores, model = cpu_info()
+    # calibrate on one query per core, then size the sample to the budget
+    t0 = time.perf_counter()
+    oracle.knn_cascade(db, queries[:cores], w, p, k, mode=1, threads=cores)
+    t1 = time.perf_counter() - t0
+    per_q = max(t1 / cores, 1e-6)
+    m = int(min(len(queries), max(cores, budget_s / per_q)))
+    t0 = time.perf_counter()
+    oracle.knn_cascade(db, queries[:m], w, p, k, mode=1, threads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": m / dt, "unit": "queries/s", "cores": cores, "cpu": model, "kind": "oracle",
+            "sample": "%d of the step's queries against the full database, Algorithm 3 scan in fp64 C, "
+                      "one query per thread" % m, "seconds": dt}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples, tagged with host time on arrival."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.samples = []
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.th = threading.Thread(target=self._read, daemon=True)
+        self.th.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 8:
+                self.samples.append((time.time(), parts))
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self, t0, t1):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        win = [s for t, s in self.samples if t0 <= t <= t1]
+        note = "timed region"
+        if len(win) < 3:
+            win = [s for _, s in self.samples]
+            note = "whole run (timed region shorter than the sampling interval)"
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(s[0]) for s in win if num(s[0]) is not None]
+        mx = [num(s[1]) for s in win if num(s[1]) is not None]
+        pw = [num(s[2]) for s in win if num(s[2]) is not None]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for s in win:
+            for name, v in zip(names, s[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(pw) if pw else None, "reasons": sorted(reasons), "samples": len(win),
+                "window": note}
+
+
+def roofline(prof, a, steps, peaks, stats):
+    """Roofline of the dominant stage (largest device time in the timed region)."""
+    import torch
+
+    stages = {k: v for k, v in prof.items() if v["launches"] > 0}
+    total = sum(v["ms"] for v in stages.values())
+    dom = max(stages, key=lambda k: stages[k]["ms"])
+    ms = stages[dom]["ms"] / max(1, stages[dom]["launches"])
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    clock = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    alu_peak = sms * 128 * clock / 1e12  # fp32 lane-ops per second, T
+    share = {k: round(v["ms"] / total, 4) for k, v in stages.items()}
+    if dom == "lb_keogh":
+        # 4 fp32 ops per (query, candidate, index): 2 subtractions, a 3-input max, an add/fma
+        work = a.Q * a.N * a.n * 4.0 / 1e12
+        achieved = work / (ms / 1e3)
+        return {"kernel": "k_lbk_tile", "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Top/s",
+                "frac": achieved / alu_peak, "traffic": None, "ms_per_launch": ms, "stage_share": share,
+                "peak_note": "%d SMs x 128 fp32 lanes x %.0f MHz (max SM clock)" % (sms, clock / 1e6)}
+    if dom in ("dtw", "seed_dtw"):
+        cells = stats.get("dtw_cells" if dom == "dtw" else "seed_cells", 0)
+        work = cells * 3.0 / 1e12  # 3 ops per cell: subtraction, 3-input min, add/fma
+        achieved = work / (ms / 1e3) if cells else None
+        return {"kernel": "k_dtw_reg", "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Top/s",
+                "frac": (achieved / alu_peak) if achieved else None, "traffic": None, "ms_per_launch": ms,
+                "cells_per_launch": cells, "stage_share": share,
+                "peak_note": "%d SMs x 128 fp32 lanes x %.0f MHz (max SM clock)" % (sms, clock / 1e6)}
+    return {"kernel": dom, "bound": "alu", "achieved": None, "peak": alu_peak, "unit": "Top/s", "frac": None,
+            "traffic": None, "ms_per_launch": ms, "stage_share": share}
+
+
+def run_ours(a):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    from paper_0811_3301_gb300 import build
+
+    if rank == 0:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    from paper_0811_3301_gb300 import _native as N
+    from paper_0811_3301_gb300 import api
+
+    db_h = synth.random_walks(a.N, a.n, seed=a.seed)
+    q_h = synth.random_walks(a.Q, a.n, seed=a.seed, stream=synth.STREAM_QUERY + 16 * rank)
+    db = torch.from_numpy(db_h).to(dev)
+    qs = torch.from_numpy(q_h).to(dev)
+    flush = torch.empty(256 * 2**20 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+            torch.cuda.synchronize()
+
+    def step(p):
+        return api.knn_search(db, qs, a.w, p, a.k)
+
+    # pruning report (untimed): LB_Keogh alone vs LB_Keogh + LB_Improved
+    pruning = {}
+    for mode in ("keogh", "improved"):
+        _, _, st = api.knn_search(db, qs, a.w, a.p, a.k, mode=mode, return_stats=True)
+        tot = max(1, st["candidates"])
+        pruning[mode] = dict(st, pruned_fraction=round((st["pruned_keogh"] + st["pruned_improved"]) / tot, 6),
+                             dtw_fraction=round((st["dtw_computed"] + st["seeds"]) / tot, 6))
+
+    for _ in range(a.warmup):
+        step(a.p)
+    barrier()
+
+    sampler = ClockSampler(local) if rank == 0 else None
+    N.profile_read(reset=True)
+    N.profile_enable(True)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    barrier()
+    t_wall0 = time.time()
+    for i in range(a.steps):
+        flush.fill_(float(i))  # evict the database and the previous step's buffers from L2
+        evs[i][0].record(stream)
+        step(a.p)
+        evs[i][1].record(stream)
+    barrier()
+    t_wall1 = time.time()
+    N.profile_enable(False)
+    prof = N.profile_read(reset=True)
+    ms_steps = [s.elapsed_time(e) for s, e in evs]
+    ms_total = sum(ms_steps)
+    t = torch.tensor([ms_total], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * a.Q * a.steps / (ms_max / 1e3)
+    clocks = sampler.summary(t_wall0, t_wall1) if sampler else None
+
+    # DTW rows evaluated per step (for the DTW roofline): one extra stats run
+    _, _, st_main = api.knn_search(db, qs, a.w, a.p, a.k, return_stats=True)
+
+    # DTW_2 side measurement (same workload, same timing method)
+    p2 = None
+    if not a.no_p2:
+        other = 2 if a.p == 1 else 1
+        for _ in range(a.warmup):
+            step(other)
+        barrier()
+        ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+        for i in range(a.steps):
+            flush.fill_(float(i))
+            ev2[i][0].record(stream)
+            step(other)
+            ev2[i][1].record(stream)
+        barrier()
+        ms2 = sum(s.elapsed_time(e) for s, e in ev2)
+        t2 = torch.tensor([ms2], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(t2, op=dist.ReduceOp.MAX)
+        p2 = {"p": other, "value": world * a.Q * a.steps / (float(t2.item()) / 1e3), "unit": "queries/s",
+              "ms_per_step": float(t2.item()) / a.steps}
+
+    # end to end through the public API: queries from pinned host memory,
+    # results read back to pinned host memory, every step
+    q_pin = torch.from_numpy(q_h).pin_memory()
+    oi = torch.empty((a.Q, a.k), dtype=torch.int64).pin_memory()
+    od = torch.empty((a.Q, a.k), dtype=torch.float32).pin_memory()
+    for _ in range(a.warmup):
+        api.knn_search(db, q_pin, a.w, a.p, a.k, out_idx=oi, out_dist=od)
+    barrier()
+    e2e_s = 0.0
+    for i in range(a.steps):
+        flush.fill_(float(i))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        api.knn_search(db, q_pin, a.w, a.p, a.k, out_idx=oi, out_dist=od)  # synchronous (host outputs)
+        e2e_s += time.perf_counter() - t0
+    te = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e = {"value": world * a.Q * a.steps / float(te.item()), "unit": "queries/s",
+           "h2d_bytes_per_step": a.Q * a.n * 4, "d2h_bytes_per_step": a.Q * a.k * (8 + 4)}
+
+    if sampler:
+        sampler.stop()
+
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    launches = sum(v["launches"] for v in prof.values())
+    roof = roofline(prof, a, a.steps, peaks, st_main)
+
+    if rank != 0:
+        return None
+    cpu = None
+    if world == 1:
+        cpu = oracle_rate(db_h, q_h, a.w, a.p, a.k, a.cpu_seconds)
+    out = {
+        "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded random walks)",
+        "config": workload_config(a, world), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+        "gpu_launches": launches, "clocks": clocks, "p2": p2, "pruning": pruning,
+        "stages_ms_per_step": {k: v["ms"] / a.steps for k, v in prof.items()},
+        "stats_per_step": st_main,
+    }
+    return out
+
+
+def run_reference(a):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return None
+    import oracle
+
+    oracle.build()
+    db_h = synth.random_walks(a.N, a.n, seed=a.seed)
+    q_h = synth.random_walks(a.Q, a.n, seed=a.seed, stream=synth.STREAM_QUERY)
+    cores, model = cpu_info()
+    budget = max(2.0, 120.0 / max(1, a.warmup + a.steps))  # whole run within a few minutes
+    per_step = []
+    base = None
+    for i in range(a.warmup + a.steps):
+        r = oracle_rate(db_h, q_h, a.w, a.p, a.k, budget)
+        if i >= a.warmup:
+            per_step.append(r)
+        base = r
+    v = statistics.median(r["value"] for r in per_step)
+    return {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "queries/s", "n_gpus": world,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * a.Q / v, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded random walks)",
+        "config": workload_config(a, world),
+        "cpu_baseline": {"value": v, "unit": "queries/s", "cores": cores, "cpu": model, "kind": "oracle",
+                         "sample": base["sample"] + "; each step a bounded sample of the 1,000-query batch"},
+        "e2e": {"value": v, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    a = parse()
+    out = run_reference(a) if a.impl == "reference" else run_ours(a)
+    if out is not None:
+        print(json.dumps(out))
+    if int(os.environ.get("WORLD_SIZE", "1")) > 1 and a.impl == "ours":
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

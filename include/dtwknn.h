@@ -1,0 +1,183 @@
+/*
+ * dtwknn.h - C ABI of the GB300 (sm_103a) exact nearest-neighbour DTW
+ * retrieval cascade of D. Lemire, "Faster Retrieval with a Two-Pass
+ * Dynamic-Time-Warping Lower Bound" (arXiv:0811.3301).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Series are fp32, row-major and contiguous: a set of `count` series of
+ *    length n is a [count][n] array.  Indices are 0-based (the paper's are
+ *    1-based, Sec. 2).
+ *  - n >= 1 and n <= DTW_MAX_N.  w >= 0 is the locality constraint of
+ *    Sec. 4: x_i and y_j may be aligned only if |i - j| <= w; any w >= n - 1
+ *    means no constraint.  p is 1 or 2 (the l_p norm of Sec. 2).
+ *  - Distances and bounds are returned with the p-th root taken, as the
+ *    paper defines them (DTW_p = q_{1,1}^(1/p), Sec. 4).  Internally the
+ *    kernels compare in power space.
+ *  - Unless an entry point says otherwise, array pointers are DEVICE
+ *    pointers owned by the caller, and outputs are preallocated by the caller.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Calls are asynchronous on it unless documented otherwise.
+ *  - Inputs must be finite; NaN or Inf inputs give unspecified results.
+ *  - Every call returns a dtw_status; on failure dtw_last_error() gives a
+ *    message for the calling host thread and no output is written.
+ *  - Calls that need scratch memory take it from a per-device workspace
+ *    that the library grows on demand with cudaMalloc; growth synchronises
+ *    the device, so the first call at a new size must not be made inside a
+ *    CUDA stream capture.  Calls that use the workspace must not overlap on
+ *    the GPU (one such call at a time per device).
+ */
+#ifndef DTWKNN_H
+#define DTWKNN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DTW_MAX_N 4096 /* longest supported series */
+#define DTW_MAX_K 128  /* largest supported neighbour count */
+
+typedef enum {
+    DTW_OK = 0,
+    DTW_ERR_INVALID_ARG = 1, /* a size, pointer or parameter is out of range */
+    DTW_ERR_CUDA = 2,        /* a CUDA runtime call or kernel launch failed */
+    DTW_ERR_OOM = 3,         /* the workspace could not be grown */
+    DTW_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up */
+    DTW_ERR_NO_BUCKET = 5,   /* no database series has the query's length */
+    DTW_ERR_INTERNAL = 6     /* an internal consistency check failed */
+} dtw_status;
+
+/* Cascade variants for knn_search_ex (Sec. 7 and Sec. 8). */
+typedef enum {
+    DTW_MODE_IMPROVED = 0, /* LB_Keogh, then LB_Improved, then DTW (Algorithm 3) */
+    DTW_MODE_KEOGH = 1,    /* LB_Keogh, then DTW (Algorithm 2) */
+    DTW_MODE_NOPRUNE = 2   /* every candidate gets a full DTW (validation) */
+} dtw_mode;
+
+/* Counters of one knn_search call, summed over queries. */
+typedef struct {
+    int64_t candidates;      /* (query, candidate) pairs: Q * N */
+    int64_t seeds;           /* pairs whose DTW was computed first to seed the threshold */
+    int64_t pruned_keogh;    /* pairs discarded by LB_Keogh */
+    int64_t pruned_improved; /* pairs discarded by LB_Improved */
+    int64_t dtw_computed;    /* non-seed pairs whose DTW was started */
+    int64_t dtw_abandoned;   /* of which abandoned early (row minimum above the threshold) */
+    int64_t dtw_cells;       /* band cells evaluated by those DTWs (rows x (2w+1)) */
+    int64_t seed_cells;      /* band cells evaluated by the seed DTWs */
+} dtw_stats;
+
+typedef struct {
+    int32_t mode;  /* a dtw_mode */
+    float slack;   /* relative pruning slack; the kernels use the larger of this
+                      and the worst-case fp32 rounding bound of the compared sums */
+    int32_t seeds; /* candidates per query (lowest LB_Keogh first) whose DTW seeds the
+                      threshold; 0 selects the default (16, at least k, at most N) */
+} dtw_options;
+
+/*
+ * Warping envelope (Sec. 5): U(y)_i = max { y_k : |k - i| <= w } and
+ * L(y)_i = min { y_k : |k - i| <= w }, k restricted to the series, for each of
+ * `count` series y [count][n].  Outputs U, L are [count][n].  The result is
+ * exact (min and max do not round).  The paper computes it with the
+ * streaming Algorithm 1 (Sec. 6); this library uses a block-parallel
+ * doubling scheme with the same result.
+ */
+dtw_status dtw_envelope(const float *y, int64_t count, int32_t n, int32_t w,
+                        float *U, float *L, void *stream);
+
+/*
+ * LB_Keogh_p(x, y) = || x - H(x, y) ||_p (Sec. 7, Eq. 1) of every candidate
+ * x = cand[c] (cand is [N][n]) against one query y given by its envelope
+ * U = U(y), L = L(y) ([n] each).  out[c] receives the bound (root taken), [N].
+ */
+dtw_status lb_keogh(const float *cand, int64_t N, const float *U, const float *L,
+                    int32_t n, int32_t p, float *out, void *stream);
+
+/*
+ * LB_Improved_p(x, y) with LB_Improved_p^p = LB_Keogh_p(x, y)^p +
+ * LB_Keogh_p(y, H(x, y))^p (Sec. 8) for every candidate x = cand[c] against
+ * the query q [n] with envelope U, L ([n] each, computed with the same w).
+ * out[c] receives the bound (root taken), [N].
+ */
+dtw_status lb_improved(const float *cand, int64_t N, const float *q, const float *U,
+                       const float *L, int32_t n, int32_t w, int32_t p, float *out,
+                       void *stream);
+
+/*
+ * Band-constrained DTW_p (Sec. 4 recursion) of the pairs (x[c], y) for
+ * c < N: x is [N][n]; y is one series [n] when y_stride == 0, or [N][n] when
+ * y_stride == n (pair c uses y + c * n).  If threshold is finite, a pair whose
+ * DTW_p provably exceeds it (the minimum of a row of the dynamic program is
+ * above threshold^p, an exact test since costs are non-negative) is abandoned
+ * and gets +INF; +INF disables abandoning.  out is [N] (root taken).
+ */
+dtw_status dtw_band(const float *x, const float *y, int64_t N, int32_t y_stride,
+                    int32_t n, int32_t w, int32_t p, float threshold, float *out,
+                    void *stream);
+
+/*
+ * Exact k nearest neighbours under DTW_p with band w (Sec. 7-8 problem
+ * statement, generalised from 1 to k neighbours): for each of the Q queries
+ * [Q][n], the k database series db [N][n] of smallest DTW_p, ordered by
+ * (distance, index) ascending, so that ties go to the lower index.  The
+ * cascade computes the query envelopes, LB_Keogh of every pair, the DTW of
+ * the lowest-bound seeds, LB_Improved of the LB_Keogh survivors and a DTW
+ * with early abandoning of the LB_Improved survivors, every stage pruning
+ * against the current k-th best distance.
+ * out_idx [Q][k] (int64) and out_dist [Q][k] (fp32, root taken) receive the
+ * result; when k > N the tail is idx -1, distance +INF.
+ * db, queries, out_idx and out_dist may each be host or device memory; host
+ * inputs are copied in, and host outputs make the call synchronous.
+ * stats (host, nullable) receives counters and also makes the call
+ * synchronous.
+ */
+dtw_status knn_search(const float *db, int64_t N, const float *queries, int64_t Q,
+                      int32_t n, int32_t w, int32_t p, int32_t k, int64_t *out_idx,
+                      float *out_dist, dtw_stats *stats, void *stream);
+
+/* knn_search with a cascade mode, slack and seed count (opt may be NULL). */
+dtw_status knn_search_ex(const float *db, int64_t N, const float *queries, int64_t Q,
+                         int32_t n, int32_t w, int32_t p, int32_t k,
+                         const dtw_options *opt, int64_t *out_idx, float *out_dist,
+                         dtw_stats *stats, void *stream);
+
+/*
+ * Stage timing.  While enabled, knn_search records a pair of CUDA events on
+ * its stream around each stage (stage index: DTW_STAGE_*), so that the
+ * device time of each kernel is measured on the stream it runs on.
+ * dtw_profile_read waits for the recorded events, adds their elapsed times
+ * into *out (milliseconds and launch counts per stage) and, if reset is
+ * non-zero, forgets them.  Recording costs two event records per stage.
+ */
+enum {
+    DTW_STAGE_ENVELOPE = 0,
+    DTW_STAGE_LB_KEOGH = 1,
+    DTW_STAGE_SEED_SELECT = 2,
+    DTW_STAGE_SEED_DTW = 3,
+    DTW_STAGE_SEED_KTH = 4,
+    DTW_STAGE_LB_IMPROVED = 5,
+    DTW_STAGE_DTW = 6,
+    DTW_STAGE_FINALIZE = 7,
+    DTW_NUM_STAGES = 8
+};
+typedef struct {
+    double ms[DTW_NUM_STAGES];
+    int64_t launches[DTW_NUM_STAGES];
+} dtw_profile;
+
+dtw_status dtw_profile_enable(int32_t on);
+dtw_status dtw_profile_read(dtw_profile *out, int32_t reset);
+
+/* Message of the last failed call on this host thread ("" if none). */
+const char *dtw_last_error(void);
+
+/* Library version string. */
+const char *dtw_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DTWKNN_H */

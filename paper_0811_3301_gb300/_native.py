@@ -1,0 +1,123 @@
+"""ctypes binding of libdtwknn.so (the C ABI of include/dtwknn.h).
+
+Argument marshalling only: every step of the cascade runs in the library's
+CUDA kernels.  Importing this module loads the in-tree library and fails
+loudly when it is missing; there is no CPU fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdtwknn.so")
+
+DTW_OK = 0
+STATUS_NAMES = {
+    0: "DTW_OK",
+    1: "DTW_ERR_INVALID_ARG",
+    2: "DTW_ERR_CUDA",
+    3: "DTW_ERR_OOM",
+    4: "DTW_ERR_TIMEOUT",
+    5: "DTW_ERR_NO_BUCKET",
+    6: "DTW_ERR_INTERNAL",
+}
+MODE_IMPROVED, MODE_KEOGH, MODE_NOPRUNE = 0, 1, 2
+MAX_N = 4096
+MAX_K = 128
+
+
+class DtwError(RuntimeError):
+    """A library call returned a status other than DTW_OK."""
+
+    def __init__(self, status: int, message: str):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, str(status)), message))
+        self.status = status
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [
+        ("candidates", ctypes.c_int64),
+        ("seeds", ctypes.c_int64),
+        ("pruned_keogh", ctypes.c_int64),
+        ("pruned_improved", ctypes.c_int64),
+        ("dtw_computed", ctypes.c_int64),
+        ("dtw_abandoned", ctypes.c_int64),
+        ("dtw_cells", ctypes.c_int64),
+        ("seed_cells", ctypes.c_int64),
+    ]
+
+    def as_dict(self) -> dict:
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
+NUM_STAGES = 8
+STAGE_NAMES = ["envelope", "lb_keogh", "seed_select", "seed_dtw", "seed_kth", "lb_improved", "dtw", "finalize"]
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * NUM_STAGES), ("launches", ctypes.c_int64 * NUM_STAGES)]
+
+    def as_dict(self) -> dict:
+        return {name: {"ms": float(self.ms[i]), "launches": int(self.launches[i])} for i, name in enumerate(STAGE_NAMES)}
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("slack", ctypes.c_float), ("seeds", ctypes.c_int32)]
+
+
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_i32 = ctypes.c_int32
+_f32 = ctypes.c_float
+
+# name -> argtypes; every entry point returns dtw_status (int)
+SIGNATURES = {
+    "dtw_envelope": [_vp, _i64, _i32, _i32, _vp, _vp, _vp],
+    "lb_keogh": [_vp, _i64, _vp, _vp, _i32, _i32, _vp, _vp],
+    "lb_improved": [_vp, _i64, _vp, _vp, _vp, _i32, _i32, _i32, _vp, _vp],
+    "dtw_band": [_vp, _vp, _i64, _i32, _i32, _i32, _i32, _f32, _vp, _vp],
+    "knn_search": [_vp, _i64, _vp, _i64, _i32, _i32, _i32, _i32, _vp, _vp, ctypes.POINTER(Stats), _vp],
+    "dtw_profile_enable": [_i32],
+    "dtw_profile_read": [ctypes.c_void_p, _i32],
+    "knn_search_ex": [_vp, _i64, _vp, _i64, _i32, _i32, _i32, _i32, ctypes.POINTER(Options), _vp, _vp,
+                      ctypes.POINTER(Stats), _vp],
+}
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libdtwknn.so is not built (%s); run `python -m paper_0811_3301_gb300.build`" % LIB_PATH)
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, args in SIGNATURES.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    lib.dtw_last_error.argtypes = []
+    lib.dtw_last_error.restype = ctypes.c_char_p
+    lib.dtw_version.argtypes = []
+    lib.dtw_version.restype = ctypes.c_char_p
+    return lib
+
+
+lib = _load()
+
+
+def check(status: int) -> None:
+    if status != DTW_OK:
+        raise DtwError(status, lib.dtw_last_error().decode(errors="replace"))
+
+
+def profile_enable(on: bool) -> None:
+    check(lib.dtw_profile_enable(1 if on else 0))
+
+
+def profile_read(reset: bool = True) -> dict:
+    p = Profile()
+    check(lib.dtw_profile_read(ctypes.byref(p), 1 if reset else 0))
+    return p.as_dict()
+
+
+def version() -> str:
+    return lib.dtw_version().decode()

@@ -1,0 +1,142 @@
+"""Python entry points of the DTW retrieval cascade, one per C-ABI call.
+
+Each function checks and marshals torch tensors (device memory and the
+current CUDA stream come from PyTorch) and calls the same-named function of
+libdtwknn.so; all arithmetic runs in the library's sm_103a kernels.
+Bounds and distances carry the p-th root, as in the paper.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import math
+
+import torch
+
+from . import _native as N
+
+__all__ = ["dtw_envelope", "lb_keogh", "lb_improved", "dtw_band", "knn_search", "DtwError", "version"]
+
+DtwError = N.DtwError
+version = N.version
+
+_MODES = {"improved": N.MODE_IMPROVED, "keogh": N.MODE_KEOGH, "noprune": N.MODE_NOPRUNE}
+
+
+def _stream() -> int:
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _cuda_f32(t: torch.Tensor, name: str) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if t.dtype != torch.float32:
+        raise TypeError("%s must be float32" % name)
+    return t.contiguous()
+
+
+def _f32(t: torch.Tensor, name: str) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.float32:
+        raise TypeError("%s must be a float32 tensor" % name)
+    return t.contiguous()
+
+
+def _ptr(t: torch.Tensor | None) -> int | None:
+    return None if t is None else t.data_ptr()
+
+
+def dtw_envelope(y: torch.Tensor, w: int, U: torch.Tensor | None = None, L: torch.Tensor | None = None):
+    """Warping envelope (U, L) of each row of y ([count, n] or [n]), Sec. 5."""
+    y = _cuda_f32(y, "y")
+    y2 = y.reshape(-1, y.shape[-1])
+    U = torch.empty_like(y2) if U is None else U
+    L = torch.empty_like(y2) if L is None else L
+    N.check(N.lib.dtw_envelope(_ptr(y2), y2.shape[0], y2.shape[1], int(w), _ptr(U), _ptr(L), _stream()))
+    return U.reshape(y.shape), L.reshape(y.shape)
+
+
+def lb_keogh(cand: torch.Tensor, U: torch.Tensor, L: torch.Tensor, p: int, out: torch.Tensor | None = None):
+    """LB_Keogh_p of every row of cand [N, n] against one query envelope U, L [n] (Sec. 7)."""
+    cand = _cuda_f32(cand, "cand")
+    U = _cuda_f32(U, "U")
+    L = _cuda_f32(L, "L")
+    n = cand.shape[-1]
+    if U.numel() != n or L.numel() != n:
+        raise ValueError("U and L must have n = %d elements" % n)
+    out = torch.empty(cand.shape[0], device=cand.device, dtype=torch.float32) if out is None else out
+    N.check(N.lib.lb_keogh(_ptr(cand), cand.shape[0], _ptr(U), _ptr(L), n, int(p), _ptr(out), _stream()))
+    return out
+
+
+def lb_improved(cand: torch.Tensor, q: torch.Tensor, U: torch.Tensor, L: torch.Tensor, w: int, p: int,
+                out: torch.Tensor | None = None):
+    """LB_Improved_p of every row of cand [N, n] against query q [n] with envelope U, L (Sec. 8)."""
+    cand = _cuda_f32(cand, "cand")
+    q = _cuda_f32(q, "q")
+    U = _cuda_f32(U, "U")
+    L = _cuda_f32(L, "L")
+    n = cand.shape[-1]
+    if q.numel() != n or U.numel() != n or L.numel() != n:
+        raise ValueError("q, U and L must have n = %d elements" % n)
+    out = torch.empty(cand.shape[0], device=cand.device, dtype=torch.float32) if out is None else out
+    N.check(N.lib.lb_improved(_ptr(cand), cand.shape[0], _ptr(q), _ptr(U), _ptr(L), n, int(w), int(p),
+                              _ptr(out), _stream()))
+    return out
+
+
+def dtw_band(x: torch.Tensor, y: torch.Tensor, w: int, p: int, threshold: float = math.inf,
+             out: torch.Tensor | None = None):
+    """DTW_p with band w of the rows of x [N, n] against y ([n] shared, or [N, n] per pair), Sec. 4.
+
+    With a finite threshold, pairs whose DTW_p exceeds it return +inf.
+    """
+    x = _cuda_f32(x, "x")
+    y = _cuda_f32(y, "y")
+    n = x.shape[-1]
+    if y.dim() == 1:
+        if y.shape[0] != n:
+            raise ValueError("y must have n = %d elements" % n)
+        stride = 0
+    else:
+        if y.shape != x.shape:
+            raise ValueError("per-pair y must have the shape of x")
+        stride = n
+    out = torch.empty(x.shape[0], device=x.device, dtype=torch.float32) if out is None else out
+    N.check(N.lib.dtw_band(_ptr(x), _ptr(y), x.shape[0], stride, n, int(w), int(p), float(threshold),
+                           _ptr(out), _stream()))
+    return out
+
+
+def knn_search(db: torch.Tensor, queries: torch.Tensor, w: int, p: int, k: int = 1, *, mode: str = "improved",
+               slack: float = 1e-6, seeds: int = 0, out_idx: torch.Tensor | None = None,
+               out_dist: torch.Tensor | None = None, return_stats: bool = False):
+    """Exact k nearest neighbours of each query row under DTW_p with band w (Sec. 7-8).
+
+    db [N, n] and queries [Q, n] may live on the GPU or in host memory
+    (host tensors are copied by the library).  Returns (idx int64 [Q, k],
+    dist float32 [Q, k]) ordered by (distance, index); with return_stats
+    also the cascade counters.  Outputs default to the device of `queries`
+    when it is a CUDA tensor, else to host memory.
+    """
+    db = _f32(db, "db")
+    queries = _f32(queries, "queries")
+    if queries.dim() == 1:
+        queries = queries.unsqueeze(0)
+    if db.dim() != 2 or queries.dim() != 2 or db.shape[1] != queries.shape[1]:
+        raise ValueError("db [N, n] and queries [Q, n] must share n")
+    Q, n = queries.shape
+    dev = queries.device
+    if out_idx is None:
+        out_idx = torch.empty((Q, k), dtype=torch.int64, device=dev, pin_memory=not queries.is_cuda and torch.cuda.is_available())
+    if out_dist is None:
+        out_dist = torch.empty((Q, k), dtype=torch.float32, device=dev, pin_memory=not queries.is_cuda and torch.cuda.is_available())
+    if mode not in _MODES:
+        raise ValueError("mode must be one of %s" % sorted(_MODES))
+    opt = N.Options(_MODES[mode], float(slack), int(seeds))
+    st = N.Stats()
+    N.check(N.lib.knn_search_ex(_ptr(db), db.shape[0], _ptr(queries), Q, n, int(w), int(p), int(k),
+                                ctypes.byref(opt), _ptr(out_idx), _ptr(out_dist),
+                                ctypes.byref(st) if return_stats else None, _stream()))
+    if return_stats:
+        return out_idx, out_dist, st.as_dict()
+    return out_idx, out_dist

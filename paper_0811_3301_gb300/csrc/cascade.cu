@@ -1,0 +1,208 @@
+// Best-so-far linking of the cascade (Algorithms 2 and 3, generalised to k
+// neighbours): seed selection, the seed threshold, and the final ordered
+// top-k.  The threshold b of a query is its current k-th best DTW_p^p (fp32
+// bits, so that atomicMin orders it); candidates are compared by
+// (distance, index), so ties go to the lower index as in a sequential scan
+// with strict "<" tests.
+#include "common.cuh"
+
+namespace dtwk {
+
+constexpr int kSeedMax = 32;
+
+__device__ __forceinline__ unsigned long long pack_key(float d, int c) {
+    return ((unsigned long long)__float_as_uint(d) << 32) | (unsigned)c;
+}
+
+// ---------------------------------------------------------------------------
+// Seeds: per query, the S candidates of smallest LB_Keogh (ties to the lower
+// index).  Their exact DTW is computed first so that the threshold is close
+// to its final value before the bulk of the candidates is filtered; this is
+// the GPU counterpart of visiting candidates in order of their lower bound.
+// One CTA per query; each thread keeps a sorted list of its kSeedMax best
+// keys, then S rounds of a block-wide minimum pop the global best.
+// Also resets the query's thresholds to +INF.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_seed_select(CascadeBufs b) {
+    const int q = blockIdx.x;
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    if (t == 0) b.bsf[q] = 0x7f800000u;
+    for (int g = t; g < b.k; g += blockDim.x) b.gmin[(int64_t)q * b.k + g] = 0x7f800000u;
+    unsigned long long key[kSeedMax];
+#pragma unroll
+    for (int s = 0; s < kSeedMax; ++s) key[s] = ~0ull;
+    const float *row = b.lb + (int64_t)q * b.N;
+    for (int c = t; c < b.N; c += blockDim.x) {
+        unsigned long long v = pack_key(row[c], c);
+        if (v < key[kSeedMax - 1]) {
+            // insertion into the sorted list
+#pragma unroll
+            for (int s = kSeedMax - 1; s > 0; --s) {
+                unsigned long long prev = key[s - 1];
+                bool shift = v < prev;
+                key[s] = shift ? prev : (v < key[s] ? v : key[s]);
+            }
+            key[0] = v < key[0] ? v : key[0];
+        }
+    }
+    __shared__ unsigned long long wmin[8];
+    __shared__ unsigned long long winner;
+    for (int s = 0; s < b.S; ++s) {
+        unsigned long long m = key[0];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            unsigned long long other = __shfl_xor_sync(0xffffffffu, m, o);
+            m = other < m ? other : m;
+        }
+        if (lane == 0) wmin[wid] = m;
+        __syncthreads();
+        if (t == 0) {
+            unsigned long long best = wmin[0];
+            for (int v = 1; v < (int)(blockDim.x >> 5); ++v) best = wmin[v] < best ? wmin[v] : best;
+            winner = best;
+            int c = (best == ~0ull) ? -1 : (int)(unsigned)(best & 0xffffffffull);
+            b.seed_pairs[(int64_t)q * b.S + s] = Pair{q, c};
+            b.seed_res[(int64_t)q * b.S + s] = kInf;
+        }
+        __syncthreads();
+        if (key[0] == winner && winner != ~0ull) {
+            // pop: only the owner holds this (unique) key
+#pragma unroll
+            for (int u = 0; u + 1 < kSeedMax; ++u) key[u] = key[u + 1];
+            key[kSeedMax - 1] = ~0ull;
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_seed_select(const CascadeBufs &b, cudaStream_t s) {
+    if (b.Q <= 0) return cudaSuccess;
+    k_seed_select<<<b.Q, 256, 0, s>>>(b);
+    return cudaGetLastError();
+}
+
+// After the seeds' DTW: b = k-th smallest seed distance (one warp per query).
+__global__ void k_seed_kth(CascadeBufs b) {
+    const int q = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (q >= b.Q) return;
+    unsigned long long mine = ~0ull;
+    if (lane < b.S) {
+        Pair pr = b.seed_pairs[(int64_t)q * b.S + lane];
+        float d = b.seed_res[(int64_t)q * b.S + lane];
+        if (pr.c >= 0 && d < kInf) mine = pack_key(d, pr.c);
+    }
+    int rank = 0;
+    for (int o = 0; o < 32; ++o) {
+        unsigned long long other = __shfl_sync(0xffffffffu, mine, o);
+        rank += (other < mine) ? 1 : 0;
+    }
+    if (mine != ~0ull && rank == b.k - 1) atomicMin(b.bsf + q, (uint32_t)(mine >> 32));
+}
+
+cudaError_t launch_seed_kth(const CascadeBufs &b, cudaStream_t s) {
+    if (b.Q <= 0 || b.S < b.k) return cudaSuccess;
+    const int per = 4;
+    k_seed_kth<<<(b.Q + per - 1) / per, 32 * per, 0, s>>>(b);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Final top-k per query: the k smallest (distance, index) keys among the
+// seeds and the listed pairs whose DTW completed, keeping only distances not
+// above the final threshold (every true neighbour satisfies that).  k rounds
+// of a block-wide minimum over keys greater than the previous round's key.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_finalize(CascadeBufs b) {
+    const int q = blockIdx.x;
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    const float bq = __uint_as_float(b.bsf[q]);
+    __shared__ unsigned long long wmin[8];
+    __shared__ unsigned long long sel;
+    unsigned long long last = 0;
+    bool first = true;
+    for (int r = 0; r < b.k; ++r) {
+        unsigned long long m = ~0ull;
+        for (int s = t; s < b.S; s += blockDim.x) {
+            Pair pr = b.seed_pairs[(int64_t)q * b.S + s];
+            float d = b.seed_res[(int64_t)q * b.S + s];
+            if (pr.c >= 0 && d < kInf && d <= bq) {
+                unsigned long long v = pack_key(d, pr.c);
+                if ((first || v > last) && v < m) m = v;
+            }
+        }
+        for (int sg = 0; sg < b.nseg; ++sg) {
+            const int cnt = b.seg_count[(int64_t)q * b.nseg + sg];
+            const int64_t base = b.seg_start[(int64_t)q * b.nseg + sg];
+            for (int e = t; e < cnt; e += blockDim.x) {
+                float d = b.pair_res[base + e];
+                if (d < kInf && d <= bq) {
+                    unsigned long long v = pack_key(d, b.pairs[base + e].c);
+                    if ((first || v > last) && v < m) m = v;
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            unsigned long long other = __shfl_xor_sync(0xffffffffu, m, o);
+            m = other < m ? other : m;
+        }
+        if (lane == 0) wmin[wid] = m;
+        __syncthreads();
+        if (t == 0) {
+            unsigned long long best = wmin[0];
+            for (int v = 1; v < (int)(blockDim.x >> 5); ++v) best = wmin[v] < best ? wmin[v] : best;
+            sel = best;
+            int64_t o = (int64_t)q * b.k + r;
+            if (best == ~0ull) {
+                b.out_idx[o] = -1;
+                b.out_dist[o] = kInf;
+            } else {
+                b.out_idx[o] = (int64_t)(best & 0xffffffffull);
+                b.out_dist[o] = root_p(__uint_as_float((uint32_t)(best >> 32)), b.p);
+            }
+        }
+        __syncthreads();
+        last = sel;
+        first = false;
+        if (last == ~0ull) {
+            // nothing left: pad the remaining ranks
+            for (int rr = r + 1 + t; rr < b.k; rr += blockDim.x) {
+                b.out_idx[(int64_t)q * b.k + rr] = -1;
+                b.out_dist[(int64_t)q * b.k + rr] = kInf;
+            }
+            break;
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_finalize(const CascadeBufs &b, cudaStream_t s) {
+    if (b.Q <= 0) return cudaSuccess;
+    k_finalize<<<b.Q, 256, 0, s>>>(b);
+    return cudaGetLastError();
+}
+
+// Shifted, +INF-padded query copies only (no envelope), for dtw_band.
+__global__ void k_query_copies(const float *__restrict__ y, int64_t count, int n, float *copies,
+                               int padl, int ylen) {
+    const int64_t total = count * 4 * (int64_t)ylen;
+    for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < total;
+         o += (int64_t)gridDim.x * blockDim.x) {
+        int64_t row = o / (4 * (int64_t)ylen);
+        int rem = (int)(o - row * 4 * (int64_t)ylen);
+        int r = rem / ylen, tt = rem - r * ylen;
+        int j = tt + r - padl;
+        copies[o] = (j >= 0 && j < n) ? y[row * n + j] : kInf;
+    }
+}
+
+cudaError_t launch_query_copies(const float *y, int64_t count, int n, QueryCopies qc, cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    int64_t total = count * 4 * (int64_t)qc.ylen;
+    int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)device_sm_count() * 16);
+    k_query_copies<<<blocks, 256, 0, s>>>(y, count, n, qc.data, qc.padl, qc.ylen);
+    return cudaGetLastError();
+}
+
+}  // namespace dtwk

@@ -1,0 +1,185 @@
+// Shared device helpers and internal launcher declarations of the DTW cascade
+// library (sm_103a).  Internal: the public ABI is include/dtwknn.h.
+#pragma once
+
+#include <algorithm>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/dtwknn.h"
+
+namespace dtwk {
+
+constexpr float kInf = __builtin_huge_valf();
+
+// Three-input fp32 min/max (PTX ISA 8.8, sm_100+).  NaN-free inputs only.
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+    float d;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+    float d;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
+// (k == m) ? a : b, written in PTX so that loops of such selects over a
+// register array are not folded into a dynamically indexed (local-memory)
+// access by the optimiser.
+__device__ __forceinline__ float sel_eq(int k, int m, float a, float b) {
+    float r;
+    asm("{\n\t.reg .pred p;\n\tsetp.eq.s32 p, %1, %2;\n\tselp.f32 %0, %3, %4, p;\n\t}"
+        : "=f"(r)
+        : "r"(k), "r"(m), "f"(a), "f"(b));
+    return r;
+}
+
+// Distance from v to the interval [lo, hi] (lo <= hi), raised to the power P:
+// the per-index term of LB_Keogh (Sec. 7, Eq. 1): |v - H_i|^P.
+template <int P>
+__device__ __forceinline__ float dist_pow(float v, float lo, float hi) {
+    float d = max3f(v - hi, lo - v, 0.0f);
+    return P == 1 ? d : d * d;
+}
+template <int P>
+__device__ __forceinline__ float acc_dist(float acc, float v, float lo, float hi) {
+    float d = max3f(v - hi, lo - v, 0.0f);
+    return P == 1 ? acc + d : fmaf(d, d, acc);
+}
+
+// Root of a power-space value (the paper's DTW_p and LB_p carry the root).
+__device__ __forceinline__ float root_p(float v, int p) { return p == 1 ? v : sqrtf(v); }
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Non-negative floats order like their bit patterns; +INF is 0x7f800000.
+__device__ __forceinline__ float load_threshold(const uint32_t *bits) {
+    return __uint_as_float(*(volatile const uint32_t *)bits);
+}
+
+// Worst-case relative fp32 rounding of the quantities compared by the
+// pruning tests (derivation in the design notes): an LB sum of up to 2n
+// terms and a DTW path sum of up to 2n - 1 cells, each term rounded once.
+__host__ __device__ inline float auto_slack(int n) {
+    const double u = 5.9604644775390625e-8;  // 2^-24
+    return (float)((4.0 * n + 16.0) * u * 1.0625);
+}
+
+// ---------------------------------------------------------------------------
+// Per-query preprocessed data used by the DTW kernels: four copies of the
+// query padded with +INF on both sides and shifted by 0..3 elements, so that
+// any band window starts on a 16-byte boundary in one of the copies.
+//   ycopy[(q * 4 + r) * ylen + t] = ypad(t + r - padl),
+//   ypad(j) = y[j] for 0 <= j < n, +INF otherwise.
+// ---------------------------------------------------------------------------
+struct QueryCopies {
+    float *data = nullptr;
+    int padl = 0;   // multiple of 4
+    int ylen = 0;   // multiple of 4
+};
+
+
+// ---------------------------------------------------------------------------
+// Launchers (all asynchronous on `s`; they return cudaGetLastError()).
+// ---------------------------------------------------------------------------
+cudaError_t launch_envelope(const float *y, int64_t count, int n, int w, float *U, float *L,
+                            QueryCopies qc, int copies_padl, cudaStream_t s);
+
+cudaError_t launch_lbk_single(const float *cand, int64_t N, const float *U, const float *L, int n,
+                              int p, float *out, cudaStream_t s);
+cudaError_t launch_lbk_tile(const float *db, int N, const float *U, const float *L, int Q, int n,
+                            int p, float *lb, cudaStream_t s);
+
+// One (query, candidate) pair for the LB_Improved and DTW stages.
+struct Pair {
+    int32_t q;
+    int32_t c;
+};
+
+cudaError_t launch_lbi_single(const float *cand, int64_t N, const float *q, const float *U,
+                              const float *L, int n, int w, int p, float *out, cudaStream_t s);
+
+struct CascadeBufs {
+    // inputs
+    const float *db;        // [N][n]
+    const float *queries;   // [Q][n]
+    const float *U, *L;     // [Q][n]
+    QueryCopies qc;
+    int N, Q, n, w, p, k, mode;
+    float slack;
+    // LB_Keogh matrix, [Q][N], power space
+    float *lb;
+    // seeds: [Q][S]
+    int S;
+    Pair *seed_pairs;
+    float *seed_res;
+    // thresholds: group minima [Q][k] and the bound [Q], float bits
+    uint32_t *gmin;
+    uint32_t *bsf;
+    // survivors of the bound stages
+    Pair *pairs;
+    float *pair_lbi;
+    float *pair_res;
+    int64_t pair_cap;
+    unsigned long long *pair_count;
+    int seg_len, nseg;
+    int32_t *seg_start;   // [Q][nseg]
+    int32_t *seg_count;   // [Q][nseg]
+    // work cursors and counters
+    unsigned long long *cursor;       // DTW chunk cursor
+    unsigned long long *counters;     // 8 counters, see dtw_stats
+    // outputs (device)
+    int64_t *out_idx;
+    float *out_dist;
+};
+
+cudaError_t launch_seed_select(const CascadeBufs &b, cudaStream_t s);
+cudaError_t launch_seed_kth(const CascadeBufs &b, cudaStream_t s);
+cudaError_t launch_query_copies(const float *y, int64_t count, int n, QueryCopies qc, cudaStream_t s);
+cudaError_t launch_lbi_filter(const CascadeBufs &b, cudaStream_t s);
+cudaError_t launch_finalize(const CascadeBufs &b, cudaStream_t s);
+
+// DTW over an explicit pair list (pairs != nullptr) or the implicit pairs
+// c -> (q = per_pair_y ? c : 0, c).  thr_bits: per-query thresholds (float
+// bits, power space) read live for early abandoning, or nullptr with a fixed
+// power-space threshold fixed_thr.  res receives DTW^p or +INF.
+struct DtwJob {
+    const float *db;
+    int n, w, p, k;
+    QueryCopies qc;
+    const Pair *pairs;        // or nullptr
+    int64_t npairs;           // pair count, or the upper bound when npairs_dev is set
+    const unsigned long long *npairs_dev;  // nullable: pair count in device memory
+    int per_pair_y;           // implicit pairs: query index = pair index
+    const float *pair_lbi;    // nullable: skip a pair whose bound exceeds the live threshold
+    float slack;
+    uint32_t *bsf;            // nullable: live per-query threshold (updated on completion)
+    uint32_t *gmin;           // nullable: per-query group minima [Q][k]
+    float fixed_thr;          // used when bsf == nullptr
+    int abandon;              // 0: never abandon
+    float *res;               // [npairs]
+    int root_out;             // store DTW_p (root taken) instead of DTW_p^p
+    unsigned long long *cursor;    // chunk cursor (zeroed by the caller)
+    unsigned long long *counters;  // nullable
+};
+
+
+// counters layout
+enum {
+    CNT_KEOGH_PASS = 0,     // non-seed pairs with LB_Keogh^p <= thr
+    CNT_LBI_PASS = 1,       // pairs written to the DTW list
+    CNT_DTW_SKIP = 2,       // listed pairs skipped because the live threshold fell below their bound
+    CNT_DTW_COMPUTED = 3,   // listed pairs whose DTW was started
+    CNT_DTW_ABANDONED = 4,  // of which abandoned early
+    CNT_DTW_ROWS = 5,       // DP rows evaluated
+    CNT_NUM = 8
+};
+
+int device_sm_count();
+
+}  // namespace dtwk

@@ -1,0 +1,59 @@
+// Band-constrained DTW_p with early abandoning (Sec. 4 recursion; early
+// abandoning as cited in Sec. 3).  The paper's suffix recursion
+//   q_{i,j} = |x_i - y_j|^p + min(q_{i+1,j}, q_{i,j+1}, q_{i+1,j+1})
+// is evaluated here in the mirrored prefix form
+//   D(i,j) = |x_i - y_j|^p + min(D(i-1,j), D(i,j-1), D(i-1,j-1)),
+// D(-1,-1) = 0, other out-of-range or out-of-band cells +INF, which is the same
+// minimum over the same warping paths.  Rows i = 0..n-1 are swept in order;
+// a row holds the band cells j = i-w..i+w in "slots" k, column j = i - wl + k.
+//
+// Early abandoning: costs are >= 0 and fp32 addition of a non-negative term
+// never decreases a value, so every path's fp32 sum is at least the minimum
+// of any row it crosses; once a row minimum exceeds the threshold the final
+// value does too, and the pair is abandoned (result +INF).
+#pragma once
+#include "common.cuh"
+
+namespace dtwk {
+
+constexpr int kDtwRegMaxC = 208;  // widest band kept in one thread's registers
+constexpr int kDtwThreads = 128;
+
+struct DtwGeom {
+    int C;      // slots per pair (register path) or per warp (wide path)
+    int e;      // bottom padding slots (register path), 0 for the wide path
+    int wl;     // slot k holds column i - wl + k
+    int padl;   // query copy left padding
+    int ylen;   // query copy length
+    bool wide;  // warp-split wide-band path
+    int cl;     // wide path: slots per lane
+};
+
+inline DtwGeom dtw_geom(int n, int w) {
+    DtwGeom g{};
+    w = w < n - 1 ? w : n - 1;
+    const int bw = 2 * w + 1;
+    if (bw <= kDtwRegMaxC) {
+        g.C = (bw + 15) / 16 * 16;
+        g.e = g.C - bw;
+        g.wl = w + g.e;
+        g.wide = false;
+        g.cl = 0;
+    } else {
+        int cl = 8;
+        while (32 * cl < bw) cl *= 2;
+        g.cl = cl;
+        g.C = 32 * cl;
+        g.e = 0;
+        g.wl = w;
+        g.wide = true;
+    }
+    g.padl = g.C;                               // >= wl, multiple of 4
+    g.ylen = (n + g.padl + g.C + w + 1 + 3) / 4 * 4;
+    return g;
+}
+
+cudaError_t launch_dtw_p1(const DtwJob &j, const DtwGeom &g, cudaStream_t s);
+cudaError_t launch_dtw_p2(const DtwJob &j, const DtwGeom &g, cudaStream_t s);
+
+}  // namespace dtwk

@@ -1,0 +1,314 @@
+// DTW kernel bodies, instantiated per band width in dtw_p1.cu / dtw_p2.cu.
+#pragma once
+#include "dtw.cuh"
+
+namespace dtwk {
+
+// Update the k-NN thresholds of query q after a completed DTW value d
+// (power space) of candidate c: group minima gmin[q][g] (g = c mod k) and the
+// bound bsf[q] = max_g gmin[q][g], an upper bound on the k-th best distance
+// because the k groups hold k distinct candidates.  Both only decrease.
+__device__ __forceinline__ void update_threshold(uint32_t *bsf, uint32_t *gmin, int k, int q, int g,
+                                                 float d) {
+    const uint32_t bits = __float_as_uint(d);
+    if (k == 1) {
+        atomicMin(bsf + q, bits);
+        return;
+    }
+    uint32_t old = atomicMin(gmin + (int64_t)q * k + g, bits);
+    if (bits < old) {
+        uint32_t mx = 0;
+        for (int t = 0; t < k; ++t) {
+            uint32_t v = *(volatile uint32_t *)(gmin + (int64_t)q * k + t);
+            mx = v > mx ? v : mx;
+        }
+        atomicMin(bsf + q, mx);
+    }
+}
+
+__device__ __forceinline__ void fetch_pair(const DtwJob &j, int64_t pi, int &q, int &c, bool &valid) {
+    valid = pi < j.npairs;
+    q = 0;
+    c = 0;
+    if (valid) {
+        if (j.pairs) {
+            Pair pr = j.pairs[pi];
+            q = pr.q;
+            c = pr.c;
+        } else {
+            c = (int)pi;
+            q = j.per_pair_y ? (int)pi : 0;
+        }
+        if (c < 0) valid = false;
+    }
+}
+
+// One band cell: slot K of the current row.  D[K] holds D(i-1, j-1) on entry,
+// D[K+1] holds D(i-1, j), D[K-1] already holds D(i, j-1).
+template <int K, int C, int P>
+__device__ __forceinline__ void dtw_cell(float (&D)[C], float xi, float yv) {
+    float above, below;
+    if constexpr (K + 1 < C) above = D[K + 1]; else above = kInf;
+    if constexpr (K > 0) below = D[K - 1]; else below = kInf;
+    const float m = min3f(D[K], above, below);
+    const float d = xi - yv;
+    D[K] = (P == 1) ? fabsf(d) + m : fmaf(d, d, m);
+}
+#define DTW_CELL(K, YV) dtw_cell<K, C, P>(D, xi, YV);
+
+// Cells K..C-1, four per 128-bit load of the query window.
+template <int K, int C, int P>
+__device__ __forceinline__ void dtw_cells_from(float (&D)[C], float xi, const float4 *yb) {
+    if constexpr (K < C) {
+        const float4 t = __ldg(yb + (K >> 2));
+        dtw_cell<K, C, P>(D, xi, t.x);
+        dtw_cell<K + 1, C, P>(D, xi, t.y);
+        dtw_cell<K + 2, C, P>(D, xi, t.z);
+        dtw_cell<K + 3, C, P>(D, xi, t.w);
+        dtw_cells_from<K + 4, C, P>(D, xi, yb);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Register path: one thread per pair, the whole band of C = round_up(2w+1, 16)
+// slots in registers.  The band occupies slots e..C-1 (e = C - (2w+1) < 16);
+// slots below e are never written and stay +INF.  Each row enters the
+// unrolled cell sequence at slot e (a jump on the uniform e).  The query band
+// window is read from the four shifted copies with aligned 128-bit loads;
+// when the 32 lanes of a warp share a query these are broadcasts.
+// Pairs are taken 32 at a time from a global cursor (persistent grid).
+// ---------------------------------------------------------------------------
+template <int C, int P>
+__global__ void __launch_bounds__(kDtwThreads)
+k_dtw_reg(DtwJob j, int e, int wl) {
+    const int lane = threadIdx.x & 31;
+    const int n = j.n;
+    const int ylen = j.qc.ylen, padl = j.qc.padl;
+    if (j.npairs_dev) j.npairs = (int64_t)*j.npairs_dev;
+    unsigned long long n_skip = 0, n_comp = 0, n_aband = 0, n_rows = 0;
+    for (;;) {
+        unsigned long long chunk = 0;
+        if (lane == 0) chunk = atomicAdd(j.cursor, 1ull);
+        chunk = __shfl_sync(0xffffffffu, chunk, 0);
+        const int64_t p0 = (int64_t)chunk * 32;
+        if (p0 >= j.npairs) break;
+        const int64_t pi = p0 + lane;
+        int q, c;
+        bool valid;
+        fetch_pair(j, pi, q, c, valid);
+        float thr = kInf;
+        if (valid) {
+            thr = j.bsf ? load_threshold(j.bsf + q) : j.fixed_thr;
+            if (j.pair_lbi && j.pair_lbi[pi] > thr * (1.0f + j.slack)) {
+                j.res[pi] = kInf;
+                valid = false;
+                ++n_skip;
+            }
+        }
+        if (valid) {
+        ++n_comp;
+        const float *x = j.db + (int64_t)c * n;
+        const float *yc = j.qc.data + (int64_t)q * 4 * ylen;
+        float D[C];
+#pragma unroll
+        for (int k = 0; k < C; ++k) D[k] = sel_eq(k, wl, 0.0f, kInf);  // row -1: D(-1,-1) = 0
+        bool abandoned = false;
+        int rows = n;
+        for (int i = 0; i < n; ++i) {
+            const float xi = __ldg(x + i);
+            const int a = i - wl + padl;
+            const int r = a & 3;
+            const float4 *yb = reinterpret_cast<const float4 *>(yc + r * ylen + (a - r));
+            const float4 h0 = __ldg(yb + 0), h1 = __ldg(yb + 1), h2 = __ldg(yb + 2), h3 = __ldg(yb + 3);
+            switch (e) {
+                case 0: DTW_CELL(0, h0.x) [[fallthrough]];
+                case 1: DTW_CELL(1, h0.y) [[fallthrough]];
+                case 2: DTW_CELL(2, h0.z) [[fallthrough]];
+                case 3: DTW_CELL(3, h0.w) [[fallthrough]];
+                case 4: DTW_CELL(4, h1.x) [[fallthrough]];
+                case 5: DTW_CELL(5, h1.y) [[fallthrough]];
+                case 6: DTW_CELL(6, h1.z) [[fallthrough]];
+                case 7: DTW_CELL(7, h1.w) [[fallthrough]];
+                case 8: DTW_CELL(8, h2.x) [[fallthrough]];
+                case 9: DTW_CELL(9, h2.y) [[fallthrough]];
+                case 10: DTW_CELL(10, h2.z) [[fallthrough]];
+                case 11: DTW_CELL(11, h2.w) [[fallthrough]];
+                case 12: DTW_CELL(12, h3.x) [[fallthrough]];
+                case 13: DTW_CELL(13, h3.y) [[fallthrough]];
+                case 14: DTW_CELL(14, h3.z) [[fallthrough]];
+                default: DTW_CELL(15, h3.w)
+            }
+            dtw_cells_from<16, C, P>(D, xi, yb);
+            if (j.abandon && (i & 7) == 7 && i + 1 < n) {
+                float mn = D[0];
+#pragma unroll
+                for (int k = 1; k < C; ++k) mn = fminf(mn, D[k]);
+                if (j.bsf) thr = load_threshold(j.bsf + q);
+                if (mn > thr) {
+                    abandoned = true;
+                    rows = i + 1;
+                    break;
+                }
+            }
+        }
+        n_rows += rows;
+        float d = kInf;
+#pragma unroll
+        for (int k = 0; k < C; ++k) d = sel_eq(k, wl, D[k], d);
+        if (abandoned) {
+            d = kInf;
+            ++n_aband;
+        }
+        if (!j.bsf && d > j.fixed_thr) d = kInf;
+        j.res[pi] = j.root_out ? root_p(d, P) : d;
+        if (!abandoned && j.bsf) update_threshold(j.bsf, j.gmin, j.k, q, c % j.k, d);
+        }  // valid
+    }
+    if (j.counters) {
+        // one atomic per warp and counter
+        n_skip = __reduce_add_sync(0xffffffffu, (unsigned)n_skip);
+        n_comp = __reduce_add_sync(0xffffffffu, (unsigned)n_comp);
+        n_aband = __reduce_add_sync(0xffffffffu, (unsigned)n_aband);
+        unsigned long long rows_w = 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) n_rows += __shfl_xor_sync(0xffffffffu, n_rows, o);
+        rows_w = n_rows;
+        if (lane == 0) {
+            if (rows_w) atomicAdd(j.counters + CNT_DTW_ROWS, rows_w);
+            if (n_skip) atomicAdd(j.counters + CNT_DTW_SKIP, n_skip);
+            if (n_comp) atomicAdd(j.counters + CNT_DTW_COMPUTED, n_comp);
+            if (n_aband) atomicAdd(j.counters + CNT_DTW_ABANDONED, n_aband);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Wide path (2w+1 > 208): one warp per pair, lane l owns the CL slots
+// l*CL .. l*CL+CL-1 of the band (slot k holds column i - w + k; slots above
+// 2w are outside the band).  A slot depends on the slot below it in the same
+// row and on the slot above it in the previous row, so lane l computes row i
+// at step t = 2i + l: the left neighbour finished row i and the right
+// neighbour finished row i-1 one step earlier, and their boundary values
+// arrive by shuffles.  The lane that holds slot 2w+1 resets it to +INF after
+// each row so that the band's top edge reads +INF.  Each lane keeps its
+// window of the query in registers and slides it by one column per row.
+// The row minimum is carried along the lanes with the boundary values; the
+// lane holding slot 2w sees the full minimum of its row.
+// ---------------------------------------------------------------------------
+template <int CL, int P>
+__global__ void __launch_bounds__(kDtwThreads)
+k_dtw_wide(DtwJob j) {
+    const int lane = threadIdx.x & 31;
+    const int n = j.n;
+    const int w = min(j.w, n - 1);
+    const int padl = j.qc.padl;
+    const int top = 2 * w;             // highest band slot
+    const int lane_top = top / CL;     // lane holding slot 2w
+    const int lane_dead = (top + 1) / CL, c_dead = (top + 1) % CL;  // slot 2w+1
+    const int lane_diag = w / CL, c_diag = w % CL;                  // slot of column i
+    if (j.npairs_dev) j.npairs = (int64_t)*j.npairs_dev;
+    unsigned long long n_skip = 0, n_comp = 0, n_aband = 0, n_rows = 0;
+    for (;;) {
+        unsigned long long pw = 0;
+        if (lane == 0) pw = atomicAdd(j.cursor, 1ull);
+        pw = __shfl_sync(0xffffffffu, pw, 0);
+        const int64_t pi = (int64_t)pw;
+        if (pi >= j.npairs) break;
+        int q, c;
+        bool valid;
+        fetch_pair(j, pi, q, c, valid);
+        float thr = kInf;
+        if (valid) {
+            thr = j.bsf ? load_threshold(j.bsf + q) : j.fixed_thr;
+            if (j.pair_lbi && j.pair_lbi[pi] > thr * (1.0f + j.slack)) {
+                if (lane == 0) {
+                    j.res[pi] = kInf;
+                    ++n_skip;
+                }
+                valid = false;
+            }
+        }
+        if (!valid) continue;  // uniform across the warp
+        if (lane == 0) ++n_comp;
+        const float *x = j.db + (int64_t)c * n;
+        const float *yp = j.qc.data + (int64_t)q * 4 * j.qc.ylen + padl;  // copy 0, column 0
+        float D[CL], yw[CL];
+        const int k0 = lane * CL;
+#pragma unroll
+        for (int t = 0; t < CL; ++t) {
+            D[t] = sel_eq(k0 + t, w, 0.0f, kInf);  // row -1: D(-1,-1) = 0
+            yw[t] = __ldg(yp + (0 - w + k0 + t));  // window of row 0
+        }
+        float ex_first = D[0], ex_last = D[CL - 1], ex_min = kInf;
+        bool abandoned = false;
+        const int steps = 2 * (n - 1) + 32;
+        for (int t = 0; t < steps; ++t) {
+            float left = __shfl_up_sync(0xffffffffu, ex_last, 1);
+            float up = __shfl_down_sync(0xffffffffu, ex_first, 1);
+            float lmin = __shfl_up_sync(0xffffffffu, ex_min, 1);
+            if (lane == 0) {
+                left = kInf;
+                lmin = kInf;
+            }
+            if (lane == 31) up = kInf;
+            const int dd = t - lane;
+            if (dd >= 0 && !(dd & 1) && (dd >> 1) < n && lane <= lane_dead) {
+                const int i = dd >> 1;
+                if (i > 0) {
+#pragma unroll
+                    for (int u = 0; u + 1 < CL; ++u) yw[u] = yw[u + 1];
+                    yw[CL - 1] = __ldg(yp + (i - w + k0 + CL - 1));
+                }
+                const float xi = __ldg(x + i);
+                float mn = kInf;
+#pragma unroll
+                for (int u = 0; u < CL; ++u) {
+                    const float above = (u + 1 < CL) ? D[(u + 1 < CL) ? u + 1 : u] : up;
+                    const float below = (u > 0) ? D[(u > 0) ? u - 1 : 0] : left;
+                    const float m = min3f(D[u], above, below);
+                    const float df = xi - yw[u];
+                    D[u] = (P == 1) ? fabsf(df) + m : fmaf(df, df, m);
+                    mn = fminf(mn, D[u]);
+                }
+                if (lane == lane_dead) {
+                    // slot 2w+1 lies outside the band
+#pragma unroll
+                    for (int u = 0; u < CL; ++u) D[u] = sel_eq(u, c_dead, kInf, D[u]);
+                }
+                ex_first = D[0];
+                ex_last = D[CL - 1];
+                ex_min = (lane <= lane_top) ? fminf(mn, lmin) : lmin;
+            }
+            if (j.abandon && (t & 7) == 7) {
+                const float rowmin = __shfl_sync(0xffffffffu, ex_min, lane_top);
+                if (j.bsf) thr = load_threshold(j.bsf + q);
+                thr = __shfl_sync(0xffffffffu, thr, 0);
+                if (rowmin > thr) {  // uniform: every lane sees lane_top's value
+                    abandoned = true;
+                    n_rows += (unsigned long long)max(0, min(n, (t - lane_top) / 2 + 1));
+                    break;
+                }
+            }
+        }
+        if (!abandoned) n_rows += (unsigned long long)n;
+        float dv = kInf;
+#pragma unroll
+        for (int u = 0; u < CL; ++u) dv = sel_eq(u, c_diag, D[u], dv);
+        dv = __shfl_sync(0xffffffffu, dv, lane_diag);
+        if (abandoned) dv = kInf;
+        if (lane == 0) {
+            if (abandoned) ++n_aband;
+            if (!j.bsf && dv > j.fixed_thr) dv = kInf;
+            j.res[pi] = j.root_out ? root_p(dv, P) : dv;
+            if (!abandoned && j.bsf) update_threshold(j.bsf, j.gmin, j.k, q, c % j.k, dv);
+        }
+    }
+    if (j.counters && lane == 0) {
+        if (n_rows) atomicAdd(j.counters + CNT_DTW_ROWS, n_rows);
+        if (n_skip) atomicAdd(j.counters + CNT_DTW_SKIP, n_skip);
+        if (n_comp) atomicAdd(j.counters + CNT_DTW_COMPUTED, n_comp);
+        if (n_aband) atomicAdd(j.counters + CNT_DTW_ABANDONED, n_aband);
+    }
+}
+
+}  // namespace dtwk

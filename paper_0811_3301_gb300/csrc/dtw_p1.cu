@@ -1,0 +1,54 @@
+// DTW kernel instantiations for p = 1 (band widths of the register and wide paths).
+#include "dtw_kernels.cuh"
+
+namespace dtwk {
+
+namespace {
+template <typename K>
+int blocks_for(K kernel, int64_t warps_needed) {
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kDtwThreads, 0);
+    if (per_sm < 1) per_sm = 1;
+    int64_t full = (int64_t)per_sm * device_sm_count();
+    int64_t need = (warps_needed + (kDtwThreads / 32) - 1) / (kDtwThreads / 32);
+    if (need < 1) need = 1;
+    return (int)(need < full ? need : full);
+}
+}  // namespace
+
+cudaError_t launch_dtw_p1(const DtwJob &j, const DtwGeom &g, cudaStream_t s) {
+    if (j.npairs <= 0) return cudaSuccess;
+    if (!g.wide) {
+        const int64_t warps = (j.npairs + 31) / 32;
+#define DTW_REG_CASE(CC)                                                              \
+    case CC: {                                                                        \
+        auto kern = k_dtw_reg<CC, 1>;                                                \
+        kern<<<blocks_for(kern, warps), kDtwThreads, 0, s>>>(j, g.e, g.wl);           \
+        break;                                                                        \
+    }
+        switch (g.C) {
+            DTW_REG_CASE(16) DTW_REG_CASE(32) DTW_REG_CASE(48) DTW_REG_CASE(64)
+            DTW_REG_CASE(80) DTW_REG_CASE(96) DTW_REG_CASE(112) DTW_REG_CASE(128)
+            DTW_REG_CASE(144) DTW_REG_CASE(160) DTW_REG_CASE(176) DTW_REG_CASE(192)
+            DTW_REG_CASE(208)
+            default: return cudaErrorInvalidValue;
+        }
+#undef DTW_REG_CASE
+    } else {
+        const int64_t warps = j.npairs;
+#define DTW_WIDE_CASE(CC)                                                             \
+    case CC: {                                                                        \
+        auto kern = k_dtw_wide<CC, 1>;                                               \
+        kern<<<blocks_for(kern, warps), kDtwThreads, 0, s>>>(j);                      \
+        break;                                                                        \
+    }
+        switch (g.cl) {
+            DTW_WIDE_CASE(8) DTW_WIDE_CASE(16) DTW_WIDE_CASE(32) DTW_WIDE_CASE(64)
+            default: return cudaErrorInvalidValue;
+        }
+#undef DTW_WIDE_CASE
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace dtwk

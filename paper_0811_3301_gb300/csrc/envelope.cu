@@ -1,0 +1,90 @@
+// Warping envelope (Sec. 5): U(y)_i = max_{|k-i|<=w} y_k, L(y)_i = min_{|k-i|<=w} y_k,
+// with k clipped to the series.  The paper's Algorithm 1 (Sec. 6) is a
+// sequential monotone-deque scan; on the GPU one CTA per series builds a
+// sparse table by doubling in shared memory instead:
+//   T_0 = y,  T_j[i] = max(T_{j-1}[i], T_{j-1}[min(i + 2^(j-1), n-1)]),
+// so T_j[i] is the maximum over [i, min(i + 2^j - 1, n-1)].  A clipped window
+// [a, b] of length len has floor(log2(len)) in {kmax-1, kmax}, with
+// kmax = floor(log2(min(2w+1, n))), and its maximum is
+// max(T_k[a], T_k[b - 2^k + 1]).  Min and max do not round, so the result is
+// bit-identical to the definition.
+//
+// The same kernel optionally writes the four shifted, +INF-padded copies of
+// each series that the DTW kernels read their band windows from.
+#include "common.cuh"
+
+namespace dtwk {
+
+constexpr int kEnvThreads = 256;
+
+__device__ __forceinline__ int floor_log2(int v) { return 31 - __clz(v); }
+
+__global__ void __launch_bounds__(kEnvThreads)
+k_envelope(const float *__restrict__ y, int n, int w, float *__restrict__ U, float *__restrict__ L,
+           float *__restrict__ copies, int padl, int ylen) {
+    extern __shared__ float sm[];
+    float *ax = sm;          // level j max
+    float *an = sm + n;      // level j min
+    float *bx = sm + 2 * n;  // level j-1 max (after the loop)
+    float *bn = sm + 3 * n;  // level j-1 min
+    const int64_t row = blockIdx.x;
+    const float *yr = y + row * (int64_t)n;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        float v = yr[i];
+        ax[i] = v;
+        an[i] = v;
+    }
+    if (copies != nullptr) {
+        float *cr = copies + row * 4 * (int64_t)ylen;
+        for (int t = threadIdx.x; t < 4 * ylen; t += blockDim.x) {
+            int r = t / ylen, tt = t - r * ylen;
+            int j = tt + r - padl;
+            cr[t] = (j >= 0 && j < n) ? yr[j] : kInf;
+        }
+    }
+    __syncthreads();
+    const int len_max = min(2 * w + 1, n);
+    const int kmax = floor_log2(len_max);
+    for (int j = 1; j <= kmax; ++j) {
+        const int h = 1 << (j - 1);
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            int i2 = min(i + h, n - 1);
+            bx[i] = fmaxf(ax[i], ax[i2]);
+            bn[i] = fminf(an[i], an[i2]);
+        }
+        __syncthreads();
+        float *t;
+        t = ax; ax = bx; bx = t;
+        t = an; an = bn; bn = t;
+    }
+    // now ax/an = T_kmax and bx/bn = T_(kmax-1) (unused when kmax == 0)
+    float *Ur = U + row * (int64_t)n;
+    float *Lr = L + row * (int64_t)n;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        int a = max(0, i - w), b = min(n - 1, i + w);
+        int k = floor_log2(b - a + 1);
+        const float *tx = (k == kmax) ? ax : bx;
+        const float *tn = (k == kmax) ? an : bn;
+        int b2 = b - (1 << k) + 1;
+        Ur[i] = fmaxf(tx[a], tx[b2]);
+        Lr[i] = fminf(tn[a], tn[b2]);
+    }
+}
+
+cudaError_t launch_envelope(const float *y, int64_t count, int n, int w, float *U, float *L,
+                            QueryCopies qc, int copies_padl, cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    w = min(w, n - 1);
+    size_t smem = 4 * (size_t)n * sizeof(float);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_envelope, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             4 * DTW_MAX_N * (int)sizeof(float));
+        attr_set = true;
+    }
+    k_envelope<<<(unsigned)count, kEnvThreads, smem, s>>>(y, n, w, U, L, qc.data, copies_padl,
+                                                          qc.ylen);
+    return cudaGetLastError();
+}
+
+}  // namespace dtwk

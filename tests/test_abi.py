@@ -1,0 +1,107 @@
+"""The C-ABI library builds, loads and exports every symbol the header
+declares; argument checks run on the host (no GPU needed)."""
+
+import ctypes
+import math
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "dtwknn.h")
+
+
+def _declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:dtw_status|const char\s*\*)\s*(\w+)\s*\(", text, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def native():
+    from paper_0811_3301_gb300 import build
+
+    build.build()
+    from paper_0811_3301_gb300 import _native
+
+    return _native
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for required in ("dtw_envelope", "lb_keogh", "lb_improved", "dtw_band", "knn_search", "knn_search_ex",
+                     "dtw_last_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(native):
+    lib = ctypes.CDLL(native.LIB_PATH)
+    missing = [name for name in _declared_functions() if not hasattr(lib, name)]
+    assert missing == []
+
+
+def test_binding_covers_every_declared_symbol(native):
+    bound = set(native.SIGNATURES) | {"dtw_last_error", "dtw_version"}
+    assert set(_declared_functions()) <= bound
+
+
+def test_library_is_built_for_sm103a(native):
+    # the objects were produced with -gencode arch=compute_103a,code=sm_103a
+    from paper_0811_3301_gb300 import build
+
+    assert "arch=compute_103a,code=sm_103a" in build.ARCH
+
+
+def _status(native, call):
+    st = call()
+    msg = native.lib.dtw_last_error().decode()
+    return st, msg
+
+
+@pytest.mark.parametrize(
+    "n,w,p,k,msg",
+    [
+        (0, 1, 1, 1, "n=0"),
+        (5000, 1, 1, 1, "n=5000"),
+        (16, -1, 1, 1, "w=-1"),
+        (16, 1, 3, 1, "p=3"),
+        (16, 1, 1, 0, "k=0"),
+        (16, 1, 1, 1000, "k=1000"),
+        (4000, 3000, 1, 1, "band"),
+    ],
+)
+def test_knn_search_rejects_bad_arguments_on_host(native, n, w, p, k, msg):
+    idx = (ctypes.c_int64 * 4)()
+    dist = (ctypes.c_float * 4)()
+    buf = (ctypes.c_float * 16)()
+    st, text = _status(native, lambda: native.lib.knn_search(buf, 1, buf, 1, n, w, p, k, idx, dist, None, None))
+    assert st == 1, text  # DTW_ERR_INVALID_ARG
+    assert msg.split("=")[0] in text
+
+
+def test_single_op_calls_validate_on_host(native):
+    buf = (ctypes.c_float * 16)()
+    assert native.lib.dtw_envelope(buf, 1, 0, 1, buf, buf, None) == 1
+    assert native.lib.lb_keogh(buf, 1, buf, buf, 16, 5, buf, None) == 1
+    assert native.lib.lb_improved(buf, -1, buf, buf, buf, 16, 1, 1, buf, None) == 1
+    assert native.lib.dtw_band(buf, buf, 1, 7, 16, 1, 1, math.inf, buf, None) == 1  # bad y_stride
+    assert native.lib.dtw_band(buf, buf, 1, 0, 16, 1, 1, float("nan"), buf, None) == 1
+    # empty inputs are a no-op success
+    assert native.lib.dtw_envelope(buf, 0, 16, 1, buf, buf, None) == 0
+    assert native.lib.lb_keogh(buf, 0, buf, buf, 16, 1, buf, None) == 0
+
+
+def test_bad_mode_and_slack_rejected(native):
+    buf = (ctypes.c_float * 16)()
+    idx = (ctypes.c_int64 * 4)()
+    for opt in (native.Options(7, 1e-6, 0), native.Options(0, -1.0, 0), native.Options(0, 1e-6, -3)):
+        st = native.lib.knn_search_ex(buf, 1, buf, 1, 16, 1, 1, 1, ctypes.byref(opt), idx, buf, None, None)
+        assert st == 1
+
+
+def test_profile_api_without_gpu(native):
+    native.profile_enable(True)
+    native.profile_enable(False)
+    prof = native.profile_read(reset=True)
+    assert set(prof) == set(native.STAGE_NAMES)

@@ -1,0 +1,265 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances: envelopes are compared bit for bit (min/max do not round).
+Bounds and DTW distances are fp32 sums of up to 2n terms; they must match
+the oracle within REL = 1e-5 relative (plus a tiny absolute floor for values
+near zero).  Neighbour indices must equal the oracle's exactly, except where
+the oracle's own distances of the two candidates differ by less than REL
+(a near-tie that fp32 cannot order); there the GPU's choice must still be a
+candidate whose oracle distance equals the reported one within REL.
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+REL = 1e-5
+ABS = 1e-5
+
+
+@pytest.fixture(scope="module")
+def api():
+    from paper_0811_3301_gb300 import build
+
+    build.build()
+    from paper_0811_3301_gb300 import api as a
+
+    return a
+
+
+def cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def close(gpu, ref, rel=REL, abs_=ABS):
+    gpu = np.asarray(gpu, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    both_inf = np.isinf(gpu) & np.isinf(ref)
+    ok = both_inf | (np.abs(gpu - ref) <= rel * np.abs(ref) + abs_)
+    return ok
+
+
+def assert_knn(db, queries, w, p, k, gidx, gdist, ref_idx, ref_dist):
+    gidx = gidx.cpu().numpy()
+    gdist = gdist.cpu().numpy().astype(np.float64)
+    Q = queries.shape[0]
+    for q in range(Q):
+        for r in range(k):
+            oi, od = int(ref_idx[q, r]), float(ref_dist[q, r])
+            gi, gd = int(gidx[q, r]), float(gdist[q, r])
+            if oi < 0:
+                assert gi == -1 and math.isinf(gd), (q, r, gi, gd)
+                continue
+            assert close(gd, od), (q, r, gd, od)
+            if gi != oi:
+                # accepted only as a near-tie: the oracle's distance of the GPU's
+                # candidate equals the rank-r distance within REL
+                d_gi = oracle.dtw(db[gi], queries[q], w, p)
+                assert abs(d_gi - od) <= REL * od + ABS, (q, r, gi, oi, d_gi, od)
+
+
+# ---------------------------------------------------------------------------
+# envelope
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [1, 2, 7, 64, 129, 256, 1000, 2048, 4096])
+def test_envelope_bit_exact(api, n):
+    rng = np.random.default_rng(n)
+    Y = np.concatenate([synth.random_walks(3, n, seed=n),
+                        rng.integers(-2, 3, size=(2, n)).astype(np.float32)])  # ties
+    for w in sorted({0, 1, 3, n // 10, n // 2, n - 1, n, n + 5}):
+        U, L = api.dtw_envelope(cuda(Y), w)
+        U, L = U.cpu().numpy(), L.cpu().numpy()
+        for r in range(Y.shape[0]):
+            Ur, Lr = oracle.envelope(Y[r], w)
+            assert np.array_equal(U[r].astype(np.float64), Ur), (n, w, r)
+            assert np.array_equal(L[r].astype(np.float64), Lr), (n, w, r)
+
+
+# ---------------------------------------------------------------------------
+# LB_Keogh and LB_Improved
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("p", [1, 2])
+@pytest.mark.parametrize("n,w", [(1, 0), (5, 1), (128, 12), (131, 13), (256, 25), (1024, 102), (2048, 204)])
+def test_lb_keogh_and_improved(api, p, n, w):
+    N = 300
+    X = synth.random_walks(N, n, seed=7 + n)
+    y = synth.random_walks(1, n, seed=8 + n, stream=synth.STREAM_QUERY)[0]
+    U, L = api.dtw_envelope(cuda(y), w)
+    lbk = api.lb_keogh(cuda(X), U, L, p).cpu().numpy()
+    lbi = api.lb_improved(cuda(X), cuda(y), U, L, w, p).cpu().numpy()
+    for c in range(N):
+        ri, rk = oracle.lb_improved_pow(X[c], y, w, p, with_first=True)
+        assert close(lbk[c], rk ** (1.0 / p)), (c, lbk[c], rk)
+        assert close(lbi[c], ri ** (1.0 / p)), (c, lbi[c], ri)
+
+
+# ---------------------------------------------------------------------------
+# DTW
+# ---------------------------------------------------------------------------
+
+DTW_CASES = [(1, 0), (2, 1), (8, 3), (33, 0), (64, 6), (128, 12), (181, 18), (256, 25), (257, 51),
+             (512, 51), (1024, 102), (400, 103), (300, 104), (1024, 150), (1024, 204), (600, 599)]
+
+
+@pytest.mark.parametrize("p", [1, 2])
+@pytest.mark.parametrize("n,w", DTW_CASES)
+def test_dtw_band_shared_query(api, p, n, w):
+    N = 70  # two full warps and a ragged tail
+    X = synth.random_walks(N, n, seed=100 + n)
+    y = synth.random_walks(1, n, seed=200 + n, stream=synth.STREAM_QUERY)[0]
+    d = api.dtw_band(cuda(X), cuda(y), w, p).cpu().numpy()
+    for c in range(N):
+        ref = oracle.dtw(X[c], y, w, p)
+        assert close(d[c], ref), (n, w, c, d[c], ref)
+
+
+@pytest.mark.parametrize("p", [1, 2])
+@pytest.mark.parametrize("n,w", [(16, 2), (256, 25), (1024, 204)])
+def test_dtw_band_per_pair_query(api, p, n, w):
+    N = 40
+    X = synth.random_walks(N, n, seed=300 + n)
+    Y = synth.random_walks(N, n, seed=301 + n, stream=synth.STREAM_QUERY)
+    d = api.dtw_band(cuda(X), cuda(Y), w, p).cpu().numpy()
+    for c in range(N):
+        assert close(d[c], oracle.dtw(X[c], Y[c], w, p)), (c,)
+
+
+@pytest.mark.parametrize("p", [1, 2])
+@pytest.mark.parametrize("n,w", [(128, 12), (1024, 204)])
+def test_dtw_band_threshold(api, p, n, w):
+    N = 64
+    X = synth.random_walks(N, n, seed=400 + n)
+    y = synth.random_walks(1, n, seed=401 + n, stream=synth.STREAM_QUERY)[0]
+    ref = np.array([oracle.dtw(X[c], y, w, p) for c in range(N)])
+    thr = float(np.median(ref))
+    d = api.dtw_band(cuda(X), cuda(y), w, p, threshold=thr).cpu().numpy()
+    for c in range(N):
+        if ref[c] > thr * (1 + 1e-4):
+            assert math.isinf(d[c]), (c, d[c], ref[c], thr)
+        elif ref[c] < thr * (1 - 1e-4):
+            assert close(d[c], ref[c]), (c, d[c], ref[c])
+
+
+def test_dtw_worked_examples(api):
+    # Sec. 4 and App. A examples through the GPU path
+    cases = [([0, 0, 1, 0], [2, 3, 2, 2], 1, 2, 17.0 ** 0.5), ([0, 0, 1, 0], [2, 3, 2, 2], 0, 2, 18.0 ** 0.5),
+             ([0, 1, 2], [1, 2, 3], 1, 1, 2.0), ([0, 1, 2], [1, 2, 3], 0, 1, 3.0)]
+    for x, y, w, p, v in cases:
+        d = api.dtw_band(cuda(np.array([x])), cuda(np.array(y)), w, p).cpu().numpy()
+        assert close(d[0], v)
+
+
+# ---------------------------------------------------------------------------
+# k nearest neighbours
+# ---------------------------------------------------------------------------
+
+def _knn_case(api, db, queries, w, p, k, mode="improved", **kw):
+    idx, dist, st = api.knn_search(cuda(db), cuda(queries), w, p, k, mode=mode, return_stats=True, **kw)
+    ri, rd, _ = oracle.knn_cascade(db, queries, w, p, k, mode=1, threads=8)
+    assert_knn(db, queries, w, p, k, idx, dist, ri, rd)
+    Q, N = queries.shape[0], db.shape[0]
+    assert st["candidates"] == Q * N
+    assert st["seeds"] + st["pruned_keogh"] + st["pruned_improved"] + st["dtw_computed"] == Q * N
+    return idx, dist, st
+
+
+@pytest.mark.parametrize("p", [1, 2])
+@pytest.mark.parametrize("k", [1, 3, 10])
+def test_knn_plain_cascade_small(api, p, k):
+    # 1,000 random walks of length 128, band 12, 10 queries (the small plain case)
+    db = synth.random_walks(1000, 128, seed=1)
+    qs = synth.random_walks(10, 128, seed=1, stream=synth.STREAM_QUERY)
+    _knn_case(api, db, qs, 12, p, k)
+
+
+@pytest.mark.parametrize("mode", ["improved", "keogh", "noprune"])
+def test_knn_modes_agree(api, mode):
+    db = synth.random_walks(700, 96, seed=2)
+    qs = synth.random_walks(9, 96, seed=2, stream=synth.STREAM_QUERY)
+    _knn_case(api, db, qs, 9, 1, 4, mode=mode)
+
+
+def test_knn_pruning_never_loses_the_neighbour(api):
+    db = synth.random_walks(3000, 64, seed=3)
+    qs = synth.random_walks(20, 64, seed=3, stream=synth.STREAM_QUERY)
+    a = api.knn_search(cuda(db), cuda(qs), 6, 2, 5)
+    b = api.knn_search(cuda(db), cuda(qs), 6, 2, 5, mode="noprune")
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+    # an extreme slack prunes almost nothing and must give the same answer
+    c = api.knn_search(cuda(db), cuda(qs), 6, 2, 5, slack=10.0)
+    assert torch.equal(a[0], c[0]) and torch.equal(a[1], c[1])
+
+
+@pytest.mark.parametrize("seeds", [1, 2, 32])
+def test_knn_seed_count(api, seeds):
+    db = synth.random_walks(900, 64, seed=4)
+    qs = synth.random_walks(7, 64, seed=4, stream=synth.STREAM_QUERY)
+    _knn_case(api, db, qs, 6, 1, 3, seeds=seeds)
+
+
+def test_knn_edge_cases(api):
+    # k > N pads with -1 / +inf; N = 1; n = 1; odd n (scalar load path); w = 0; w >= n
+    db = synth.random_walks(5, 33, seed=5)
+    qs = synth.random_walks(3, 33, seed=5, stream=synth.STREAM_QUERY)
+    for w in (0, 4, 32, 100):
+        for k in (1, 5, 8):
+            _knn_case(api, db, qs, w, 1, k)
+    _knn_case(api, db[:1], qs, 3, 2, 2)
+    one = np.arange(12, dtype=np.float32).reshape(12, 1)
+    _knn_case(api, one, one[[3, 7]] + 0.25, 0, 1, 3)
+
+
+def test_knn_ties_go_to_lower_index(api):
+    db = synth.random_walks(300, 40, seed=6)
+    db[250] = db[17]
+    db[260] = db[17]
+    db[120] = db[200]
+    qs = db[[17, 200]].copy()
+    idx, dist = api.knn_search(cuda(db), cuda(qs), 4, 1, 3)
+    idx = idx.cpu().numpy()
+    assert list(idx[0]) == [17, 250, 260]
+    assert list(idx[1][:2]) == [120, 200]
+    assert float(dist[0, 0]) == 0.0
+
+
+def test_knn_host_buffers(api):
+    db = synth.random_walks(800, 64, seed=8)
+    qs = synth.random_walks(6, 64, seed=8, stream=synth.STREAM_QUERY)
+    dev = api.knn_search(cuda(db), cuda(qs), 6, 1, 2)
+    host_q = torch.from_numpy(qs).pin_memory()
+    host = api.knn_search(cuda(db), host_q, 6, 1, 2)
+    assert not host[0].is_cuda
+    assert torch.equal(dev[0].cpu(), host[0]) and torch.equal(dev[1].cpu(), host[1])
+    allhost = api.knn_search(torch.from_numpy(db), torch.from_numpy(qs), 6, 1, 2)
+    assert torch.equal(dev[0].cpu(), allhost[0])
+
+
+def test_knn_shapes_long_series_wide_band(api):
+    # shape-like series of length 1024 with w = 5 %, 10 %, 20 % (register and wide DTW paths)
+    db = synth.shapes(1500, 1024, seed=9)
+    qs = synth.shapes(3, 1024, seed=9, stream=synth.STREAM_QUERY)
+    for w in (51, 102, 204):
+        _knn_case(api, db, qs, w, 1, 1)
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_knn_full_size_sampled(api, p):
+    # 100,000 random walks of length 256, band 25, 1,000 queries, in the
+    # launch configuration the benchmark times; a sample of queries is
+    # checked against the oracle.
+    db = synth.random_walks(100_000, 256, seed=2)
+    qs = synth.random_walks(1000, 256, seed=2, stream=synth.STREAM_QUERY)
+    idx, dist = api.knn_search(cuda(db), cuda(qs), 25, p, 1)
+    sample = np.array([0, 1, 2, 3, 500, 997, 998, 999])
+    ri, rd, _ = oracle.knn_cascade(db, qs[sample], 25, p, 1, mode=1, threads=16)
+    assert_knn(db, qs[sample], 25, p, 1, idx[sample], dist[sample], ri, rd)
