@@ -335,7 +335,7 @@ dtw_status knn_search_ex(const float *db, int64_t N, const float *queries, int64
             Pair *seed_pairs, *pairs;
             uint32_t *gmin, *bsf;
             int32_t *seg_start, *seg_count;
-            unsigned long long *misc;
+            unsigned long long *misc, *tile_min;
             int64_t *out_idx;
         } l;
         l.db = db_dev ? nullptr : cv.take<float>((size_t)N * n);
@@ -344,6 +344,7 @@ dtw_status knn_search_ex(const float *db, int64_t N, const float *queries, int64
         l.L = cv.take<float>((size_t)Qc * n);
         l.copies = cv.take<float>((size_t)Qc * 4 * g.ylen);
         l.lb = cv.take<float>((size_t)Qc * Nc);
+        l.tile_min = cv.take<unsigned long long>((size_t)Qc * lbk_tiles((int)Nc));
         l.seed_pairs = cv.take<Pair>((size_t)Qc * S);
         l.seed_res = cv.take<float>((size_t)Qc * S);
         l.gmin = cv.take<uint32_t>((size_t)Qc * k);
@@ -415,6 +416,8 @@ dtw_status knn_search_ex(const float *db, int64_t N, const float *queries, int64
         b.mode = o.mode;
         b.slack = slack;
         b.lb = l.lb;
+        b.tile_min = l.tile_min;
+        b.ntiles = lbk_tiles((int)Nc);
         b.S = N > 0 ? S : 0;
         b.seed_pairs = l.seed_pairs;
         b.seed_res = l.seed_res;
@@ -437,7 +440,7 @@ dtw_status knn_search_ex(const float *db, int64_t N, const float *queries, int64
         if (N > 0) {
             {
                 StageTimer tm(DTW_STAGE_LB_KEOGH, s);
-                CUDA_TRY(launch_lbk_tile(dbd, (int)N, l.U, l.L, qn, n, p, l.lb, s));
+                CUDA_TRY(launch_lbk_tile(dbd, (int)N, l.U, l.L, qn, n, p, l.lb, l.tile_min, s));
             }
             {
                 StageTimer tm(DTW_STAGE_SEED_SELECT, s);

@@ -15,12 +15,14 @@ __device__ __forceinline__ unsigned long long pack_key(float d, int c) {
 }
 
 // ---------------------------------------------------------------------------
-// Seeds: per query, the S candidates of smallest LB_Keogh (ties to the lower
-// index).  Their exact DTW is computed first so that the threshold is close
-// to its final value before the bulk of the candidates is filtered; this is
-// the GPU counterpart of visiting candidates in order of their lower bound.
-// One CTA per query; each thread keeps a sorted list of its kSeedMax best
-// keys, then S rounds of a block-wide minimum pop the global best.
+// Seeds: per query, the S smallest of the per-tile LB_Keogh minima (each the
+// smallest (bound, index) among 128 consecutive candidates), or for small
+// databases (N <= 8192) the S smallest bounds overall.  Their exact DTW
+// is computed first so that the threshold is close to its final value before
+// the bulk of the candidates is filtered; this is the GPU counterpart of
+// visiting candidates in order of their lower bound.  One CTA per query;
+// each thread keeps a sorted list of its kSeedMax best keys, then S rounds of
+// a block-wide minimum pop the global best.
 // Also resets the query's thresholds to +INF.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_seed_select(CascadeBufs b) {
@@ -31,9 +33,13 @@ __global__ void __launch_bounds__(256) k_seed_select(CascadeBufs b) {
     unsigned long long key[kSeedMax];
 #pragma unroll
     for (int s = 0; s < kSeedMax; ++s) key[s] = ~0ull;
-    const float *row = b.lb + (int64_t)q * b.N;
-    for (int c = t; c < b.N; c += blockDim.x) {
-        unsigned long long v = pack_key(row[c], c);
+    // small databases: scan every bound (the tiles may be fewer than S)
+    const bool full = b.N <= 8192;
+    const int cnt = full ? b.N : b.ntiles;
+    const float *lbrow = b.lb + (int64_t)q * b.N;
+    const unsigned long long *row = b.tile_min + (int64_t)q * b.ntiles;
+    for (int c = t; c < cnt; c += blockDim.x) {
+        unsigned long long v = full ? pack_key(lbrow[c], c) : row[c];
         if (v < key[kSeedMax - 1]) {
             // insertion into the sorted list
 #pragma unroll

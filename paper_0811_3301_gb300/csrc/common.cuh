@@ -93,7 +93,8 @@ cudaError_t launch_envelope(const float *y, int64_t count, int n, int w, float *
 cudaError_t launch_lbk_single(const float *cand, int64_t N, const float *U, const float *L, int n,
                               int p, float *out, cudaStream_t s);
 cudaError_t launch_lbk_tile(const float *db, int N, const float *U, const float *L, int Q, int n,
-                            int p, float *lb, cudaStream_t s);
+                            int p, float *lb, unsigned long long *tile_min, cudaStream_t s);
+int lbk_tiles(int N);  // candidate tiles of the all-pairs kernel
 
 // One (query, candidate) pair for the LB_Improved and DTW stages.
 struct Pair {
@@ -112,8 +113,10 @@ struct CascadeBufs {
     QueryCopies qc;
     int N, Q, n, w, p, k, mode;
     float slack;
-    // LB_Keogh matrix, [Q][N], power space
+    // LB_Keogh matrix, [Q][N], power space, and per (query, tile) minimum keys
     float *lb;
+    unsigned long long *tile_min;  // [Q][ntiles]
+    int ntiles;
     // seeds: [Q][S]
     int S;
     Pair *seed_pairs;

@@ -279,7 +279,9 @@ k_dtw_wide(DtwJob j) {
                 ex_last = D[CL - 1];
                 ex_min = (lane <= lane_top) ? fminf(mn, lmin) : lmin;
             }
-            if (j.abandon && (t & 7) == 7) {
+            if (j.abandon && (t & 7) == 7 && t >= lane_top) {
+                // lane_top has completed at least row 0, so its running
+                // minimum covers a whole row
                 const float rowmin = __shfl_sync(0xffffffffu, ex_min, lane_top);
                 if (j.bsf) thr = load_threshold(j.bsf + q);
                 thr = __shfl_sync(0xffffffffu, thr, 0);

@@ -74,7 +74,8 @@ cudaError_t launch_lbk_single(const float *cand, int64_t N, const float *U, cons
 // warp-wide broadcasts.  Out-of-range elements and candidates are
 // zero-filled: x = U = L = 0 contributes nothing.  Each thread keeps 16
 // accumulators (4 queries x 4 candidates), summed per chunk and then added to
-// the running total.
+// the running total.  Each CTA also writes, per query, the smallest
+// (bound, index) key over its 128 candidates, from which the seeds are drawn.
 // ---------------------------------------------------------------------------
 constexpr int TQ = 32, TC = 128, KC = 32, XS = KC + 4;  // XS: padded row stride
 
@@ -145,7 +146,8 @@ __device__ __forceinline__ void tile_load(TileSmem &sm, int buf, const float *db
 template <int P, bool VEC>
 __global__ void __launch_bounds__(256)
 k_lbk_tile(const float *__restrict__ db, int N, const float *__restrict__ U,
-           const float *__restrict__ L, int Q, int n, float *__restrict__ lb) {
+           const float *__restrict__ L, int Q, int n, float *__restrict__ lb,
+           unsigned long long *__restrict__ tile_min) {
     extern __shared__ __align__(16) unsigned char smraw[];
     TileSmem &sm = *reinterpret_cast<TileSmem *>(smraw);
     const int c0 = blockIdx.x * TC;
@@ -208,18 +210,31 @@ k_lbk_tile(const float *__restrict__ db, int N, const float *__restrict__ U,
     }
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
-        int q = q0 + wq + a;
-        if (q >= Q) continue;
+        const int q = q0 + wq + a;
+        unsigned long long key = ~0ull;
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
-            int c = c0 + lane + 32 * b;
-            if (c < N) lb[(int64_t)q * N + c] = tot[a][b];
+            const int c = c0 + lane + 32 * b;
+            if (c < N && q < Q) {
+                lb[(int64_t)q * N + c] = tot[a][b];
+                const unsigned long long v = ((unsigned long long)__float_as_uint(tot[a][b]) << 32) | (unsigned)c;
+                key = v < key ? v : key;
+            }
         }
+        // smallest (bound, index) of this query over the tile's 128 candidates
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long other = __shfl_xor_sync(0xffffffffu, key, o);
+            key = other < key ? other : key;
+        }
+        if (lane == 0 && q < Q && tile_min) tile_min[(int64_t)q * gridDim.x + blockIdx.x] = key;
     }
 }
 
+int lbk_tiles(int N) { return (N + TC - 1) / TC; }
+
 cudaError_t launch_lbk_tile(const float *db, int N, const float *U, const float *L, int Q, int n,
-                            int p, float *lb, cudaStream_t s) {
+                            int p, float *lb, unsigned long long *tile_min, cudaStream_t s) {
     if (N <= 0 || Q <= 0) return cudaSuccess;
     bool vec = (n % 4 == 0) && ((reinterpret_cast<uintptr_t>(db) & 15) == 0) &&
                ((reinterpret_cast<uintptr_t>(U) & 15) == 0) &&
@@ -230,11 +245,11 @@ cudaError_t launch_lbk_tile(const float *db, int N, const float *U, const float 
         cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     };
     if (p == 1) {
-        if (vec) { set((const void *)k_lbk_tile<1, true>); k_lbk_tile<1, true><<<grid, 256, smem, s>>>(db, N, U, L, Q, n, lb); }
-        else { set((const void *)k_lbk_tile<1, false>); k_lbk_tile<1, false><<<grid, 256, smem, s>>>(db, N, U, L, Q, n, lb); }
+        if (vec) { set((const void *)k_lbk_tile<1, true>); k_lbk_tile<1, true><<<grid, 256, smem, s>>>(db, N, U, L, Q, n, lb, tile_min); }
+        else { set((const void *)k_lbk_tile<1, false>); k_lbk_tile<1, false><<<grid, 256, smem, s>>>(db, N, U, L, Q, n, lb, tile_min); }
     } else {
-        if (vec) { set((const void *)k_lbk_tile<2, true>); k_lbk_tile<2, true><<<grid, 256, smem, s>>>(db, N, U, L, Q, n, lb); }
-        else { set((const void *)k_lbk_tile<2, false>); k_lbk_tile<2, false><<<grid, 256, smem, s>>>(db, N, U, L, Q, n, lb); }
+        if (vec) { set((const void *)k_lbk_tile<2, true>); k_lbk_tile<2, true><<<grid, 256, smem, s>>>(db, N, U, L, Q, n, lb, tile_min); }
+        else { set((const void *)k_lbk_tile<2, false>); k_lbk_tile<2, false><<<grid, 256, smem, s>>>(db, N, U, L, Q, n, lb, tile_min); }
     }
     return cudaGetLastError();
 }
