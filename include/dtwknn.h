@@ -170,6 +170,24 @@ typedef struct {
 dtw_status dtw_profile_enable(int32_t on);
 dtw_status dtw_profile_read(dtw_profile *out, int32_t reset);
 
+/*
+ * dtw_band_noalloc: dtw_band (same arguments, same results) for callers that
+ * cannot call cudaMalloc or cudaFree, such as a service whose device memory is
+ * owned by another allocator or a loop that must not stall on cudaFree's
+ * device-wide synchronisation.  The paper has no counterpart: this is a
+ * deployment variant.  Its scratch is a fixed 8 MiB array of device memory
+ * that belongs to the library and is held on every GPU that loads it until
+ * the process exits; it never allocates.  A call whose scratch (the padded
+ * query copies: 16 * (n + w + 2*C + 1) bytes per query row, with C the band
+ * slot count, plus 256 bytes) does not fit returns DTW_ERR_INVALID_ARG.  All
+ * calls share the array, so calls that overlap on the GPU race.  The first
+ * call on a device looks up the array's device address; make it before any
+ * stream capture.
+ */
+dtw_status dtw_band_noalloc(const float *x, const float *y, int64_t N, int32_t y_stride,
+                            int32_t n, int32_t w, int32_t p, float threshold, float *out,
+                            void *stream);
+
 /* Message of the last failed call on this host thread ("" if none). */
 const char *dtw_last_error(void);
 

@@ -26,6 +26,10 @@ static dtw_status fail(dtw_status st, const char *fmt, ...) {
     return st;
 }
 
+// Sets this thread's last-error message (used by entry points defined in
+// other translation units).
+void set_error_message(const char *msg) { snprintf(g_err, sizeof(g_err), "%s", msg ? msg : ""); }
+
 #define CUDA_TRY(expr)                                                                    \
     do {                                                                                  \
         cudaError_t e_ = (expr);                                                          \
