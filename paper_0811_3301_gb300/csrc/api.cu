@@ -329,14 +329,17 @@ dtw_status knn_search_ex(const float *db, int64_t N, const float *queries, int64
     if (Qc < 1) Qc = 1;
     if (Qc > 32768) Qc = 32768;  // grid.y limit of the per-query kernels
     if (Qc > Q) Qc = Q;
-    const int seg_len = 2048;
-    const int nseg = N > 0 ? (int)((N + seg_len - 1) / seg_len) : 1;
+    const int seg_len = 1024;
+    const int filter_warps = lbi_filter_warps(n, we, S, seg_len);
+    // sub-segments per query: candidate segments x filter warps
+    const int nseg = N > 0 ? (int)((N + seg_len - 1) / seg_len) * filter_warps : 1;
     const int64_t Nc = N > 0 ? N : 1;
 
     auto layout = [&](Carve &cv) {
         struct L {
-            float *db, *q, *U, *L, *copies, *lb, *seed_res, *pair_lbi, *pair_res, *out_dist;
-            Pair *seed_pairs, *pairs;
+            float *db, *q, *U, *L, *copies, *lb, *seed_res, *pair_lbi, *pair_res, *out_dist, *lbi_u;
+            Pair *seed_pairs, *pairs, *pairs_u;
+            int32_t *qcount, *qstart;
             uint32_t *gmin, *bsf;
             int32_t *seg_start, *seg_count;
             unsigned long long *misc, *tile_min;
@@ -353,6 +356,11 @@ dtw_status knn_search_ex(const float *db, int64_t N, const float *queries, int64
         l.seed_res = cv.take<float>((size_t)Qc * S);
         l.gmin = cv.take<uint32_t>((size_t)Qc * k);
         l.bsf = cv.take<uint32_t>((size_t)Qc);
+        l.pairs_u = cv.take<Pair>((size_t)Qc * Nc);
+        l.lbi_u = cv.take<float>((size_t)Qc * Nc);
+        l.qcount = cv.take<int32_t>((size_t)Qc);
+        l.qstart = cv.take<int32_t>((size_t)Qc);
+
         l.pairs = cv.take<Pair>((size_t)Qc * Nc);
         l.pair_lbi = cv.take<float>((size_t)Qc * Nc);
         l.pair_res = cv.take<float>((size_t)Qc * Nc);
@@ -427,6 +435,12 @@ dtw_status knn_search_ex(const float *db, int64_t N, const float *queries, int64
         b.seed_res = l.seed_res;
         b.gmin = l.gmin;
         b.bsf = l.bsf;
+        b.pairs_u = l.pairs_u;
+        b.lbi_u = l.lbi_u;
+        b.qcount = l.qcount;
+        b.qstart = l.qstart;
+        b.pair_total = l.misc + 4;
+        b.lbi_inline = o.mode == DTW_MODE_IMPROVED ? 1 : 0;
         b.pairs = l.pairs;
         b.pair_lbi = l.pair_lbi;
         b.pair_res = l.pair_res;
@@ -476,12 +490,14 @@ dtw_status knn_search_ex(const float *db, int64_t N, const float *queries, int64
             }
             {
                 StageTimer tm(DTW_STAGE_LB_IMPROVED, s);
+                CUDA_TRY(cudaMemsetAsync(l.qcount, 0, (size_t)qn * sizeof(int32_t), s));
                 CUDA_TRY(launch_lbi_filter(b, s));
+                CUDA_TRY(launch_group_by_query(b, s));
             }
             DtwJob jp = js;
             jp.pairs = l.pairs;
             jp.npairs = (int64_t)qn * Nc;
-            jp.npairs_dev = pair_count;
+            jp.npairs_dev = b.pair_total;
             jp.pair_lbi = o.mode == DTW_MODE_NOPRUNE ? nullptr : l.pair_lbi;
             jp.abandon = o.mode == DTW_MODE_NOPRUNE ? 0 : 1;
             jp.res = l.pair_res;

@@ -137,9 +137,9 @@ __global__ void __launch_bounds__(256) k_finalize(CascadeBufs b) {
                 if ((first || v > last) && v < m) m = v;
             }
         }
-        for (int sg = 0; sg < b.nseg; ++sg) {
-            const int cnt = b.seg_count[(int64_t)q * b.nseg + sg];
-            const int64_t base = b.seg_start[(int64_t)q * b.nseg + sg];
+        if (b.nseg > 0) {
+            const int cnt = b.qcount[q];
+            const int64_t base = b.qstart[q];
             for (int e = t; e < cnt; e += blockDim.x) {
                 float d = b.pair_res[base + e];
                 if (d < kInf && d <= bq) {
@@ -186,6 +186,92 @@ __global__ void __launch_bounds__(256) k_finalize(CascadeBufs b) {
 cudaError_t launch_finalize(const CascadeBufs &b, cudaStream_t s) {
     if (b.Q <= 0) return cudaSuccess;
     k_finalize<<<b.Q, 256, 0, s>>>(b);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Group the filter's survivors by query (a counting sort): an exclusive scan
+// of the per-query counts gives each query a contiguous range, and one CTA
+// per query copies its sub-segments into it in order.  The DTW stage then
+// sees runs of pairs that share a query (warp-uniform band-window loads).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_qscan(const int32_t *__restrict__ cnt, int32_t *__restrict__ start, int Q,
+                                                unsigned long long *total) {
+    __shared__ int32_t wsum[32];
+    __shared__ int32_t carry;
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    if (t == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < Q; base += blockDim.x) {
+        const int i = base + t;
+        const int v = i < Q ? cnt[i] : 0;
+        int x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[wid] = x;
+        __syncthreads();
+        if (wid == 0) {
+            int s = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, s, o);
+                if (lane >= o) s += y;
+            }
+            wsum[lane] = s;  // inclusive over warps
+        }
+        __syncthreads();
+        const int before = (wid > 0 ? wsum[wid - 1] : 0) + carry;
+        if (i < Q) start[i] = before + x - v;
+        __syncthreads();
+        if (t == blockDim.x - 1) carry = before + x;
+        __syncthreads();
+    }
+    if (t == 0 && total) *total = (unsigned long long)carry;
+}
+
+__global__ void __launch_bounds__(256) k_gather(CascadeBufs b) {
+    const int q = blockIdx.x;
+    const int t = threadIdx.x;
+    __shared__ int32_t offs[256];
+    __shared__ int32_t carry;
+    if (t == 0) carry = 0;
+    __syncthreads();
+    const int64_t out0 = b.qstart[q];
+    for (int s0 = 0; s0 < b.nseg; s0 += blockDim.x) {
+        const int sg = s0 + t;
+        const int c = sg < b.nseg ? b.seg_count[(int64_t)q * b.nseg + sg] : 0;
+        // block exclusive scan of the sub-segment counts (simple, nseg is small)
+        offs[t] = c;
+        __syncthreads();
+        for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+            const int v = t >= o ? offs[t - o] : 0;
+            __syncthreads();
+            offs[t] += v;
+            __syncthreads();
+        }
+        const int excl = offs[t] - c + carry;
+        __syncthreads();
+        if (t == blockDim.x - 1) carry += offs[t];
+        // copy this sub-segment (one thread per sub-segment; they are short)
+        if (sg < b.nseg && c > 0) {
+            const int64_t src = b.seg_start[(int64_t)q * b.nseg + sg];
+            for (int e = 0; e < c; ++e) {
+                b.pairs[out0 + excl + e] = b.pairs_u[src + e];
+                b.pair_lbi[out0 + excl + e] = b.lbi_u[src + e];
+                b.pair_res[out0 + excl + e] = kInf;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_group_by_query(const CascadeBufs &b, cudaStream_t s) {
+    if (b.Q <= 0 || b.nseg <= 0) return cudaSuccess;
+    k_qscan<<<1, 1024, 0, s>>>(b.qcount, b.qstart, b.Q, b.pair_total);
+    k_gather<<<b.Q, 256, 0, s>>>(b);
     return cudaGetLastError();
 }
 

@@ -124,13 +124,20 @@ struct CascadeBufs {
     // thresholds: group minima [Q][k] and the bound [Q], float bits
     uint32_t *gmin;
     uint32_t *bsf;
-    // survivors of the bound stages
+    // survivors of the bound stages, as written by the filter (unordered) ...
+    Pair *pairs_u;
+    float *lbi_u;
+    // ... and grouped by query: query q owns [qstart[q], qstart[q] + qcount[q])
     Pair *pairs;
     float *pair_lbi;
     float *pair_res;
+    int32_t *qcount;      // [Q], zeroed before the filter
+    int32_t *qstart;      // [Q]
+    unsigned long long *pair_total;  // pairs after grouping
+    int lbi_inline;       // the filter computes LB_Improved itself (warp per pair)
     int64_t pair_cap;
     unsigned long long *pair_count;
-    int seg_len, nseg;
+    int seg_len, nseg;    // nseg: sub-segments per query (segments x filter warps)
     int32_t *seg_start;   // [Q][nseg]
     int32_t *seg_count;   // [Q][nseg]
     // work cursors and counters
@@ -145,7 +152,10 @@ cudaError_t launch_seed_select(const CascadeBufs &b, cudaStream_t s);
 cudaError_t launch_seed_kth(const CascadeBufs &b, cudaStream_t s);
 cudaError_t launch_query_copies(const float *y, int64_t count, int n, QueryCopies qc, cudaStream_t s);
 cudaError_t launch_lbi_filter(const CascadeBufs &b, cudaStream_t s);
+int lbi_filter_warps(int n, int w, int S, int seg_len);  // warps per filter CTA (one sub-segment each)
 cudaError_t launch_finalize(const CascadeBufs &b, cudaStream_t s);
+cudaError_t launch_group_by_query(const CascadeBufs &b, cudaStream_t s);
+
 
 // DTW over an explicit pair list (pairs != nullptr) or the implicit pairs
 // c -> (q = per_pair_y ? c : 0, c).  thr_bits: per-query thresholds (float

@@ -18,6 +18,7 @@ namespace dtwk {
 
 constexpr int kDtwRegMaxC = 208;  // widest band kept in one thread's registers
 constexpr int kDtwThreads = 128;
+constexpr int kDtwGroupMaxC = 64;  // band widths processed 4 rows per window load
 
 struct DtwGeom {
     int C;      // slots per pair (register path) or per warp (wide path)
@@ -48,8 +49,11 @@ inline DtwGeom dtw_geom(int n, int w) {
         g.wl = w;
         g.wide = true;
     }
-    g.padl = g.C;                               // >= wl, multiple of 4
-    g.ylen = (n + g.padl + g.C + w + 1 + 3) / 4 * 4;
+    // Register path: padl = wl puts row i's band window at padded index i, so
+    // a group of 4 rows starting at a multiple of 4 reads one aligned span of
+    // copy 0.  Wide path: padl = C (scalar loads).
+    g.padl = g.wide ? g.C : g.wl;
+    g.ylen = (n + g.padl + g.C + w + 8 + 3) / 4 * 4;
     return g;
 }
 

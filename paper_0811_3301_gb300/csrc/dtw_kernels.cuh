@@ -183,6 +183,144 @@ k_dtw_reg(DtwJob j, int e, int wl) {
 }
 
 // ---------------------------------------------------------------------------
+// Register path, 4 rows per window load (C <= 64).  Rows 4g .. 4g+3 need the
+// query at padded indices 4g .. 4g + C + 2; with padl = wl that span starts
+// on a 16-byte boundary of copy 0, so (C + 4) / 4 aligned 128-bit loads serve
+// all four rows and row u's slot K reads window element u + K (a fixed
+// register).  One 128-bit load of x covers the four rows.
+// ---------------------------------------------------------------------------
+template <int K, int C, int P, int U>
+__device__ __forceinline__ void dtw_cells_win(float (&D)[C], float xi, const float (&yw)[C + 4]) {
+    if constexpr (K < C) {
+        dtw_cell<K, C, P>(D, xi, yw[U + K]);
+        dtw_cells_win<K + 1, C, P, U>(D, xi, yw);
+    }
+}
+
+template <int C, int P, int U>
+__device__ __forceinline__ void dtw_row_win(float (&D)[C], float xi, const float (&yw)[C + 4], int e) {
+    switch (e) {
+        case 0: dtw_cell<0, C, P>(D, xi, yw[U + 0]); [[fallthrough]];
+        case 1: dtw_cell<1, C, P>(D, xi, yw[U + 1]); [[fallthrough]];
+        case 2: dtw_cell<2, C, P>(D, xi, yw[U + 2]); [[fallthrough]];
+        case 3: dtw_cell<3, C, P>(D, xi, yw[U + 3]); [[fallthrough]];
+        case 4: dtw_cell<4, C, P>(D, xi, yw[U + 4]); [[fallthrough]];
+        case 5: dtw_cell<5, C, P>(D, xi, yw[U + 5]); [[fallthrough]];
+        case 6: dtw_cell<6, C, P>(D, xi, yw[U + 6]); [[fallthrough]];
+        case 7: dtw_cell<7, C, P>(D, xi, yw[U + 7]); [[fallthrough]];
+        case 8: dtw_cell<8, C, P>(D, xi, yw[U + 8]); [[fallthrough]];
+        case 9: dtw_cell<9, C, P>(D, xi, yw[U + 9]); [[fallthrough]];
+        case 10: dtw_cell<10, C, P>(D, xi, yw[U + 10]); [[fallthrough]];
+        case 11: dtw_cell<11, C, P>(D, xi, yw[U + 11]); [[fallthrough]];
+        case 12: dtw_cell<12, C, P>(D, xi, yw[U + 12]); [[fallthrough]];
+        case 13: dtw_cell<13, C, P>(D, xi, yw[U + 13]); [[fallthrough]];
+        case 14: dtw_cell<14, C, P>(D, xi, yw[U + 14]); [[fallthrough]];
+        default: dtw_cell<15, C, P>(D, xi, yw[U + 15]);
+    }
+    dtw_cells_win<16, C, P, U>(D, xi, yw);
+}
+
+template <int C, int P>
+__global__ void __launch_bounds__(kDtwThreads)
+k_dtw_reg4(DtwJob j, int e, int wl, bool xvec) {
+    const int lane = threadIdx.x & 31;
+    const int n = j.n;
+    const int ylen = j.qc.ylen;
+    if (j.npairs_dev) j.npairs = (int64_t)*j.npairs_dev;
+    unsigned long long n_skip = 0, n_comp = 0, n_aband = 0, n_rows = 0;
+    for (;;) {
+        unsigned long long chunk = 0;
+        if (lane == 0) chunk = atomicAdd(j.cursor, 1ull);
+        chunk = __shfl_sync(0xffffffffu, chunk, 0);
+        const int64_t p0 = (int64_t)chunk * 32;
+        if (p0 >= j.npairs) break;
+        const int64_t pi = p0 + lane;
+        int q, c;
+        bool valid;
+        fetch_pair(j, pi, q, c, valid);
+        float thr = kInf;
+        if (valid) {
+            thr = j.bsf ? load_threshold(j.bsf + q) : j.fixed_thr;
+            if (j.pair_lbi && j.pair_lbi[pi] > thr * (1.0f + j.slack)) {
+                j.res[pi] = kInf;
+                valid = false;
+                ++n_skip;
+            }
+        }
+        if (valid) {
+            ++n_comp;
+            const float *x = j.db + (int64_t)c * n;
+            const float *y0 = j.qc.data + (int64_t)q * 4 * ylen;  // copy 0; row i starts at index i
+            float D[C];
+#pragma unroll
+            for (int k = 0; k < C; ++k) D[k] = sel_eq(k, wl, 0.0f, kInf);  // row -1: D(-1,-1) = 0
+            bool abandoned = false;
+            int rows = n;
+            for (int i = 0; i < n; i += 4) {
+                float yw[C + 4];
+                const float4 *yb = reinterpret_cast<const float4 *>(y0 + i);
+#pragma unroll
+                for (int v = 0; v < (C + 4) / 4; ++v) {
+                    const float4 t = __ldg(yb + v);
+                    yw[4 * v] = t.x;
+                    yw[4 * v + 1] = t.y;
+                    yw[4 * v + 2] = t.z;
+                    yw[4 * v + 3] = t.w;
+                }
+                float4 x4;
+                if (xvec && i + 4 <= n) {
+                    x4 = __ldg(reinterpret_cast<const float4 *>(x + i));
+                } else {
+                    x4.x = __ldg(x + i);
+                    x4.y = i + 1 < n ? __ldg(x + i + 1) : 0.0f;
+                    x4.z = i + 2 < n ? __ldg(x + i + 2) : 0.0f;
+                    x4.w = i + 3 < n ? __ldg(x + i + 3) : 0.0f;
+                }
+                dtw_row_win<C, P, 0>(D, x4.x, yw, e);
+                if (i + 1 < n) dtw_row_win<C, P, 1>(D, x4.y, yw, e);
+                if (i + 2 < n) dtw_row_win<C, P, 2>(D, x4.z, yw, e);
+                if (i + 3 < n) dtw_row_win<C, P, 3>(D, x4.w, yw, e);
+                if (j.abandon && (i & 4) && i + 4 < n) {
+                    float mn = D[0];
+#pragma unroll
+                    for (int k = 1; k < C; ++k) mn = fminf(mn, D[k]);
+                    if (j.bsf) thr = load_threshold(j.bsf + q);
+                    if (mn > thr) {
+                        abandoned = true;
+                        rows = i + 4;
+                        break;
+                    }
+                }
+            }
+            n_rows += rows;
+            float d = kInf;
+#pragma unroll
+            for (int k = 0; k < C; ++k) d = sel_eq(k, wl, D[k], d);
+            if (abandoned) {
+                d = kInf;
+                ++n_aband;
+            }
+            if (!j.bsf && d > j.fixed_thr) d = kInf;
+            j.res[pi] = j.root_out ? root_p(d, P) : d;
+            if (!abandoned && j.bsf) update_threshold(j.bsf, j.gmin, j.k, q, c % j.k, d);
+        }  // valid
+    }
+    if (j.counters) {
+        n_skip = __reduce_add_sync(0xffffffffu, (unsigned)n_skip);
+        n_comp = __reduce_add_sync(0xffffffffu, (unsigned)n_comp);
+        n_aband = __reduce_add_sync(0xffffffffu, (unsigned)n_aband);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) n_rows += __shfl_xor_sync(0xffffffffu, n_rows, o);
+        if (lane == 0) {
+            if (n_rows) atomicAdd(j.counters + CNT_DTW_ROWS, n_rows);
+            if (n_skip) atomicAdd(j.counters + CNT_DTW_SKIP, n_skip);
+            if (n_comp) atomicAdd(j.counters + CNT_DTW_COMPUTED, n_comp);
+            if (n_aband) atomicAdd(j.counters + CNT_DTW_ABANDONED, n_aband);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Wide path (2w+1 > 208): one warp per pair, lane l owns the CL slots
 // l*CL .. l*CL+CL-1 of the band (slot k holds column i - w + k; slots above
 // 2w are outside the band).  A slot depends on the slot below it in the same

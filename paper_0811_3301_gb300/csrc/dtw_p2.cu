@@ -18,7 +18,21 @@ int blocks_for(K kernel, int64_t warps_needed) {
 
 cudaError_t launch_dtw_p2(const DtwJob &j, const DtwGeom &g, cudaStream_t s) {
     if (j.npairs <= 0) return cudaSuccess;
-    if (!g.wide) {
+    if (!g.wide && g.C <= kDtwGroupMaxC) {
+        const int64_t warps = (j.npairs + 31) / 32;
+        const bool xvec = (j.n % 4 == 0) && ((reinterpret_cast<uintptr_t>(j.db) & 15) == 0);
+#define DTW_REG4_CASE(CC)                                                             \
+    case CC: {                                                                        \
+        auto kern = k_dtw_reg4<CC, 2>;                                              \
+        kern<<<blocks_for(kern, warps), kDtwThreads, 0, s>>>(j, g.e, g.wl, xvec);     \
+        break;                                                                        \
+    }
+        switch (g.C) {
+            DTW_REG4_CASE(16) DTW_REG4_CASE(32) DTW_REG4_CASE(48) DTW_REG4_CASE(64)
+            default: return cudaErrorInvalidValue;
+        }
+#undef DTW_REG4_CASE
+    } else if (!g.wide) {
         const int64_t warps = (j.npairs + 31) / 32;
 #define DTW_REG_CASE(CC)                                                              \
     case CC: {                                                                        \

@@ -73,8 +73,8 @@ cudaError_t launch_lbk_single(const float *cand, int64_t N, const float *U, cons
 // candidate reads are conflict-free 128-bit loads and the envelope reads are
 // warp-wide broadcasts.  Out-of-range elements and candidates are
 // zero-filled: x = U = L = 0 contributes nothing.  Each thread keeps 16
-// accumulators (4 queries x 4 candidates), summed per chunk and then added to
-// the running total.  Each CTA also writes, per query, the smallest
+// pairs of accumulators (4 queries x 4 candidates, even and odd indices),
+// summed per chunk and then added to the running total.  Each CTA also writes, per query, the smallest
 // (bound, index) key over its 128 candidates, from which the seeds are drawn.
 // ---------------------------------------------------------------------------
 constexpr int TQ = 32, TC = 128, KC = 32, XS = KC + 4;  // XS: padded row stride
@@ -147,11 +147,13 @@ template <int P, bool VEC>
 __global__ void __launch_bounds__(256)
 k_lbk_tile(const float *__restrict__ db, int N, const float *__restrict__ U,
            const float *__restrict__ L, int Q, int n, float *__restrict__ lb,
-           unsigned long long *__restrict__ tile_min) {
+           unsigned long long *__restrict__ tile_min, int tile0, int ntiles) {
     extern __shared__ __align__(16) unsigned char smraw[];
     TileSmem &sm = *reinterpret_cast<TileSmem *>(smraw);
-    const int c0 = blockIdx.x * TC;
-    const int q0 = blockIdx.y * TQ;
+    // consecutive CTAs share a candidate tile (the database is read once)
+    const int q0 = blockIdx.x * TQ;
+    const int tile = tile0 + blockIdx.y;
+    const int c0 = tile * TC;
     const int lane = threadIdx.x & 31;
     const int wq = (threadIdx.x >> 5) * 4;  // first query row of this warp in the tile
     float tot[4][4];
@@ -171,14 +173,19 @@ k_lbk_tile(const float *__restrict__ db, int N, const float *__restrict__ U,
             cp_async_wait<0>();
         }
         __syncthreads();
-        float acc[4][4];
+        // two partial sums per pair (even and odd indices), updated with
+        // packed fp32x2 arithmetic: x - U and L - x as fma(., -1, .) (one
+        // rounding, as a subtraction), a 3-input max per index, then a packed
+        // add (p = 1) or fma (p = 2)
+        float2 acc[4][4];
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
-            for (int b = 0; b < 4; ++b) acc[a][b] = 0.0f;
+            for (int b = 0; b < 4; ++b) acc[a][b] = make_float2(0.0f, 0.0f);
         const float *xs = sm.x[buf];
         const float *us = sm.u[buf];
         const float *ls = sm.l[buf];
+        const float2 m1 = make_float2(-1.0f, -1.0f);
 #pragma unroll 2
         for (int k = 0; k < KC; k += 4) {
             float4 xv[4], uv[4], lv[4];
@@ -194,18 +201,24 @@ k_lbk_tile(const float *__restrict__ db, int N, const float *__restrict__ U,
             for (int a = 0; a < 4; ++a)
 #pragma unroll
                 for (int b = 0; b < 4; ++b) {
-                    float s = acc[a][b];
-                    s = acc_dist<P>(s, xv[b].x, lv[a].x, uv[a].x);
-                    s = acc_dist<P>(s, xv[b].y, lv[a].y, uv[a].y);
-                    s = acc_dist<P>(s, xv[b].z, lv[a].z, uv[a].z);
-                    s = acc_dist<P>(s, xv[b].w, lv[a].w, uv[a].w);
+                    float2 s = acc[a][b];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const float2 xx = h ? make_float2(xv[b].z, xv[b].w) : make_float2(xv[b].x, xv[b].y);
+                        const float2 uu = h ? make_float2(uv[a].z, uv[a].w) : make_float2(uv[a].x, uv[a].y);
+                        const float2 ll = h ? make_float2(lv[a].z, lv[a].w) : make_float2(lv[a].x, lv[a].y);
+                        const float2 d1 = __ffma2_rn(uu, m1, xx);  // x - U
+                        const float2 d2 = __ffma2_rn(xx, m1, ll);  // L - x
+                        const float2 dd = make_float2(max3f(d1.x, d2.x, 0.0f), max3f(d1.y, d2.y, 0.0f));
+                        s = (P == 1) ? __fadd2_rn(s, dd) : __ffma2_rn(dd, dd, s);
+                    }
                     acc[a][b] = s;
                 }
         }
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
-            for (int b = 0; b < 4; ++b) tot[a][b] += acc[a][b];
+            for (int b = 0; b < 4; ++b) tot[a][b] += acc[a][b].x + acc[a][b].y;
         __syncthreads();  // buffer `buf` is refilled in the next iteration
     }
 #pragma unroll
@@ -227,7 +240,7 @@ k_lbk_tile(const float *__restrict__ db, int N, const float *__restrict__ U,
             const unsigned long long other = __shfl_xor_sync(0xffffffffu, key, o);
             key = other < key ? other : key;
         }
-        if (lane == 0 && q < Q && tile_min) tile_min[(int64_t)q * gridDim.x + blockIdx.x] = key;
+        if (lane == 0 && q < Q && tile_min) tile_min[(int64_t)q * ntiles + tile] = key;
     }
 }
 
@@ -239,109 +252,361 @@ cudaError_t launch_lbk_tile(const float *db, int N, const float *U, const float 
     bool vec = (n % 4 == 0) && ((reinterpret_cast<uintptr_t>(db) & 15) == 0) &&
                ((reinterpret_cast<uintptr_t>(U) & 15) == 0) &&
                ((reinterpret_cast<uintptr_t>(L) & 15) == 0);
-    dim3 grid((N + TC - 1) / TC, (Q + TQ - 1) / TQ);
+    const int ntiles = (N + TC - 1) / TC;
     size_t smem = sizeof(TileSmem);
-    auto set = [&](const void *f) {
-        cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    };
-    if (p == 1) {
-        if (vec) { set((const void *)k_lbk_tile<1, true>); k_lbk_tile<1, true><<<grid, 256, smem, s>>>(db, N, U, L, Q, n, lb, tile_min); }
-        else { set((const void *)k_lbk_tile<1, false>); k_lbk_tile<1, false><<<grid, 256, smem, s>>>(db, N, U, L, Q, n, lb, tile_min); }
-    } else {
-        if (vec) { set((const void *)k_lbk_tile<2, true>); k_lbk_tile<2, true><<<grid, 256, smem, s>>>(db, N, U, L, Q, n, lb, tile_min); }
-        else { set((const void *)k_lbk_tile<2, false>); k_lbk_tile<2, false><<<grid, 256, smem, s>>>(db, N, U, L, Q, n, lb, tile_min); }
+    auto kern = p == 1 ? (vec ? k_lbk_tile<1, true> : k_lbk_tile<1, false>)
+                       : (vec ? k_lbk_tile<2, true> : k_lbk_tile<2, false>);
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    for (int t0 = 0; t0 < ntiles; t0 += 65535) {  // grid.y limit
+        dim3 grid((Q + TQ - 1) / TQ, std::min(65535, ntiles - t0));
+        kern<<<grid, 256, smem, s>>>(db, N, U, L, Q, n, lb, tile_min, t0, ntiles);
     }
     return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
-// LB_Improved of one pair by one warp (Sec. 8).  Lane l owns the indices
-// i = l + 32 t.  The projection h = H(x, y) is written to the warp's shared
-// scratch, its envelope with the same w is built by doubling (as in the
-// envelope kernel), then the distance from y to that envelope is summed.
-// scratch: 4n floats per warp.  Returns LB_Improved^p on every lane and the
-// first-pass sum LB_Keogh^p in *lbk.
+// LB_Improved of one pair by one warp (Sec. 8).
+//
+// Lane l owns the M consecutive indices l*M .. l*M+M-1 ("chunk" l), M the
+// power of two >= n/32.  For one query the lane keeps its chunk of U(y),
+// L(y) and y; per candidate it loads its chunk of x, clamps it into the
+// envelope (h = H(x, y), Eq. 1), adds the first-pass terms |x_i - h_i|^p and
+// forms the chunk's prefix and suffix max/min of h.  A table over the 32
+// chunk totals (max/min of 2^j consecutive chunks) covers whole chunks.  The
+// envelope of h at i, over [a, b] = [i-w, i+w] clipped, is suffix(a) of
+// chunk(a), the whole chunks strictly between, and prefix(b) of chunk(b) --
+// or a direct max/min over h when [a, b] lies strictly inside one chunk.  The
+// second-pass terms are d(y_i, [L'_i, U'_i])^p.
+//
+// Prefix/suffix pairs (max, min) and the table live in shared memory in
+// position-major order [t][lane], so that a lane's writes (fixed lane) and the
+// window lookups of a warp (fixed t, consecutive chunks) are conflict-free.
+// MT is M when M <= 16 (chunk held in registers) and 0 for a runtime M
+// (chunk streamed through shared memory).
 // ---------------------------------------------------------------------------
-template <int P>
-__device__ float warp_lb_improved(const float *__restrict__ x, const float *__restrict__ y,
-                                  const float *__restrict__ U, const float *__restrict__ L, int n,
-                                  int w, float *scratch, float *lbk) {
-    const int lane = threadIdx.x & 31;
-    float *ax = scratch, *an = scratch + n, *bx = scratch + 2 * n, *bn = scratch + 3 * n;
-    float acc1 = 0.0f;
-    for (int i = lane; i < n; i += 32) {
-        float xv = __ldg(x + i);
-        float u = __ldg(U + i), l = __ldg(L + i);
-        float h = fminf(fmaxf(xv, l), u);  // Eq. 1 (L <= U)
-        float d = fabsf(xv - h);
-        acc1 = (P == 1) ? acc1 + d : fmaf(d, d, acc1);
-        ax[i] = h;
-        an[i] = h;
+constexpr int kLbiRegM = 8;  // largest chunk kept in registers
+
+struct LbiGeom {
+    int m, lg;
+};
+__host__ __device__ inline LbiGeom lbi_geom(int n) {
+    LbiGeom g;
+    const int need = (n + 31) / 32;
+    g.m = 1;
+    g.lg = 0;
+    while (g.m < need) {
+        g.m <<= 1;
+        ++g.lg;
     }
-    __syncwarp();
-    const int len_max = min(2 * w + 1, n);
-    const int kmax = 31 - __clz(len_max);
-    for (int j = 1; j <= kmax; ++j) {
-        const int hh = 1 << (j - 1);
-        for (int i = lane; i < n; i += 32) {
-            int i2 = min(i + hh, n - 1);
-            bx[i] = fmaxf(ax[i], ax[i2]);
-            bn[i] = fminf(an[i], an[i2]);
+    return g;
+}
+// Chunk columns of the prefix/suffix arrays.  For chunks held in registers
+// (M <= kLbiRegM) the arrays carry neutral (-inf, +inf) columns beyond both
+// ends of the series, so that a window reaching past an end needs no
+// clamping: column c of chunk c - pad_left.
+struct LbiCols {
+    int left, width;
+};
+__host__ __device__ inline LbiCols lbi_cols(int n, int w) {
+    const int m = lbi_geom(n).m;
+    LbiCols c;
+    if (m > kLbiRegM) {
+        c.left = 0;
+        c.width = 32;
+    } else {
+        c.left = (w + m - 1) / m + 1;
+        c.width = c.left + 32 + (w + 2 * m - 1) / m + 1;
+    }
+    return c;
+}
+// per-warp scratch in floats: prefix and suffix (max, min) pairs [M][width]
+// each, the chunk table (max, min) [6][32] and the chunk of h [M][32]
+__host__ __device__ inline int lbi_scratch_floats(int n, int w) {
+    const int m = lbi_geom(n).m;
+    return 2 * 2 * m * lbi_cols(n, w).width + 2 * 6 * 32 + 32 * m;
+}
+// per-query staging: y in [t][32] layout, and for runtime M also U and L
+__host__ __device__ inline int lbi_query_floats(int n) {
+    const int m = lbi_geom(n).m;
+    return m > kLbiRegM ? 3 * 32 * m : 32 * m;
+}
+
+// Per-lane view of the query: the chunk of U and L in registers for MT > 0,
+// otherwise in shared memory; y always in shared memory.
+template <int MT>
+struct LbiQuery {
+    float u[MT > 0 ? MT : 1], l[MT > 0 ? MT : 1];
+    const float *sq;  // y [M][32]; for MT == 0 then U [M][32], L [M][32]
+    __device__ float U(int t, int lane, int m) const { return sq[(m + t) * 32 + lane]; }
+    __device__ float L(int t, int lane, int m) const { return sq[(2 * m + t) * 32 + lane]; }
+    __device__ float Y(int t, int lane, int m) const { return sq[t * 32 + lane]; }
+};
+
+// Load the query chunk of this lane (MT > 0: into registers; MT == 0: the
+// whole block stages [t][32] arrays into sq, caller synchronises).
+template <int MT>
+__device__ __forceinline__ void lbi_load_query(LbiQuery<MT> &Qv, const float *__restrict__ y, const float *__restrict__ U,
+                                               const float *__restrict__ L, int n, float *sq) {
+    const LbiGeom g = lbi_geom(n);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int c = i >> g.lg, t = i & (g.m - 1);
+        sq[t * 32 + c] = y[i];
+        if constexpr (MT == 0) {
+            sq[(g.m + t) * 32 + c] = U[i];
+            sq[(2 * g.m + t) * 32 + c] = L[i];
+        }
+    }
+    Qv.sq = sq;
+    if constexpr (MT > 0) {
+        const int lane = threadIdx.x & 31;
+#pragma unroll
+        for (int t = 0; t < MT; ++t) {
+            const int i = lane * MT + t;
+            Qv.u[t] = i < n ? U[i] : 0.0f;
+            Qv.l[t] = i < n ? L[i] : 0.0f;
+        }
+    }
+}
+
+// Write the neutral padding columns of a warp's prefix/suffix arrays (once
+// per warp; the per-pair passes only write the 32 real columns).
+template <int MT>
+__device__ inline void lbi_init_scratch(float *scratch, int n, int w) {
+    if constexpr (MT > 0) {
+        const int lane = threadIdx.x & 31;
+        const LbiCols cols = lbi_cols(n, w);
+        float2 *Pre = reinterpret_cast<float2 *>(scratch);
+        float2 *Suf = Pre + MT * cols.width;
+        const float2 neutral = make_float2(-kInf, kInf);
+        for (int e = lane; e < MT * cols.width; e += 32) {
+            const int c = e % cols.width;
+            if (c < cols.left || c >= cols.left + 32) {
+                Pre[e] = neutral;
+                Suf[e] = neutral;
+            }
         }
         __syncwarp();
-        float *t;
-        t = ax; ax = bx; bx = t;
-        t = an; an = bn; bn = t;
     }
+}
+
+template <int P, int MT>
+__device__ __forceinline__ float warp_lb_improved(const float *__restrict__ x, const LbiQuery<MT> &Qv, int n, int w,
+                                                  float *scratch, bool vec) {
+    const int lane = threadIdx.x & 31;
+    const LbiGeom g = lbi_geom(n);
+    const int m = MT > 0 ? MT : g.m;
+    const int lg = g.lg;
+    const LbiCols cols = lbi_cols(n, w);
+    const int W = cols.width, PLc = cols.left;
+    float2 *Pre = reinterpret_cast<float2 *>(scratch);  // [m][W] (max, min)
+    float2 *Suf = Pre + W * m;                           // [m][W]
+    float2 *T = Suf + W * m;                             // [6][32]
+    float *Hs = reinterpret_cast<float *>(T + 6 * 32);   // [m][32]
+    const float NEG = -kInf, POS = kInf;
+    const int i0 = lane * m;
+    const int cnt_in = max(0, min(m, n - i0));
+    float acc1 = 0.0f;
+    float pmax = NEG, pmin = POS;
+    float tmax, tmin;
+    if constexpr (MT > 0) {
+        float h[MT];
+        float xv[MT];
+        if (vec && MT >= 4 && cnt_in == MT) {
+#pragma unroll
+            for (int t = 0; t < MT; t += 4) {
+                const float4 v = __ldg(reinterpret_cast<const float4 *>(x + i0 + t));
+                xv[t] = v.x;
+                xv[t + 1] = v.y;
+                xv[t + 2] = v.z;
+                xv[t + 3] = v.w;
+            }
+        } else {
+#pragma unroll
+            for (int t = 0; t < MT; ++t) xv[t] = t < cnt_in ? __ldg(x + i0 + t) : 0.0f;
+        }
+#pragma unroll
+        for (int t = 0; t < MT; ++t) {
+            const float hv = fminf(fmaxf(xv[t], Qv.l[t]), Qv.u[t]);  // Eq. 1 (L <= U)
+            const float d = fabsf(xv[t] - hv);
+            if (t < cnt_in) {
+                acc1 = (P == 1) ? acc1 + d : fmaf(d, d, acc1);
+                h[t] = hv;
+            } else {
+                h[t] = NEG;
+            }
+        }
+        if (2 * w < MT) {
+            // windows can lie inside a chunk: keep h for the direct scan
+#pragma unroll
+            for (int t = 0; t < MT; ++t) Hs[t * 32 + lane] = h[t];
+        }
+#pragma unroll
+        for (int t = 0; t < MT; ++t) {
+            pmax = fmaxf(pmax, h[t]);
+            pmin = (t < cnt_in) ? fminf(pmin, h[t]) : pmin;
+            Pre[t * W + PLc + lane] = make_float2(pmax, pmin);
+        }
+        float smax = NEG, smin = POS;
+#pragma unroll
+        for (int t = MT - 1; t >= 0; --t) {
+            smax = fmaxf(smax, h[t]);
+            smin = (t < cnt_in) ? fminf(smin, h[t]) : smin;
+            Suf[t * W + PLc + lane] = make_float2(smax, smin);
+        }
+    } else {
+        for (int t = 0; t < m; ++t) {
+            float hv = NEG;
+            if (t < cnt_in) {
+                const float xv = __ldg(x + i0 + t);
+                hv = fminf(fmaxf(xv, Qv.L(t, lane, m)), Qv.U(t, lane, m));
+                const float d = fabsf(xv - hv);
+                acc1 = (P == 1) ? acc1 + d : fmaf(d, d, acc1);
+                pmax = fmaxf(pmax, hv);
+                pmin = fminf(pmin, hv);
+            }
+            Hs[t * 32 + lane] = hv;
+            Pre[t * W + lane] = make_float2(pmax, pmin);
+        }
+        float smax = NEG, smin = POS;
+        for (int t = m - 1; t >= 0; --t) {
+            if (t < cnt_in) {
+                const float hv = Hs[t * 32 + lane];
+                smax = fmaxf(smax, hv);
+                smin = fminf(smin, hv);
+            }
+            Suf[t * W + lane] = make_float2(smax, smin);
+        }
+    }
+    // table over chunk totals: T_j[c] = max/min of chunks c .. c + 2^j - 1
+    tmax = pmax;
+    tmin = pmin;
+    T[lane] = make_float2(tmax, tmin);
+#pragma unroll
+    for (int j = 1; j < 6; ++j) {
+        const int hh = 1 << (j - 1);
+        const float omax = __shfl_down_sync(0xffffffffu, tmax, hh);
+        const float omin = __shfl_down_sync(0xffffffffu, tmin, hh);
+        if (lane + hh < 32) {
+            tmax = fmaxf(tmax, omax);
+            tmin = fminf(tmin, omin);
+        }
+        T[j * 32 + lane] = make_float2(tmax, tmin);
+    }
+    __syncwarp();
     float acc2 = 0.0f;
-    for (int i = lane; i < n; i += 32) {
-        int a = max(0, i - w), b = min(n - 1, i + w);
-        int k = 31 - __clz(b - a + 1);
-        const float *tx = (k == kmax) ? ax : bx;
-        const float *tn = (k == kmax) ? an : bn;
-        int b2 = b - (1 << k) + 1;
-        float uu = fmaxf(tx[a], tx[b2]);
-        float ll = fminf(tn[a], tn[b2]);
-        acc2 = acc_dist<P>(acc2, __ldg(y + i), ll, uu);
+    if (MT > 0 && 2 * w >= m) {
+        // Window of i = lane*M + t: [a, b] = [i - w, i + w]; chunk(a) = lane + da,
+        // position pa, with da, pa depending on t and w only (uniform); beyond
+        // the series the padded columns are neutral, so no clamping.
+#pragma unroll
+        for (int t = 0; t < (MT > 0 ? MT : 1); ++t) {
+            const int da = (t - w) >> lg, pa = (t - w) & (m - 1);
+            const int db = (t + w) >> lg, pb = (t + w) & (m - 1);
+            const float2 sa = Suf[pa * W + PLc + da + lane];
+            const float2 pv = Pre[pb * W + PLc + db + lane];
+            float uu = fmaxf(sa.x, pv.x), ll = fminf(sa.y, pv.y);
+            const int lo = max(lane + da + 1, 0), hi = min(lane + db - 1, 31);
+            if (lo <= hi) {
+                const int k = 31 - __clz(hi - lo + 1);
+                const float2 t1 = T[k * 32 + lo], t2 = T[k * 32 + hi - (1 << k) + 1];
+                uu = max3f(uu, t1.x, t2.x);
+                ll = min3f(ll, t1.y, t2.y);
+            }
+            if (t < cnt_in) acc2 = acc_dist<P>(acc2, Qv.Y(t, lane, m), ll, uu);
+        }
+    } else {
+#pragma unroll 1
+        for (int t = 0; t < cnt_in; ++t) {
+            const int i = i0 + t;
+            const int a = max(0, i - w), b = min(n - 1, i + w);
+            const int ca = a >> lg, pa = a & (m - 1);
+            const int cb = b >> lg, pb = b & (m - 1);
+            float uu, ll;
+            if (ca == cb && pa > 0 && pb < m - 1 && b < n - 1) {
+                // window strictly inside one chunk (only when 2w + 2 < m)
+                uu = NEG;
+                ll = POS;
+                for (int k = pa; k <= pb; ++k) {
+                    const float hv = Hs[k * 32 + ca];
+                    uu = fmaxf(uu, hv);
+                    ll = fminf(ll, hv);
+                }
+            } else if (ca == cb) {
+                // the window starts the chunk (prefix) or reaches its end (suffix)
+                const float2 v = (pa == 0) ? Pre[pb * W + PLc + cb] : Suf[pa * W + PLc + ca];
+                uu = v.x;
+                ll = v.y;
+            } else {
+                const float2 sa = Suf[pa * W + PLc + ca], pb2 = Pre[pb * W + PLc + cb];
+                uu = fmaxf(sa.x, pb2.x);
+                ll = fminf(sa.y, pb2.y);
+                const int cnt = cb - ca - 1;
+                if (cnt > 0) {
+                    const int k = 31 - __clz(cnt);
+                    const float2 t1 = T[k * 32 + ca + 1], t2 = T[k * 32 + cb - (1 << k)];
+                    uu = max3f(uu, t1.x, t2.x);
+                    ll = min3f(ll, t1.y, t2.y);
+                }
+            }
+            acc2 = acc_dist<P>(acc2, Qv.Y(t, lane, m), ll, uu);
+        }
     }
     __syncwarp();  // scratch is reused by the next pair
-    acc1 = warp_sum(acc1);
-    acc2 = warp_sum(acc2);
-    *lbk = acc1;
-    return acc1 + acc2;
+    return warp_sum(acc1 + acc2);
 }
 
 // All N candidates against one query, no threshold.
-template <int P>
+template <int P, int MT>
 __global__ void __launch_bounds__(128)
 k_lbi_single(const float *__restrict__ cand, int64_t N, const float *__restrict__ q,
              const float *__restrict__ U, const float *__restrict__ L, int n, int w,
-             float *__restrict__ out) {
-    extern __shared__ float sm[];
+             float *__restrict__ out, bool vec) {
+    extern __shared__ __align__(16) float sm[];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float *scratch = sm + (size_t)wid * 4 * n;
+    float *sq = sm;
+    float *scratch = sm + lbi_query_floats(n) + (size_t)wid * lbi_scratch_floats(n, w);
+    LbiQuery<MT> Qv;
+    lbi_load_query<MT>(Qv, q, U, L, n, sq);
+    lbi_init_scratch<MT>(scratch, n, w);
+    __syncthreads();
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + wid; c < N; c += warps) {
-        float lbk;
-        float v = warp_lb_improved<P>(cand + c * n, q, U, L, n, w, scratch, &lbk);
+        float v = warp_lb_improved<P, MT>(cand + c * n, Qv, n, w, scratch, vec);
         if (lane == 0) out[c] = root_p(v, P);
+    }
+}
+
+template <int P, int MT>
+static void lbi_single_go(const float *cand, int64_t N, const float *q, const float *U, const float *L, int n,
+                          int w, float *out, bool vec, cudaStream_t s) {
+    const int64_t per_warp = (int64_t)lbi_scratch_floats(n, w) * sizeof(float);
+    const int64_t per_query = (int64_t)lbi_query_floats(n) * sizeof(float);
+    const int warps = (int)std::min<int64_t>(4, std::max<int64_t>(1, (200 * 1024 - per_query) / per_warp));
+    const size_t smem = (size_t)per_query + (size_t)warps * per_warp;
+    const int blocks = (int)std::min<int64_t>((N + warps - 1) / warps, (int64_t)device_sm_count() * 16);
+    cudaFuncSetAttribute(k_lbi_single<P, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_lbi_single<P, MT><<<blocks, warps * 32, smem, s>>>(cand, N, q, U, L, n, w, out, vec);
+}
+
+template <int P>
+static void lbi_single_dispatch(const float *cand, int64_t N, const float *q, const float *U, const float *L,
+                                int n, int w, float *out, bool vec, cudaStream_t s) {
+    switch (lbi_geom(n).m) {
+        case 1: lbi_single_go<P, 1>(cand, N, q, U, L, n, w, out, vec, s); break;
+        case 2: lbi_single_go<P, 2>(cand, N, q, U, L, n, w, out, vec, s); break;
+        case 4: lbi_single_go<P, 4>(cand, N, q, U, L, n, w, out, vec, s); break;
+        case 8: lbi_single_go<P, 8>(cand, N, q, U, L, n, w, out, vec, s); break;
+        default: lbi_single_go<P, 0>(cand, N, q, U, L, n, w, out, vec, s); break;
     }
 }
 
 cudaError_t launch_lbi_single(const float *cand, int64_t N, const float *q, const float *U,
                               const float *L, int n, int w, int p, float *out, cudaStream_t s) {
     if (N <= 0) return cudaSuccess;
-    w = min(w, n - 1);
-    const int warps = 4;
-    size_t smem = (size_t)warps * 4 * n * sizeof(float);
-    int blocks = (int)std::min<int64_t>((N + warps - 1) / warps, (int64_t)device_sm_count() * 16);
-    if (p == 1) {
-        cudaFuncSetAttribute(k_lbi_single<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_lbi_single<1><<<blocks, warps * 32, smem, s>>>(cand, N, q, U, L, n, w, out);
-    } else {
-        cudaFuncSetAttribute(k_lbi_single<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_lbi_single<2><<<blocks, warps * 32, smem, s>>>(cand, N, q, U, L, n, w, out);
-    }
+    w = std::min(w, n - 1);
+    const bool vec = (n % 4 == 0) && ((reinterpret_cast<uintptr_t>(cand) & 15) == 0);
+    if (p == 1) lbi_single_dispatch<1>(cand, N, q, U, L, n, w, out, vec, s);
+    else lbi_single_dispatch<2>(cand, N, q, U, L, n, w, out, vec, s);
     return cudaGetLastError();
 }
 
@@ -354,40 +619,42 @@ cudaError_t launch_lbi_single(const float *cand, int64_t N, const float *q, cons
 // and written as one contiguous block of the pair list, whose start and
 // length are recorded per (query, segment).
 // ---------------------------------------------------------------------------
-template <int P>
-__global__ void k_lbi_filter(CascadeBufs b) {
+template <int P, int MT>
+__global__ void __launch_bounds__(256, 3) k_lbi_filter(CascadeBufs b, bool vec) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int nw = blockDim.x >> 5;
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int q = blockIdx.y, sg = blockIdx.x;
-    const int n = b.n;
-    float *scratch_all = reinterpret_cast<float *>(smraw);
-    float *scratch = scratch_all + (size_t)wid * 4 * n;
-    int32_t *surv_c = reinterpret_cast<int32_t *>(scratch_all + (size_t)nw * 4 * n);
-    float *surv_v = reinterpret_cast<float *>(surv_c + b.seg_len);
-    int32_t *seeds = reinterpret_cast<int32_t *>(surv_v + b.seg_len);
-    __shared__ int s_count;
-    __shared__ unsigned long long s_base;
-    __shared__ unsigned long long s_cnt[2];
-    if (threadIdx.x == 0) {
-        s_count = 0;
-        s_cnt[0] = s_cnt[1] = 0;
-    }
+    const int n = b.n, w = b.w;
+    const int per_warp_cap = b.seg_len / nw + 32;  // candidates one warp scans, rounded up
+    float *sq = reinterpret_cast<float *>(smraw);
+    float *scratch_all = sq + lbi_query_floats(n);
+    float *scratch = scratch_all + (size_t)wid * lbi_scratch_floats(n, w);
+    int32_t *seeds = reinterpret_cast<int32_t *>(scratch_all + (size_t)nw * lbi_scratch_floats(n, w));
+    int32_t *surv_c = seeds + b.S + (size_t)wid * 2 * per_warp_cap;
+    float *surv_v = reinterpret_cast<float *>(surv_c + per_warp_cap);
     for (int t = threadIdx.x; t < b.S; t += blockDim.x) seeds[t] = b.seed_pairs[(int64_t)q * b.S + t].c;
+    LbiQuery<MT> Qv;
+    if (b.lbi_inline) {
+        lbi_load_query<MT>(Qv, b.queries + (int64_t)q * n, b.U + (int64_t)q * n, b.L + (int64_t)q * n, n, sq);
+        lbi_init_scratch<MT>(scratch, n, b.w);
+    }
     __syncthreads();
 
+    // From here on each warp works alone: it scans its share of the segment,
+    // keeps its survivors in its own shared buffer and writes them as one
+    // contiguous block of the pair list (sub-segment (q, sg, wid)).
     const float bq = (b.mode == DTW_MODE_NOPRUNE) ? kInf : load_threshold(b.bsf + q);
     const float thr = bq * (1.0f + b.slack);
-    const float *y = b.queries + (int64_t)q * n;
-    const float *U = b.U + (int64_t)q * n;
-    const float *L = b.L + (int64_t)q * n;
     const int c0 = sg * b.seg_len;
     const int c1 = min(b.N, c0 + b.seg_len);
+    const float *lbrow = b.lb + (int64_t)q * b.N;
+    int cnt = 0;
     unsigned long long pk = 0;
     for (int base = c0 + wid * 32; base < c1; base += nw * 32) {
-        int c = base + lane;
-        bool valid = c < c1;
-        float lbv = valid ? b.lb[(int64_t)q * b.N + c] : kInf;
+        const int c = base + lane;
+        const bool valid = c < c1;
+        const float lbv = valid ? lbrow[c] : kInf;
         bool pass = valid && (lbv <= thr);
         if (pass) {
             for (int t = 0; t < b.S; ++t) pass = pass && (seeds[t] != c);
@@ -395,56 +662,79 @@ __global__ void k_lbi_filter(CascadeBufs b) {
         unsigned m = __ballot_sync(0xffffffffu, pass);
         pk += __popc(m);
         while (m) {
-            int src = __ffs(m) - 1;
+            const int src = __ffs(m) - 1;
             m &= m - 1;
-            int cc = __shfl_sync(0xffffffffu, c, src);
+            const int cc = __shfl_sync(0xffffffffu, c, src);
             float v = __shfl_sync(0xffffffffu, lbv, src);
-            if (b.mode == DTW_MODE_IMPROVED) {
-                float lbk;
-                v = warp_lb_improved<P>(b.db + (int64_t)cc * n, y, U, L, n, b.w, scratch, &lbk);
-            }
-            if (v <= thr && lane == 0) {
-                int slot = atomicAdd(&s_count, 1);
-                surv_c[slot] = cc;
-                surv_v[slot] = v;
+            if (b.lbi_inline) v = warp_lb_improved<P, MT>(b.db + (int64_t)cc * n, Qv, n, b.w, scratch, vec);
+            if (v <= thr) {
+                if (lane == 0) {
+                    surv_c[cnt] = cc;
+                    surv_v[cnt] = v;
+                }
+                ++cnt;
             }
         }
     }
-    if (lane == 0) atomicAdd(&s_cnt[0], pk);
-    __syncthreads();
-    const int cnt = s_count;
-    if (threadIdx.x == 0) {
-        unsigned long long base = cnt > 0 ? atomicAdd(b.pair_count, (unsigned long long)cnt) : 0ull;
-        s_base = base;
-        b.seg_start[(int64_t)q * b.nseg + sg] = (int32_t)base;
-        b.seg_count[(int64_t)q * b.nseg + sg] = cnt;
+    unsigned long long base = 0;
+    if (lane == 0 && cnt > 0) base = atomicAdd(b.pair_count, (unsigned long long)cnt);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    const int64_t sub = ((int64_t)q * gridDim.x + sg) * nw + wid;
+    if (lane == 0) {
+        b.seg_start[sub] = (int32_t)base;
+        b.seg_count[sub] = cnt;
+        if (cnt) atomicAdd(b.qcount + q, cnt);
         if (b.counters) {
-            if (s_cnt[0]) atomicAdd(b.counters + CNT_KEOGH_PASS, s_cnt[0]);
-            if (cnt) atomicAdd(b.counters + CNT_LBI_PASS, (unsigned long long)cnt);
+            if (pk) atomicAdd(b.counters + CNT_KEOGH_PASS, pk);
+            if (cnt && b.mode != DTW_MODE_IMPROVED) atomicAdd(b.counters + CNT_LBI_PASS, (unsigned long long)cnt);
+            if (cnt && b.lbi_inline) atomicAdd(b.counters + CNT_LBI_PASS, (unsigned long long)cnt);
         }
     }
-    __syncthreads();
-    const unsigned long long base = s_base;
-    for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
-        unsigned long long o = base + t;
-        b.pairs[o] = Pair{q, surv_c[t]};
-        b.pair_lbi[o] = surv_v[t];
-        b.pair_res[o] = kInf;
+    __syncwarp();
+    for (int t = lane; t < cnt; t += 32) {
+        const unsigned long long o = base + t;
+        b.pairs_u[o] = Pair{q, surv_c[t]};
+        b.lbi_u[o] = surv_v[t];
+    }
+}
+
+int lbi_filter_warps(int n, int w, int S, int seg_len) {
+    const int64_t per_warp = (int64_t)lbi_scratch_floats(n, w) * sizeof(float);
+    const int64_t per_query = (int64_t)lbi_query_floats(n) * sizeof(float);
+    const int64_t fixed = per_query + (int64_t)S * 4 + 64;
+    // aim at 4 CTAs of up to 8 warps per SM when the scratch is small
+    int nw = 8;
+    while (nw > 1 && fixed + nw * (per_warp + 8 * (seg_len / nw + 32)) > 56 * 1024) --nw;
+    return nw;
+}
+
+template <int P, int MT>
+static void lbi_filter_go(const CascadeBufs &b, bool vec, cudaStream_t s) {
+    const int nw = lbi_filter_warps(b.n, b.w, b.S, b.seg_len);
+    const int64_t per_warp = (int64_t)lbi_scratch_floats(b.n, b.w) * sizeof(float);
+    const int64_t per_query = (int64_t)lbi_query_floats(b.n) * sizeof(float);
+    const size_t smem = (size_t)per_query + (size_t)b.S * 4 + 64 + (size_t)nw * (per_warp + 8 * (b.seg_len / nw + 32));
+    const dim3 grid(b.nseg / nw, b.Q);
+    cudaFuncSetAttribute(k_lbi_filter<P, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_lbi_filter<P, MT><<<grid, nw * 32, smem, s>>>(b, vec);
+}
+
+template <int P>
+static void lbi_filter_dispatch(const CascadeBufs &b, bool vec, cudaStream_t s) {
+    switch (lbi_geom(b.n).m) {
+        case 1: lbi_filter_go<P, 1>(b, vec, s); break;
+        case 2: lbi_filter_go<P, 2>(b, vec, s); break;
+        case 4: lbi_filter_go<P, 4>(b, vec, s); break;
+        case 8: lbi_filter_go<P, 8>(b, vec, s); break;
+        default: lbi_filter_go<P, 0>(b, vec, s); break;
     }
 }
 
 cudaError_t launch_lbi_filter(const CascadeBufs &b, cudaStream_t s) {
     if (b.N <= 0 || b.Q <= 0) return cudaSuccess;
-    int nw = (int)std::min<int64_t>(8, std::max<int64_t>(1, (160 * 1024) / (16 * (int64_t)b.n)));
-    size_t smem = (size_t)nw * 4 * b.n * sizeof(float) + (size_t)b.seg_len * 8 + (size_t)b.S * 4 + 16;
-    dim3 grid(b.nseg, b.Q);
-    if (b.p == 1) {
-        cudaFuncSetAttribute(k_lbi_filter<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_lbi_filter<1><<<grid, nw * 32, smem, s>>>(b);
-    } else {
-        cudaFuncSetAttribute(k_lbi_filter<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_lbi_filter<2><<<grid, nw * 32, smem, s>>>(b);
-    }
+    const bool vec = (b.n % 4 == 0) && ((reinterpret_cast<uintptr_t>(b.db) & 15) == 0);
+    if (b.p == 1) lbi_filter_dispatch<1>(b, vec, s);
+    else lbi_filter_dispatch<2>(b, vec, s);
     return cudaGetLastError();
 }
 
