@@ -46,7 +46,7 @@ L2_BYTES = 129 * 2**20
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--N", type=int, default=100_000)
@@ -192,6 +192,16 @@ def roofline(prof, a, steps, peaks, stats):
         return {"kernel": "k_dtw_reg", "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Top/s",
                 "frac": (achieved / alu_peak) if achieved else None, "traffic": None, "ms_per_launch": ms,
                 "cells_per_launch": cells, "stage_share": share,
+                "peak_note": "%d SMs x 128 fp32 lanes x %.0f MHz (max SM clock)" % (sms, clock / 1e6)}
+    if dom == "lb_improved":
+        # LB_Improved of each LB_Keogh survivor: 11 fp32 ops per index (clamp 2,
+        # first term 2, envelope 3 (the paper's 3n comparisons), second term 4)
+        surv = stats.get("candidates", 0) - stats.get("seeds", 0) - stats.get("pruned_keogh", 0)
+        work = surv * a.n * 11.0 / 1e12
+        achieved = work / (ms / 1e3) if surv > 0 else None
+        return {"kernel": "k_lbi_filter", "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Top/s",
+                "frac": (achieved / alu_peak) if achieved else None, "traffic": None, "ms_per_launch": ms,
+                "pairs_per_launch": surv, "stage_share": share,
                 "peak_note": "%d SMs x 128 fp32 lanes x %.0f MHz (max SM clock)" % (sms, clock / 1e6)}
     return {"kernel": dom, "bound": "alu", "achieved": None, "peak": alu_peak, "unit": "Top/s", "frac": None,
             "traffic": None, "ms_per_launch": ms, "stage_share": share}

@@ -178,7 +178,7 @@ dtw_status dtw_profile_read(dtw_profile *out, int32_t reset);
  * deployment variant.  Its scratch is a fixed 8 MiB array of device memory
  * that belongs to the library and is held on every GPU that loads it until
  * the process exits; it never allocates.  A call whose scratch (the padded
- * query copies: 16 * (n + w + 2*C + 1) bytes per query row, with C the band
+ * query copies: about 16 * (n + w + 2*C + 8) bytes per query row, with C the band
  * slot count, plus 256 bytes) does not fit returns DTW_ERR_INVALID_ARG.  All
  * calls share the array, so calls that overlap on the GPU race.  The first
  * call on a device looks up the array's device address; make it before any

@@ -335,7 +335,7 @@ __host__ __device__ inline int lbi_query_floats(int n) {
 // otherwise in shared memory; y always in shared memory.
 template <int MT>
 struct LbiQuery {
-    float u[MT > 0 ? MT : 1], l[MT > 0 ? MT : 1];
+    float u[MT > 0 ? MT : 1], l[MT > 0 ? MT : 1], yr[MT > 0 ? MT : 1];
     const float *sq;  // y [M][32]; for MT == 0 then U [M][32], L [M][32]
     __device__ float U(int t, int lane, int m) const { return sq[(m + t) * 32 + lane]; }
     __device__ float L(int t, int lane, int m) const { return sq[(2 * m + t) * 32 + lane]; }
@@ -364,6 +364,7 @@ __device__ __forceinline__ void lbi_load_query(LbiQuery<MT> &Qv, const float *__
             const int i = lane * MT + t;
             Qv.u[t] = i < n ? U[i] : 0.0f;
             Qv.l[t] = i < n ? L[i] : 0.0f;
+            Qv.yr[t] = i < n ? y[i] : 0.0f;
         }
     }
 }
@@ -389,9 +390,36 @@ __device__ inline void lbi_init_scratch(float *scratch, int n, int w) {
     }
 }
 
+// This lane's chunk of a candidate row (MT > 0), loaded ahead of its use.
+template <int MT>
+struct LbiChunk {
+    float v[MT > 0 ? MT : 1];
+};
+template <int MT>
+__device__ __forceinline__ void lbi_load_chunk(LbiChunk<MT> &ch, const float *__restrict__ x, int n, bool vec) {
+    if constexpr (MT > 0) {
+        const int lane = threadIdx.x & 31;
+        const int i0 = lane * MT;
+        const int cnt_in = max(0, min(MT, n - i0));
+        if (vec && MT >= 4 && cnt_in == MT) {
+#pragma unroll
+            for (int t = 0; t < MT; t += 4) {
+                const float4 v = __ldg(reinterpret_cast<const float4 *>(x + i0 + t));
+                ch.v[t] = v.x;
+                ch.v[t + 1] = v.y;
+                ch.v[t + 2] = v.z;
+                ch.v[t + 3] = v.w;
+            }
+        } else {
+#pragma unroll
+            for (int t = 0; t < MT; ++t) ch.v[t] = t < cnt_in ? __ldg(x + i0 + t) : 0.0f;
+        }
+    }
+}
+
 template <int P, int MT>
 __device__ __forceinline__ float warp_lb_improved(const float *__restrict__ x, const LbiQuery<MT> &Qv, int n, int w,
-                                                  float *scratch, bool vec) {
+                                                  float *scratch, bool vec, const LbiChunk<MT> *pre = nullptr) {
     const int lane = threadIdx.x & 31;
     const LbiGeom g = lbi_geom(n);
     const int m = MT > 0 ? MT : g.m;
@@ -410,20 +438,9 @@ __device__ __forceinline__ float warp_lb_improved(const float *__restrict__ x, c
     float tmax, tmin;
     if constexpr (MT > 0) {
         float h[MT];
-        float xv[MT];
-        if (vec && MT >= 4 && cnt_in == MT) {
-#pragma unroll
-            for (int t = 0; t < MT; t += 4) {
-                const float4 v = __ldg(reinterpret_cast<const float4 *>(x + i0 + t));
-                xv[t] = v.x;
-                xv[t + 1] = v.y;
-                xv[t + 2] = v.z;
-                xv[t + 3] = v.w;
-            }
-        } else {
-#pragma unroll
-            for (int t = 0; t < MT; ++t) xv[t] = t < cnt_in ? __ldg(x + i0 + t) : 0.0f;
-        }
+        LbiChunk<MT> own;
+        if (pre == nullptr) lbi_load_chunk<MT>(own, x, n, vec);
+        const float *xv = pre ? pre->v : own.v;
 #pragma unroll
         for (int t = 0; t < MT; ++t) {
             const float hv = fminf(fmaxf(xv[t], Qv.l[t]), Qv.u[t]);  // Eq. 1 (L <= U)
@@ -495,24 +512,40 @@ __device__ __forceinline__ float warp_lb_improved(const float *__restrict__ x, c
     __syncwarp();
     float acc2 = 0.0f;
     if (MT > 0 && 2 * w >= m) {
-        // Window of i = lane*M + t: [a, b] = [i - w, i + w]; chunk(a) = lane + da,
-        // position pa, with da, pa depending on t and w only (uniform); beyond
-        // the series the padded columns are neutral, so no clamping.
+        // Window of i = lane*M + t: [a, b] = [i - w, i + w]; chunk(a) = lane + da_t
+        // at position pa_t and chunk(b) = lane + db_t at position pb_t, where
+        // da_t = D0 + fa_t and db_t = E0 + fb_t with 0/1 flags that depend on t
+        // and w only.  Beyond the series the padded columns are neutral, so the
+        // prefix/suffix lookups need no clamping.  The whole chunks strictly
+        // between take one of four ranges per lane; their max/min come from the
+        // chunk table once per pair and are selected per position.
+        const int pa0 = (-w) & (m - 1), D0 = (-w) >> lg;
+        const int pb0 = w & (m - 1), E0 = w >> lg;
+        float2 mid[2][2];
+#pragma unroll
+        for (int fa = 0; fa < 2; ++fa)
+#pragma unroll
+            for (int fb = 0; fb < 2; ++fb) {
+                const int lo = max(lane + D0 + fa + 1, 0), hi = min(lane + E0 + fb - 1, 31);
+                float2 r = make_float2(NEG, POS);
+                if (lo <= hi) {
+                    const int k = 31 - __clz(hi - lo + 1);
+                    const float2 t1 = T[k * 32 + lo], t2 = T[k * 32 + hi - (1 << k) + 1];
+                    r = make_float2(fmaxf(t1.x, t2.x), fminf(t1.y, t2.y));
+                }
+                mid[fa][fb] = r;
+            }
 #pragma unroll
         for (int t = 0; t < (MT > 0 ? MT : 1); ++t) {
-            const int da = (t - w) >> lg, pa = (t - w) & (m - 1);
-            const int db = (t + w) >> lg, pb = (t + w) & (m - 1);
-            const float2 sa = Suf[pa * W + PLc + da + lane];
-            const float2 pv = Pre[pb * W + PLc + db + lane];
-            float uu = fmaxf(sa.x, pv.x), ll = fminf(sa.y, pv.y);
-            const int lo = max(lane + da + 1, 0), hi = min(lane + db - 1, 31);
-            if (lo <= hi) {
-                const int k = 31 - __clz(hi - lo + 1);
-                const float2 t1 = T[k * 32 + lo], t2 = T[k * 32 + hi - (1 << k) + 1];
-                uu = max3f(uu, t1.x, t2.x);
-                ll = min3f(ll, t1.y, t2.y);
-            }
-            if (t < cnt_in) acc2 = acc_dist<P>(acc2, Qv.Y(t, lane, m), ll, uu);
+            const bool fa = pa0 + t >= m, fb = pb0 + t >= m;
+            const int pa = fa ? pa0 + t - m : pa0 + t;
+            const int pb = fb ? pb0 + t - m : pb0 + t;
+            const float2 sa = Suf[pa * W + PLc + D0 + (fa ? 1 : 0) + lane];
+            const float2 pv = Pre[pb * W + PLc + E0 + (fb ? 1 : 0) + lane];
+            const float2 md = fa ? (fb ? mid[1][1] : mid[1][0]) : (fb ? mid[0][1] : mid[0][0]);
+            const float uu = max3f(sa.x, pv.x, md.x);
+            const float ll = min3f(sa.y, pv.y, md.y);
+            if (t < cnt_in) acc2 = acc_dist<P>(acc2, Qv.yr[MT > 0 ? t : 0], ll, uu);
         }
     } else {
 #pragma unroll 1
@@ -624,7 +657,9 @@ __global__ void __launch_bounds__(256, 3) k_lbi_filter(CascadeBufs b, bool vec) 
     extern __shared__ __align__(16) unsigned char smraw[];
     const int nw = blockDim.x >> 5;
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int q = blockIdx.y, sg = blockIdx.x;
+    // CTAs in flight share a candidate segment (consecutive CTAs are queries),
+    // so the segment's rows stay in L2 for all the queries that test them
+    const int q = blockIdx.x, sg = blockIdx.y;
     const int n = b.n, w = b.w;
     const int per_warp_cap = b.seg_len / nw + 32;  // candidates one warp scans, rounded up
     float *sq = reinterpret_cast<float *>(smraw);
@@ -649,24 +684,42 @@ __global__ void __launch_bounds__(256, 3) k_lbi_filter(CascadeBufs b, bool vec) 
     const int c0 = sg * b.seg_len;
     const int c1 = min(b.N, c0 + b.seg_len);
     const float *lbrow = b.lb + (int64_t)q * b.N;
-    int cnt = 0;
-    unsigned long long pk = 0;
+    // phase 1: LB_Keogh test over this warp's share of the segment; the
+    // survivors (not seeds) are compacted into the warp's buffer
+    int cnt1 = 0;
     for (int base = c0 + wid * 32; base < c1; base += nw * 32) {
         const int c = base + lane;
         const bool valid = c < c1;
         const float lbv = valid ? lbrow[c] : kInf;
         bool pass = valid && (lbv <= thr);
-        if (pass) {
-            for (int t = 0; t < b.S; ++t) pass = pass && (seeds[t] != c);
+        if (__any_sync(0xffffffffu, pass)) {
+            if (pass) {
+                for (int t = 0; t < b.S; ++t) pass = pass && (seeds[t] != c);
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, pass);
+            if (pass) {
+                const int slot = cnt1 + __popc(m & ((1u << lane) - 1));
+                surv_c[slot] = c;
+                surv_v[slot] = lbv;
+            }
+            cnt1 += __popc(m);
         }
-        unsigned m = __ballot_sync(0xffffffffu, pass);
-        pk += __popc(m);
-        while (m) {
-            const int src = __ffs(m) - 1;
-            m &= m - 1;
-            const int cc = __shfl_sync(0xffffffffu, c, src);
-            float v = __shfl_sync(0xffffffffu, lbv, src);
-            if (b.lbi_inline) v = warp_lb_improved<P, MT>(b.db + (int64_t)cc * n, Qv, n, b.w, scratch, vec);
+    }
+    __syncwarp();
+    const unsigned long long pk = (unsigned long long)cnt1;
+    // phase 2: LB_Improved of each survivor, the next candidate's chunk
+    // prefetched while the current one is processed; survivors are kept in
+    // place (write index <= read index)
+    int cnt = 0;
+    if (b.lbi_inline) {
+        LbiChunk<MT> cur, nxt;
+        if (cnt1 > 0) lbi_load_chunk<MT>(nxt, b.db + (int64_t)surv_c[0] * n, n, vec);
+        for (int e = 0; e < cnt1; ++e) {
+            const int cc = surv_c[e];
+            cur = nxt;
+            if (e + 1 < cnt1) lbi_load_chunk<MT>(nxt, b.db + (int64_t)surv_c[e + 1] * n, n, vec);
+            const float v = warp_lb_improved<P, MT>(b.db + (int64_t)cc * n, Qv, n, w, scratch, vec,
+                                                    MT > 0 ? &cur : nullptr);
             if (v <= thr) {
                 if (lane == 0) {
                     surv_c[cnt] = cc;
@@ -674,12 +727,15 @@ __global__ void __launch_bounds__(256, 3) k_lbi_filter(CascadeBufs b, bool vec) 
                 }
                 ++cnt;
             }
+            __syncwarp();
         }
+    } else {
+        cnt = cnt1;
     }
     unsigned long long base = 0;
     if (lane == 0 && cnt > 0) base = atomicAdd(b.pair_count, (unsigned long long)cnt);
     base = __shfl_sync(0xffffffffu, base, 0);
-    const int64_t sub = ((int64_t)q * gridDim.x + sg) * nw + wid;
+    const int64_t sub = ((int64_t)q * gridDim.y + sg) * nw + wid;
     if (lane == 0) {
         b.seg_start[sub] = (int32_t)base;
         b.seg_count[sub] = cnt;
@@ -714,7 +770,7 @@ static void lbi_filter_go(const CascadeBufs &b, bool vec, cudaStream_t s) {
     const int64_t per_warp = (int64_t)lbi_scratch_floats(b.n, b.w) * sizeof(float);
     const int64_t per_query = (int64_t)lbi_query_floats(b.n) * sizeof(float);
     const size_t smem = (size_t)per_query + (size_t)b.S * 4 + 64 + (size_t)nw * (per_warp + 8 * (b.seg_len / nw + 32));
-    const dim3 grid(b.nseg / nw, b.Q);
+    const dim3 grid(b.Q, b.nseg / nw);
     cudaFuncSetAttribute(k_lbi_filter<P, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_lbi_filter<P, MT><<<grid, nw * 32, smem, s>>>(b, vec);
 }
