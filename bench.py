@@ -179,8 +179,11 @@ def roofline(prof, a, steps, peaks, stats):
     alu_peak = sms * 128 * clock / 1e12  # fp32 lane-ops per second, T
     share = {k: round(v["ms"] / total, 4) for k, v in stages.items()}
     if dom == "lb_keogh":
-        # 4 fp32 ops per (query, candidate, index): 2 subtractions, a 3-input max, an add/fma
-        work = a.Q * a.N * a.n * 4.0 / 1e12
+        # 4 fp32 ops per (query, candidate, index): 2 subtractions, a 3-input max,
+        # an add/fma; with the piecewise-sum pre-filter the index runs over the
+        # d = n/8 part sums instead of the n values
+        d = a.n // 8 if a.n >= 64 else a.n
+        work = a.Q * a.N * d * 4.0 / 1e12
         achieved = work / (ms / 1e3)
         return {"kernel": "k_lbk_tile", "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Top/s",
                 "frac": achieved / alu_peak, "traffic": None, "ms_per_launch": ms, "stage_share": share,
@@ -194,14 +197,18 @@ def roofline(prof, a, steps, peaks, stats):
                 "cells_per_launch": cells, "stage_share": share,
                 "peak_note": "%d SMs x 128 fp32 lanes x %.0f MHz (max SM clock)" % (sms, clock / 1e6)}
     if dom == "lb_improved":
-        # LB_Improved of each LB_Keogh survivor: 11 fp32 ops per index (clamp 2,
-        # first term 2, envelope 3 (the paper's 3n comparisons), second term 4)
-        surv = stats.get("candidates", 0) - stats.get("seeds", 0) - stats.get("pruned_keogh", 0)
-        work = surv * a.n * 11.0 / 1e12
-        achieved = work / (ms / 1e3) if surv > 0 else None
+        # the filter stage: a compare per scanned bound, LB_Keogh (4 fp32 ops
+        # per index) of each piecewise-sum survivor, and LB_Improved's second
+        # pass (7 more per index: envelope 3 -- the paper's 3n comparisons --
+        # and second term 4) of each LB_Keogh survivor
+        scanned = stats.get("candidates", 0) - stats.get("seeds", 0)
+        pd_surv = scanned - stats.get("pruned_summary", 0)
+        lbk_surv = pd_surv - stats.get("pruned_keogh", 0)
+        ops = scanned * 1.0 + pd_surv * a.n * 4.0 + lbk_surv * a.n * 7.0
+        achieved = ops / 1e12 / (ms / 1e3) if scanned > 0 else None
         return {"kernel": "k_lbi_filter", "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Top/s",
                 "frac": (achieved / alu_peak) if achieved else None, "traffic": None, "ms_per_launch": ms,
-                "pairs_per_launch": surv, "stage_share": share,
+                "lb_keogh_pairs": pd_surv, "lb_improved_pairs": lbk_surv, "stage_share": share,
                 "peak_note": "%d SMs x 128 fp32 lanes x %.0f MHz (max SM clock)" % (sms, clock / 1e6)}
     return {"kernel": dom, "bound": "alu", "achieved": None, "peak": alu_peak, "unit": "Top/s", "frac": None,
             "traffic": None, "ms_per_launch": ms, "stage_share": share}

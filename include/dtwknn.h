@@ -60,6 +60,7 @@ typedef enum {
 typedef struct {
     int64_t candidates;      /* (query, candidate) pairs: Q * N */
     int64_t seeds;           /* pairs whose DTW was computed first to seed the threshold */
+    int64_t pruned_summary;  /* pairs discarded by the piecewise-sum bound (Sec. 9) */
     int64_t pruned_keogh;    /* pairs discarded by LB_Keogh */
     int64_t pruned_improved; /* pairs discarded by LB_Improved */
     int64_t dtw_computed;    /* non-seed pairs whose DTW was started */
@@ -72,8 +73,12 @@ typedef struct {
     int32_t mode;  /* a dtw_mode */
     float slack;   /* relative pruning slack; the kernels use the larger of this
                       and the worst-case fp32 rounding bound of the compared sums */
-    int32_t seeds; /* candidates per query (lowest LB_Keogh first) whose DTW seeds the
+    int32_t seeds; /* candidates per query (lowest bound first) whose DTW seeds the
                       threshold; 0 selects the default (16, at least k, at most N) */
+    int32_t parts; /* parts d of the piecewise-sum bound (Sec. 9) computed for every pair
+                      before LB_Keogh, which then runs only on its survivors; 0 selects
+                      the default (n / 8 when n >= 64, else off), -1 disables it (LB_Keogh
+                      of every pair), otherwise 1 <= d <= n */
 } dtw_options;
 
 /*
@@ -94,6 +99,17 @@ dtw_status dtw_envelope(const float *y, int64_t count, int32_t n, int32_t w,
  */
 dtw_status lb_keogh(const float *cand, int64_t N, const float *U, const float *L,
                     int32_t n, int32_t p, float *out, void *stream);
+
+/*
+ * Piecewise-sum bound of Sec. 9 for every candidate x = cand[c] against one
+ * query envelope U, L: with the cover of d parts C_j (floor(n/d) indices each,
+ * the last part takes the rest) and D_j the distance from sum_{C_j} x to
+ * [sum_{C_j} L, sum_{C_j} U], out[c] = sum_j D_j (p = 1, the paper's bound) or
+ * sqrt(sum_j D_j^2 / max_j |C_j|) (p = 2).  Both are at most LB_Keogh_p.
+ * 1 <= d <= n.  out is [N].
+ */
+dtw_status lb_piecewise(const float *cand, int64_t N, const float *U, const float *L,
+                        int32_t n, int32_t d, int32_t p, float *out, void *stream);
 
 /*
  * LB_Improved_p(x, y) with LB_Improved_p^p = LB_Keogh_p(x, y)^p +

@@ -60,6 +60,8 @@ def _load():
             lib.oracle_lb_keogh_pow.restype = ctypes.c_double
             lib.oracle_lb_improved_pow.argtypes = [_f32p, _f32p, _f64p, _f64p, _i64, _i64, ctypes.c_int, _f64p]
             lib.oracle_lb_improved_pow.restype = ctypes.c_double
+            lib.oracle_lb_piecewise_pow.argtypes = [_f32p, _f64p, _f64p, _i64, _i64, ctypes.c_int]
+            lib.oracle_lb_piecewise_pow.restype = ctypes.c_double
             lib.oracle_dtw_pow.argtypes = [_f32p, _f32p, _i64, _i64, ctypes.c_int]
             lib.oracle_dtw_pow.restype = ctypes.c_double
             lib.oracle_knn_bruteforce.argtypes = [_f32p, _i64, _f32p, _i64, _i64, ctypes.c_int, ctypes.c_int, _i64p, _f64p]
@@ -136,6 +138,17 @@ def lb_improved_pow(x, y, w: int, p: int, with_first: bool = False):
     r = lib.oracle_lb_improved_pow(_ptr(x, _f32p), _ptr(y, _f32p), _ptr(U, _f64p), _ptr(L, _f64p),
                                    x.shape[-1], _check_w(w), int(p), ctypes.byref(first))
     return (r, first.value) if with_first else r
+
+
+def lb_piecewise_pow(x, y, w: int, d: int, p: int) -> float:
+    """Piecewise-sum bound of Sec. 9 (p-th power), cover of d parts."""
+    lib = _load()
+    x = _f32(x)
+    n = x.shape[-1]
+    if not 1 <= d <= n:
+        raise ValueError("1 <= d <= n required")
+    U, L = envelope(y, w)
+    return lib.oracle_lb_piecewise_pow(_ptr(x, _f32p), _ptr(U, _f64p), _ptr(L, _f64p), n, int(d), int(p))
 
 
 def dtw_pow(x, y, w: int, p: int) -> float:

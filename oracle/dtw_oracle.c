@@ -210,6 +210,42 @@ double oracle_dtw_pow(const float *x, const float *y, int64_t n, int64_t w, int 
     return r;
 }
 
+/*
+ * Piecewise-sum bound of Sec. 9.  P_d(x) = (sum_{i in C_j} x_i)_j over the
+ * cover C_j = [1 + (j-1) floor(n/d), j floor(n/d)] for j < d and
+ * C_d = [1 + (d-1) floor(n/d), n].  With D_j = d(P_d(x)_j, [P_d(L)_j, P_d(U)_j])
+ * (U = U(y), L = L(y)):
+ *   p = 1: sum_j D_j  (the paper's bound, <= LB_Keogh_1(x, y));
+ *   p = 2: sum_j D_j^2 / max_j |C_j|  (reading for p = 2: D_j is at most the
+ *          sum of the LB_Keogh terms over C_j, so D_j^2 / |C_j| is at most
+ *          their sum of squares by Cauchy-Schwarz; the common denominator
+ *          max_j |C_j| only weakens it).
+ * Returns the p-th power of the bound.  Requires 1 <= d <= n.
+ */
+double oracle_lb_piecewise_pow(const float *x, const double *U, const double *L, int64_t n, int64_t d, int p)
+{
+    const int64_t s = n / d;
+    const int64_t smax = n - (d - 1) * s; /* the last part takes the rest */
+    double total = 0.0;
+    for (int64_t j = 0; j < d; ++j) {
+        const int64_t lo = j * s;
+        const int64_t hi = (j == d - 1) ? n : (j + 1) * s;
+        double px = 0.0, pu = 0.0, pl = 0.0;
+        for (int64_t i = lo; i < hi; ++i) {
+            px += (double)x[i];
+            pu += U[i];
+            pl += L[i];
+        }
+        double dj = 0.0;
+        if (px > pu)
+            dj = px - pu;
+        else if (px < pl)
+            dj = pl - px;
+        total += (p == 1) ? dj : dj * dj;
+    }
+    return (p == 1) ? total : total / (double)smax;
+}
+
 /* ---------------------------------------------------------------------- */
 /* k nearest neighbours                                                    */
 /* ---------------------------------------------------------------------- */

@@ -40,6 +40,7 @@ class Stats(ctypes.Structure):
     _fields_ = [
         ("candidates", ctypes.c_int64),
         ("seeds", ctypes.c_int64),
+        ("pruned_summary", ctypes.c_int64),
         ("pruned_keogh", ctypes.c_int64),
         ("pruned_improved", ctypes.c_int64),
         ("dtw_computed", ctypes.c_int64),
@@ -64,7 +65,8 @@ class Profile(ctypes.Structure):
 
 
 class Options(ctypes.Structure):
-    _fields_ = [("mode", ctypes.c_int32), ("slack", ctypes.c_float), ("seeds", ctypes.c_int32)]
+    _fields_ = [("mode", ctypes.c_int32), ("slack", ctypes.c_float), ("seeds", ctypes.c_int32),
+                ("parts", ctypes.c_int32)]
 
 
 _vp = ctypes.c_void_p
@@ -76,6 +78,7 @@ _f32 = ctypes.c_float
 SIGNATURES = {
     "dtw_envelope": [_vp, _i64, _i32, _i32, _vp, _vp, _vp],
     "lb_keogh": [_vp, _i64, _vp, _vp, _i32, _i32, _vp, _vp],
+    "lb_piecewise": [_vp, _i64, _vp, _vp, _i32, _i32, _i32, _vp, _vp],
     "lb_improved": [_vp, _i64, _vp, _vp, _vp, _i32, _i32, _i32, _vp, _vp],
     "dtw_band": [_vp, _vp, _i64, _i32, _i32, _i32, _i32, _f32, _vp, _vp],
     "dtw_band_noalloc": [_vp, _vp, _i64, _i32, _i32, _i32, _i32, _f32, _vp, _vp],

@@ -15,7 +15,8 @@ import torch
 
 from . import _native as N
 
-__all__ = ["dtw_envelope", "lb_keogh", "lb_improved", "dtw_band", "knn_search", "DtwError", "version"]
+__all__ = ["dtw_envelope", "lb_keogh", "lb_piecewise", "lb_improved", "dtw_band", "knn_search", "DtwError",
+           "version"]
 
 DtwError = N.DtwError
 version = N.version
@@ -68,6 +69,21 @@ def lb_keogh(cand: torch.Tensor, U: torch.Tensor, L: torch.Tensor, p: int, out: 
     return out
 
 
+def lb_piecewise(cand: torch.Tensor, U: torch.Tensor, L: torch.Tensor, d: int, p: int,
+                 out: torch.Tensor | None = None):
+    """Piecewise-sum bound of Sec. 9 (d parts) of every row of cand [N, n] against one envelope."""
+    cand = _cuda_f32(cand, "cand")
+    U = _cuda_f32(U, "U")
+    L = _cuda_f32(L, "L")
+    n = cand.shape[-1]
+    if U.numel() != n or L.numel() != n:
+        raise ValueError("U and L must have n = %d elements" % n)
+    out = torch.empty(cand.shape[0], device=cand.device, dtype=torch.float32) if out is None else out
+    N.check(N.lib.lb_piecewise(_ptr(cand), cand.shape[0], _ptr(U), _ptr(L), n, int(d), int(p), _ptr(out),
+                               _stream()))
+    return out
+
+
 def lb_improved(cand: torch.Tensor, q: torch.Tensor, U: torch.Tensor, L: torch.Tensor, w: int, p: int,
                 out: torch.Tensor | None = None):
     """LB_Improved_p of every row of cand [N, n] against query q [n] with envelope U, L (Sec. 8)."""
@@ -108,7 +124,7 @@ def dtw_band(x: torch.Tensor, y: torch.Tensor, w: int, p: int, threshold: float 
 
 
 def knn_search(db: torch.Tensor, queries: torch.Tensor, w: int, p: int, k: int = 1, *, mode: str = "improved",
-               slack: float = 1e-6, seeds: int = 0, out_idx: torch.Tensor | None = None,
+               slack: float = 1e-6, seeds: int = 0, parts: int = 0, out_idx: torch.Tensor | None = None,
                out_dist: torch.Tensor | None = None, return_stats: bool = False):
     """Exact k nearest neighbours of each query row under DTW_p with band w (Sec. 7-8).
 
@@ -132,7 +148,7 @@ def knn_search(db: torch.Tensor, queries: torch.Tensor, w: int, p: int, k: int =
         out_dist = torch.empty((Q, k), dtype=torch.float32, device=dev, pin_memory=not queries.is_cuda and torch.cuda.is_available())
     if mode not in _MODES:
         raise ValueError("mode must be one of %s" % sorted(_MODES))
-    opt = N.Options(_MODES[mode], float(slack), int(seeds))
+    opt = N.Options(_MODES[mode], float(slack), int(seeds), int(parts))
     st = N.Stats()
     N.check(N.lib.knn_search_ex(_ptr(db), db.shape[0], _ptr(queries), Q, n, int(w), int(p), int(k),
                                 ctypes.byref(opt), _ptr(out_idx), _ptr(out_dist),

@@ -226,6 +226,21 @@ dtw_status lb_keogh(const float *cand, int64_t N, const float *U, const float *L
     return DTW_OK;
 }
 
+dtw_status lb_piecewise(const float *cand, int64_t N, const float *U, const float *L, int32_t n, int32_t d,
+                        int32_t p, float *out, void *stream) {
+    g_err[0] = 0;
+    dtw_status st = check_common(n, 0, p);
+    if (st != DTW_OK) return st;
+    if (d < 1 || d > n) return fail(DTW_ERR_INVALID_ARG, "d=%d outside [1, n=%d]", d, n);
+    if (N < 0) return fail(DTW_ERR_INVALID_ARG, "N=%lld must be >= 0", (long long)N);
+    if (N == 0) return DTW_OK;
+    if (!cand || !U || !L || !out) return fail(DTW_ERR_INVALID_ARG, "null pointer");
+    void *ws = nullptr;
+    if ((st = workspace_get(((size_t)N * d + 2 * (size_t)d) * sizeof(float) + 256, &ws)) != DTW_OK) return st;
+    CUDA_TRY(launch_lbp_single(cand, N, U, L, n, d, p, out, (float *)ws, (cudaStream_t)stream));
+    return DTW_OK;
+}
+
 dtw_status lb_improved(const float *cand, int64_t N, const float *q, const float *U, const float *L,
                        int32_t n, int32_t w, int32_t p, float *out, void *stream) {
     g_err[0] = 0;
@@ -298,8 +313,9 @@ dtw_status knn_search_ex(const float *db, int64_t N, const float *queries, int64
     if (N < 0 || N > INT32_MAX / 2) return fail(DTW_ERR_INVALID_ARG, "N=%lld out of range", (long long)N);
     if (Q < 0 || Q > INT32_MAX / 2) return fail(DTW_ERR_INVALID_ARG, "Q=%lld out of range", (long long)Q);
     if (k < 1 || k > DTW_MAX_K) return fail(DTW_ERR_INVALID_ARG, "k=%d outside [1, %d]", k, DTW_MAX_K);
-    dtw_options o{DTW_MODE_IMPROVED, 1e-6f, 0};
+    dtw_options o{DTW_MODE_IMPROVED, 1e-6f, 0, 0};
     if (opt) o = *opt;
+    if (o.parts < -1 || o.parts > n) return fail(DTW_ERR_INVALID_ARG, "parts=%d outside [-1, n=%d]", o.parts, n);
     if (o.mode < DTW_MODE_IMPROVED || o.mode > DTW_MODE_NOPRUNE)
         return fail(DTW_ERR_INVALID_ARG, "mode=%d unknown", o.mode);
     if (!(o.slack >= 0.0f) || std::isinf(o.slack)) return fail(DTW_ERR_INVALID_ARG, "slack must be finite and >= 0");
@@ -312,6 +328,10 @@ dtw_status knn_search_ex(const float *db, int64_t N, const float *queries, int64
     const int we = w < n - 1 ? w : n - 1;
     const DtwGeom g = dtw_geom(n, we);
     const float slack = fmaxf(o.slack, auto_slack(n));
+    // piecewise-sum pre-filter (Sec. 9): d parts
+    const int parts = o.parts == 0 ? (n >= 64 ? n / 8 : -1) : o.parts;
+    const bool summary = parts > 0 && N > 0;
+    const PartGeom pg = part_geom(n, summary ? parts : 1);
     int S = o.seeds > 0 ? o.seeds : 16;
     if (S < k) S = k;
     if (S > 32) S = 32;
@@ -337,7 +357,7 @@ dtw_status knn_search_ex(const float *db, int64_t N, const float *queries, int64
 
     auto layout = [&](Carve &cv) {
         struct L {
-            float *db, *q, *U, *L, *copies, *lb, *seed_res, *pair_lbi, *pair_res, *out_dist, *lbi_u;
+            float *db, *q, *U, *L, *copies, *lb, *seed_res, *pair_lbi, *pair_res, *out_dist, *lbi_u, *PX, *PU, *PL;
             Pair *seed_pairs, *pairs, *pairs_u;
             int32_t *qcount, *qstart;
             uint32_t *gmin, *bsf;
@@ -351,6 +371,9 @@ dtw_status knn_search_ex(const float *db, int64_t N, const float *queries, int64
         l.L = cv.take<float>((size_t)Qc * n);
         l.copies = cv.take<float>((size_t)Qc * 4 * g.ylen);
         l.lb = cv.take<float>((size_t)Qc * Nc);
+        l.PX = summary ? cv.take<float>((size_t)N * parts) : nullptr;
+        l.PU = summary ? cv.take<float>((size_t)Qc * parts) : nullptr;
+        l.PL = summary ? cv.take<float>((size_t)Qc * parts) : nullptr;
         l.tile_min = cv.take<unsigned long long>((size_t)Qc * lbk_tiles((int)Nc));
         l.seed_pairs = cv.take<Pair>((size_t)Qc * S);
         l.seed_res = cv.take<float>((size_t)Qc * S);
@@ -392,6 +415,12 @@ dtw_status knn_search_ex(const float *db, int64_t N, const float *queries, int64
     unsigned long long *counters = l.misc + 8;
     unsigned long long *seed_counters = l.misc + 16;
     CUDA_TRY(cudaMemsetAsync(counters, 0, 2 * CNT_NUM * sizeof(unsigned long long), s));
+    unsigned *xmax_bits = reinterpret_cast<unsigned *>(l.misc + 24);
+    if (summary) {
+        // part sums of the database rows, once per call
+        CUDA_TRY(cudaMemsetAsync(xmax_bits, 0, sizeof(unsigned long long), s));
+        CUDA_TRY(launch_summarize(dbd, N, n, parts, l.PX, xmax_bits, s));
+    }
 
     for (int64_t q0 = 0; q0 < Q; q0 += Qc) {
         const int qn = (int)((Q - q0) < Qc ? (Q - q0) : Qc);
@@ -441,6 +470,8 @@ dtw_status knn_search_ex(const float *db, int64_t N, const float *queries, int64
         b.qstart = l.qstart;
         b.pair_total = l.misc + 4;
         b.lbi_inline = o.mode == DTW_MODE_IMPROVED ? 1 : 0;
+        b.summary = summary ? 1 : 0;
+        b.summary_scale = (summary && p == 2) ? (float)pg.smax : 1.0f;
         b.pairs = l.pairs;
         b.pair_lbi = l.pair_lbi;
         b.pair_res = l.pair_res;
@@ -458,7 +489,13 @@ dtw_status knn_search_ex(const float *db, int64_t N, const float *queries, int64
         if (N > 0) {
             {
                 StageTimer tm(DTW_STAGE_LB_KEOGH, s);
-                CUDA_TRY(launch_lbk_tile(dbd, (int)N, l.U, l.L, qn, n, p, l.lb, l.tile_min, s));
+                if (summary) {
+                    // piecewise-sum bound of every pair (the tile kernel on the d part sums)
+                    CUDA_TRY(launch_query_summary(l.U, l.L, qn, n, parts, xmax_bits, l.PU, l.PL, 1, s));
+                    CUDA_TRY(launch_lbk_tile(l.PX, (int)N, l.PU, l.PL, qn, parts, p, l.lb, l.tile_min, s));
+                } else {
+                    CUDA_TRY(launch_lbk_tile(dbd, (int)N, l.U, l.L, qn, n, p, l.lb, l.tile_min, s));
+                }
             }
             {
                 StageTimer tm(DTW_STAGE_SEED_SELECT, s);
@@ -525,7 +562,13 @@ dtw_status knn_search_ex(const float *db, int64_t N, const float *queries, int64
             const int64_t seeds = N > 0 ? Q * (int64_t)S : 0;
             stats->candidates = Q * N;
             stats->seeds = seeds;
-            stats->pruned_keogh = Q * N - seeds - (int64_t)h[CNT_KEOGH_PASS];
+            if (summary) {
+                stats->pruned_summary = Q * N - seeds - (int64_t)h[CNT_SUMMARY_PASS];
+                stats->pruned_keogh = (int64_t)h[CNT_SUMMARY_PASS] - (int64_t)h[CNT_KEOGH_PASS];
+            } else {
+                stats->pruned_summary = 0;
+                stats->pruned_keogh = Q * N - seeds - (int64_t)h[CNT_KEOGH_PASS];
+            }
             stats->pruned_improved = (int64_t)h[CNT_KEOGH_PASS] - (int64_t)h[CNT_LBI_PASS] + (int64_t)h[CNT_DTW_SKIP];
             stats->dtw_computed = (int64_t)h[CNT_DTW_COMPUTED];
             stats->dtw_abandoned = (int64_t)h[CNT_DTW_ABANDONED];

@@ -96,6 +96,29 @@ cudaError_t launch_lbk_tile(const float *db, int N, const float *U, const float 
                             int p, float *lb, unsigned long long *tile_min, cudaStream_t s);
 int lbk_tiles(int N);  // candidate tiles of the all-pairs kernel
 
+// Piecewise-sum bound (Sec. 9): cover of d parts, floor(n/d) indices each,
+// the last part takes the rest.
+struct PartGeom {
+    int d, s, smax;
+};
+inline PartGeom part_geom(int n, int d) {
+    PartGeom g;
+    g.d = d;
+    g.s = n / d;
+    g.smax = n - (d - 1) * g.s;
+    return g;
+}
+// PX[c][j] = sum of db row c over part j; xmax_bits = max |x| (float bits).
+cudaError_t launch_summarize(const float *db, int64_t N, int n, int d, float *PX, unsigned *xmax_bits,
+                             cudaStream_t s);
+// PU[q][j], PL[q][j]: part sums of U and L, widened (when widen != 0) by the
+// worst-case fp32 rounding of the part sums so the fp32 bound never exceeds
+// the exact one.
+cudaError_t launch_query_summary(const float *U, const float *L, int64_t Q, int n, int d,
+                                 const unsigned *xmax_bits, float *PU, float *PL, int widen, cudaStream_t s);
+cudaError_t launch_lbp_single(const float *cand, int64_t N, const float *U, const float *L, int n, int d, int p,
+                              float *out, float *scratch, cudaStream_t s);
+
 // One (query, candidate) pair for the LB_Improved and DTW stages.
 struct Pair {
     int32_t q;
@@ -134,7 +157,9 @@ struct CascadeBufs {
     int32_t *qcount;      // [Q], zeroed before the filter
     int32_t *qstart;      // [Q]
     unsigned long long *pair_total;  // pairs after grouping
-    int lbi_inline;       // the filter computes LB_Improved itself (warp per pair)
+    int lbi_inline;       // the filter computes LB_Improved (warp per pair)
+    int summary;          // the matrix holds the piecewise-sum bound; LB_Keogh is computed in the filter
+    float summary_scale;  // max_j |C_j| for p = 2 (matrix units), 1 for p = 1
     int64_t pair_cap;
     unsigned long long *pair_count;
     int seg_len, nseg;    // nseg: sub-segments per query (segments x filter warps)
@@ -190,6 +215,7 @@ enum {
     CNT_DTW_COMPUTED = 3,   // listed pairs whose DTW was started
     CNT_DTW_ABANDONED = 4,  // of which abandoned early
     CNT_DTW_ROWS = 5,       // DP rows evaluated
+    CNT_SUMMARY_PASS = 6,   // non-seed pairs with piecewise-sum bound <= thr
     CNT_NUM = 8
 };
 

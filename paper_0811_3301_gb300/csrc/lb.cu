@@ -417,9 +417,14 @@ __device__ __forceinline__ void lbi_load_chunk(LbiChunk<MT> &ch, const float *__
     }
 }
 
+// Returns LB_Improved^p, or LB_Keogh^p alone when !do_lbi or when LB_Keogh^p
+// already exceeds keogh_thr (the second pass is then skipped); *lbk_out
+// receives LB_Keogh^p.
 template <int P, int MT>
 __device__ __forceinline__ float warp_lb_improved(const float *__restrict__ x, const LbiQuery<MT> &Qv, int n, int w,
-                                                  float *scratch, bool vec, const LbiChunk<MT> *pre = nullptr) {
+                                                  float *scratch, bool vec, const LbiChunk<MT> *pre = nullptr,
+                                                  bool do_lbi = true, float keogh_thr = kInf,
+                                                  float *lbk_out = nullptr) {
     const int lane = threadIdx.x & 31;
     const LbiGeom g = lbi_geom(n);
     const int m = MT > 0 ? MT : g.m;
@@ -452,6 +457,12 @@ __device__ __forceinline__ float warp_lb_improved(const float *__restrict__ x, c
                 h[t] = NEG;
             }
         }
+        {
+            const float lbk = warp_sum(acc1);
+            if (lbk_out) *lbk_out = lbk;
+            if (!do_lbi || lbk > keogh_thr) return lbk;
+            acc1 = (lane == 0) ? lbk : 0.0f;
+        }
         if (2 * w < MT) {
             // windows can lie inside a chunk: keep h for the direct scan
 #pragma unroll
@@ -483,6 +494,12 @@ __device__ __forceinline__ float warp_lb_improved(const float *__restrict__ x, c
             }
             Hs[t * 32 + lane] = hv;
             Pre[t * W + lane] = make_float2(pmax, pmin);
+        }
+        {
+            const float lbk = warp_sum(acc1);
+            if (lbk_out) *lbk_out = lbk;
+            if (!do_lbi || lbk > keogh_thr) return lbk;
+            acc1 = (lane == 0) ? lbk : 0.0f;
         }
         float smax = NEG, smin = POS;
         for (int t = m - 1; t >= 0; --t) {
@@ -670,7 +687,7 @@ __global__ void __launch_bounds__(256, 3) k_lbi_filter(CascadeBufs b, bool vec) 
     float *surv_v = reinterpret_cast<float *>(surv_c + per_warp_cap);
     for (int t = threadIdx.x; t < b.S; t += blockDim.x) seeds[t] = b.seed_pairs[(int64_t)q * b.S + t].c;
     LbiQuery<MT> Qv;
-    if (b.lbi_inline) {
+    if (b.lbi_inline || b.summary) {
         lbi_load_query<MT>(Qv, b.queries + (int64_t)q * n, b.U + (int64_t)q * n, b.L + (int64_t)q * n, n, sq);
         lbi_init_scratch<MT>(scratch, n, b.w);
     }
@@ -681,6 +698,9 @@ __global__ void __launch_bounds__(256, 3) k_lbi_filter(CascadeBufs b, bool vec) 
     // contiguous block of the pair list (sub-segment (q, sg, wid)).
     const float bq = (b.mode == DTW_MODE_NOPRUNE) ? kInf : load_threshold(b.bsf + q);
     const float thr = bq * (1.0f + b.slack);
+    // the matrix holds LB_Keogh^p, or the piecewise-sum bound in the units of
+    // sum_j D_j^p (for p = 2 the bound is that sum over max_j |C_j|)
+    const float thr_m = b.summary ? thr * b.summary_scale : thr;
     const int c0 = sg * b.seg_len;
     const int c1 = min(b.N, c0 + b.seg_len);
     const float *lbrow = b.lb + (int64_t)q * b.N;
@@ -691,7 +711,7 @@ __global__ void __launch_bounds__(256, 3) k_lbi_filter(CascadeBufs b, bool vec) 
         const int c = base + lane;
         const bool valid = c < c1;
         const float lbv = valid ? lbrow[c] : kInf;
-        bool pass = valid && (lbv <= thr);
+        bool pass = valid && (lbv <= thr_m);
         if (__any_sync(0xffffffffu, pass)) {
             if (pass) {
                 for (int t = 0; t < b.S; ++t) pass = pass && (seeds[t] != c);
@@ -711,15 +731,18 @@ __global__ void __launch_bounds__(256, 3) k_lbi_filter(CascadeBufs b, bool vec) 
     // prefetched while the current one is processed; survivors are kept in
     // place (write index <= read index)
     int cnt = 0;
-    if (b.lbi_inline) {
+    unsigned long long kp = 0;  // LB_Keogh survivors (summary mode)
+    if (b.lbi_inline || b.summary) {
         LbiChunk<MT> cur, nxt;
         if (cnt1 > 0) lbi_load_chunk<MT>(nxt, b.db + (int64_t)surv_c[0] * n, n, vec);
         for (int e = 0; e < cnt1; ++e) {
             const int cc = surv_c[e];
             cur = nxt;
             if (e + 1 < cnt1) lbi_load_chunk<MT>(nxt, b.db + (int64_t)surv_c[e + 1] * n, n, vec);
+            float lbk = 0.0f;
             const float v = warp_lb_improved<P, MT>(b.db + (int64_t)cc * n, Qv, n, w, scratch, vec,
-                                                    MT > 0 ? &cur : nullptr);
+                                                    MT > 0 ? &cur : nullptr, b.lbi_inline != 0, thr, &lbk);
+            kp += (lbk <= thr) ? 1 : 0;
             if (v <= thr) {
                 if (lane == 0) {
                     surv_c[cnt] = cc;
@@ -741,7 +764,12 @@ __global__ void __launch_bounds__(256, 3) k_lbi_filter(CascadeBufs b, bool vec) 
         b.seg_count[sub] = cnt;
         if (cnt) atomicAdd(b.qcount + q, cnt);
         if (b.counters) {
-            if (pk) atomicAdd(b.counters + CNT_KEOGH_PASS, pk);
+            if (b.summary) {
+                if (pk) atomicAdd(b.counters + CNT_SUMMARY_PASS, pk);
+                if (kp) atomicAdd(b.counters + CNT_KEOGH_PASS, kp);
+            } else if (pk) {
+                atomicAdd(b.counters + CNT_KEOGH_PASS, pk);
+            }
             if (cnt && b.mode != DTW_MODE_IMPROVED) atomicAdd(b.counters + CNT_LBI_PASS, (unsigned long long)cnt);
             if (cnt && b.lbi_inline) atomicAdd(b.counters + CNT_LBI_PASS, (unsigned long long)cnt);
         }

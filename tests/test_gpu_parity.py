@@ -103,6 +103,25 @@ def test_lb_keogh_and_improved(api, p, n, w):
         assert close(lbi[c], ri ** (1.0 / p)), (c, lbi[c], ri)
 
 
+@pytest.mark.parametrize("p", [1, 2])
+@pytest.mark.parametrize("n,d", [(1, 1), (37, 5), (128, 16), (181, 22), (256, 32), (256, 256), (1024, 128)])
+def test_lb_piecewise(api, p, n, d):
+    N = 200
+    X = synth.random_walks(N, n, seed=11 + n)
+    y = synth.random_walks(1, n, seed=12 + n, stream=synth.STREAM_QUERY)[0]
+    w = max(1, n // 10)
+    U, L = api.dtw_envelope(cuda(y), w)
+    got = api.lb_piecewise(cuda(X), U, L, d, p).cpu().numpy().astype(np.float64)
+    Uo, Lo = oracle.envelope(y, w)
+    for c in range(N):
+        ref = oracle.lb_piecewise_pow(X[c], y, w, d, p) ** (1.0 / p)
+        # fp32 part sums cancel: allow the absolute rounding of sums of |values|
+        scale = np.abs(X[c]).sum() + np.abs(Uo).sum() + np.abs(Lo).sum()
+        tol = REL * ref + 4 * (n // d + 1) * 6e-8 * scale + ABS
+        assert abs(got[c] - ref) <= tol, (c, got[c], ref)
+        assert got[c] <= oracle.lb_keogh_pow(X[c], y, w, p) ** (1.0 / p) * (1 + 1e-5) + tol
+
+
 # ---------------------------------------------------------------------------
 # DTW
 # ---------------------------------------------------------------------------
@@ -169,7 +188,8 @@ def _knn_case(api, db, queries, w, p, k, mode="improved", **kw):
     assert_knn(db, queries, w, p, k, idx, dist, ri, rd)
     Q, N = queries.shape[0], db.shape[0]
     assert st["candidates"] == Q * N
-    assert st["seeds"] + st["pruned_keogh"] + st["pruned_improved"] + st["dtw_computed"] == Q * N
+    assert (st["seeds"] + st["pruned_summary"] + st["pruned_keogh"] + st["pruned_improved"] + st["dtw_computed"]
+            == Q * N)
     return idx, dist, st
 
 
@@ -198,6 +218,18 @@ def test_knn_pruning_never_loses_the_neighbour(api):
     # an extreme slack prunes almost nothing and must give the same answer
     c = api.knn_search(cuda(db), cuda(qs), 6, 2, 5, slack=10.0)
     assert torch.equal(a[0], c[0]) and torch.equal(a[1], c[1])
+
+
+@pytest.mark.parametrize("parts", [-1, 0, 1, 8, 64])
+@pytest.mark.parametrize("mode", ["improved", "keogh"])
+def test_knn_piecewise_prefilter(api, parts, mode):
+    # the piecewise-sum pass before LB_Keogh changes no result
+    db = synth.random_walks(2500, 64, seed=13)
+    qs = synth.random_walks(8, 64, seed=13, stream=synth.STREAM_QUERY)
+    for p in (1, 2):
+        idx, dist, st = _knn_case(api, db, qs, 6, p, 2, mode=mode, parts=parts)
+        if parts == -1:
+            assert st["pruned_summary"] == 0
 
 
 @pytest.mark.parametrize("seeds", [1, 2, 32])

@@ -406,3 +406,50 @@ def test_cascades_equal_bruteforce(p):
             assert np.all(s1[:, 1] + s1[:, 2] + s1[:, 3] == 400)
             # same threshold trajectory, so LB_Improved never computes more DTWs
             assert np.all(s1[:, 1] == s0[:, 1]) and np.all(s1[:, 3] <= s0[:, 3])
+
+
+# ---------------------------------------------------------------------------
+# piecewise-sum bound (Sec. 9)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_piecewise_with_unit_parts_is_lb_keogh(p):
+    # d = n: every part is one index, so the bound is LB_Keogh itself
+    for x, y in zip(_walks(4, 37, 71), _walks(4, 37, 72)):
+        for w in (0, 3, 37):
+            assert oracle.lb_piecewise_pow(x, y, w, 37, p) == pytest.approx(oracle.lb_keogh_pow(x, y, w, p), rel=1e-13)
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_piecewise_single_part_closed_form(p):
+    # d = 1: |sum x - clip(sum x, sum L, sum U)|^p / n^(p-1)
+    for x, y in zip(_walks(4, 50, 73), _walks(4, 50, 74)):
+        U, L = oracle.envelope(y, 5)
+        sx = np.sum(x.astype(np.float64))
+        dd = abs(sx - np.clip(sx, L.sum(), U.sum()))
+        ref = dd if p == 1 else dd * dd / 50
+        assert oracle.lb_piecewise_pow(x, y, 5, 1, p) == pytest.approx(ref, rel=1e-12, abs=1e-12)
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_piecewise_is_below_lb_keogh_and_cover(p):
+    # the bound never exceeds LB_Keogh (Sec. 9 chain of inequalities); the
+    # cover: floor(n/d) per part, the last part takes the rest (checked with
+    # numpy sums over explicit index sets)
+    X, Y = _walks(10, 61, 75), _walks(10, 61, 76)
+    for x, y in zip(X, Y):
+        for w in (2, 6, 20):
+            U, L = oracle.envelope(y, w)
+            lbk = oracle.lb_keogh_pow(x, y, w, p)
+            for d in (1, 2, 7, 8, 30, 61):
+                v = oracle.lb_piecewise_pow(x, y, w, d, p)
+                assert v <= lbk * (1 + 1e-12) + 1e-12
+                s = 61 // d
+                parts = [list(range(j * s, (j + 1) * s)) for j in range(d - 1)] + [list(range((d - 1) * s, 61))]
+                smax = max(len(c) for c in parts)
+                tot = 0.0
+                for c in parts:
+                    px, pu, pl = x[c].astype(np.float64).sum(), U[c].sum(), L[c].sum()
+                    dj = max(px - pu, pl - px, 0.0)
+                    tot += dj if p == 1 else dj * dj
+                assert v == pytest.approx(tot if p == 1 else tot / smax, rel=1e-12, abs=1e-12)
