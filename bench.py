@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--k", type=int, default=1)
     ap.add_argument("--p", type=int, default=1)
     ap.add_argument("--seed", type=int, default=2)
+    ap.add_argument("--seeds", type=int, default=0, help="seed DTWs per query (0: library default)")
+    ap.add_argument("--parts", type=int, default=0, help="piecewise-sum parts (0: default n/8, -1: off)")
     ap.add_argument("--no-p2", action="store_true", help="skip the DTW_2 side measurement")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU baseline sample")
     return ap.parse_args()
@@ -248,13 +250,15 @@ def run_ours(a):
             dist.barrier()
             torch.cuda.synchronize()
 
+    kw = {"seeds": a.seeds, "parts": a.parts}
+
     def step(p):
-        return api.knn_search(db, qs, a.w, p, a.k)
+        return api.knn_search(db, qs, a.w, p, a.k, **kw)
 
     # pruning report (untimed): LB_Keogh alone vs LB_Keogh + LB_Improved
     pruning = {}
     for mode in ("keogh", "improved"):
-        _, _, st = api.knn_search(db, qs, a.w, a.p, a.k, mode=mode, return_stats=True)
+        _, _, st = api.knn_search(db, qs, a.w, a.p, a.k, mode=mode, return_stats=True, **kw)
         tot = max(1, st["candidates"])
         pruning[mode] = dict(st, pruned_fraction=round((st["pruned_keogh"] + st["pruned_improved"]) / tot, 6),
                              dtw_fraction=round((st["dtw_computed"] + st["seeds"]) / tot, 6))
@@ -288,7 +292,7 @@ def run_ours(a):
     clocks = sampler.summary(t_wall0, t_wall1) if sampler else None
 
     # DTW rows evaluated per step (for the DTW roofline): one extra stats run
-    _, _, st_main = api.knn_search(db, qs, a.w, a.p, a.k, return_stats=True)
+    _, _, st_main = api.knn_search(db, qs, a.w, a.p, a.k, return_stats=True, **kw)
 
     # DTW_2 side measurement (same workload, same timing method)
     p2 = None
@@ -317,14 +321,14 @@ def run_ours(a):
     oi = torch.empty((a.Q, a.k), dtype=torch.int64).pin_memory()
     od = torch.empty((a.Q, a.k), dtype=torch.float32).pin_memory()
     for _ in range(a.warmup):
-        api.knn_search(db, q_pin, a.w, a.p, a.k, out_idx=oi, out_dist=od)
+        api.knn_search(db, q_pin, a.w, a.p, a.k, out_idx=oi, out_dist=od, **kw)
     barrier()
     e2e_s = 0.0
     for i in range(a.steps):
         flush.fill_(float(i))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        api.knn_search(db, q_pin, a.w, a.p, a.k, out_idx=oi, out_dist=od)  # synchronous (host outputs)
+        api.knn_search(db, q_pin, a.w, a.p, a.k, out_idx=oi, out_dist=od, **kw)  # synchronous (host outputs)
         e2e_s += time.perf_counter() - t0
     te = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
     if world > 1:

@@ -197,6 +197,14 @@ __device__ __forceinline__ void dtw_cells_win(float (&D)[C], float xi, const flo
     }
 }
 
+// Cells K..C-1 of one row without a jump: used when the bottom padding E is
+// a compile-time constant (the common bands), so that the rows of a group
+// are one straight-line block the scheduler can interleave.
+template <int C, int P, int U, int E>
+__device__ __forceinline__ void dtw_row_win_fixed(float (&D)[C], float xi, const float (&yw)[C + 4]) {
+    dtw_cells_win<E, C, P, U>(D, xi, yw);
+}
+
 template <int C, int P, int U>
 __device__ __forceinline__ void dtw_row_win(float (&D)[C], float xi, const float (&yw)[C + 4], int e) {
     switch (e) {
@@ -220,7 +228,7 @@ __device__ __forceinline__ void dtw_row_win(float (&D)[C], float xi, const float
     dtw_cells_win<16, C, P, U>(D, xi, yw);
 }
 
-template <int C, int P>
+template <int C, int P, int E>
 __global__ void __launch_bounds__(kDtwThreads)
 k_dtw_reg4(DtwJob j, int e, int wl, bool xvec) {
     const int lane = threadIdx.x & 31;
@@ -276,10 +284,23 @@ k_dtw_reg4(DtwJob j, int e, int wl, bool xvec) {
                     x4.z = i + 2 < n ? __ldg(x + i + 2) : 0.0f;
                     x4.w = i + 3 < n ? __ldg(x + i + 3) : 0.0f;
                 }
-                dtw_row_win<C, P, 0>(D, x4.x, yw, e);
-                if (i + 1 < n) dtw_row_win<C, P, 1>(D, x4.y, yw, e);
-                if (i + 2 < n) dtw_row_win<C, P, 2>(D, x4.z, yw, e);
-                if (i + 3 < n) dtw_row_win<C, P, 3>(D, x4.w, yw, e);
+                if constexpr (E >= 0) {
+                    if (i + 4 <= n) {
+                        dtw_row_win_fixed<C, P, 0, E>(D, x4.x, yw);
+                        dtw_row_win_fixed<C, P, 1, E>(D, x4.y, yw);
+                        dtw_row_win_fixed<C, P, 2, E>(D, x4.z, yw);
+                        dtw_row_win_fixed<C, P, 3, E>(D, x4.w, yw);
+                    } else {
+                        dtw_row_win_fixed<C, P, 0, E>(D, x4.x, yw);
+                        if (i + 1 < n) dtw_row_win_fixed<C, P, 1, E>(D, x4.y, yw);
+                        if (i + 2 < n) dtw_row_win_fixed<C, P, 2, E>(D, x4.z, yw);
+                    }
+                } else {
+                    dtw_row_win<C, P, 0>(D, x4.x, yw, e);
+                    if (i + 1 < n) dtw_row_win<C, P, 1>(D, x4.y, yw, e);
+                    if (i + 2 < n) dtw_row_win<C, P, 2>(D, x4.z, yw, e);
+                    if (i + 3 < n) dtw_row_win<C, P, 3>(D, x4.w, yw, e);
+                }
                 if (j.abandon && (i & 4) && i + 4 < n) {
                     float mn = D[0];
 #pragma unroll

@@ -21,9 +21,19 @@ cudaError_t launch_dtw_p2(const DtwJob &j, const DtwGeom &g, cudaStream_t s) {
     if (!g.wide && g.C <= kDtwGroupMaxC) {
         const int64_t warps = (j.npairs + 31) / 32;
         const bool xvec = (j.n % 4 == 0) && ((reinterpret_cast<uintptr_t>(j.db) & 15) == 0);
+        // bands of 10 % of the common lengths get a compile-time bottom padding:
+        // (C, e) = (16, 3) w = 6, (32, 7) w = 12, (48, 11) w = 18, (64, 13) w = 25
+#define DTW_REG4_FIXED(CC, EE)                                                        \
+    if (g.C == CC && g.e == EE) {                                                     \
+        auto kern = k_dtw_reg4<CC, 2, EE>;                                          \
+        kern<<<blocks_for(kern, warps), kDtwThreads, 0, s>>>(j, g.e, g.wl, xvec);     \
+        return cudaGetLastError();                                                    \
+    }
+        DTW_REG4_FIXED(16, 3) DTW_REG4_FIXED(32, 7) DTW_REG4_FIXED(48, 11) DTW_REG4_FIXED(64, 13)
+#undef DTW_REG4_FIXED
 #define DTW_REG4_CASE(CC)                                                             \
     case CC: {                                                                        \
-        auto kern = k_dtw_reg4<CC, 2>;                                              \
+        auto kern = k_dtw_reg4<CC, 2, -1>;                                          \
         kern<<<blocks_for(kern, warps), kDtwThreads, 0, s>>>(j, g.e, g.wl, xvec);     \
         break;                                                                        \
     }

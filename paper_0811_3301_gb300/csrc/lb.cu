@@ -417,6 +417,32 @@ __device__ __forceinline__ void lbi_load_chunk(LbiChunk<MT> &ch, const float *__
     }
 }
 
+// Second-pass terms of one lane's chunk when pa0 = (-w) mod M = PA0 is a
+// compile-time constant: position t's window starts in chunk lane + D0 + fa at
+// position pa and ends in chunk lane + E0 + fb at position pb, with fa, fb,
+// pa, pb known at compile time, so every lookup is a fixed offset.
+template <int P, int MT, int PA0>
+__device__ __forceinline__ float lbi_pass3(const float2 *sufb, const float2 *preb, int W, const float2 (&mid)[2][2],
+                                           const LbiQuery<MT> &Qv, int cnt_in) {
+    constexpr int PB0 = (MT - PA0) & (MT - 1);
+    float acc2 = 0.0f;
+#pragma unroll
+    for (int t = 0; t < MT; ++t) {
+        constexpr int dummy = 0;
+        (void)dummy;
+        const bool fa = PA0 + t >= MT, fb = PB0 + t >= MT;
+        const int pa = fa ? PA0 + t - MT : PA0 + t;
+        const int pb = fb ? PB0 + t - MT : PB0 + t;
+        const float2 sa = sufb[pa * W + (fa ? 1 : 0)];
+        const float2 pv = preb[pb * W + (fb ? 1 : 0)];
+        const float2 md = mid[fa ? 1 : 0][fb ? 1 : 0];
+        const float uu = max3f(sa.x, pv.x, md.x);
+        const float ll = min3f(sa.y, pv.y, md.y);
+        if (t < cnt_in) acc2 = acc_dist<P>(acc2, Qv.yr[t], ll, uu);
+    }
+    return acc2;
+}
+
 // Returns LB_Improved^p, or LB_Keogh^p alone when !do_lbi or when LB_Keogh^p
 // already exceeds keogh_thr (the second pass is then skipped); *lbk_out
 // receives LB_Keogh^p.
@@ -552,17 +578,19 @@ __device__ __forceinline__ float warp_lb_improved(const float *__restrict__ x, c
                 }
                 mid[fa][fb] = r;
             }
-#pragma unroll
-        for (int t = 0; t < (MT > 0 ? MT : 1); ++t) {
-            const bool fa = pa0 + t >= m, fb = pb0 + t >= m;
-            const int pa = fa ? pa0 + t - m : pa0 + t;
-            const int pb = fb ? pb0 + t - m : pb0 + t;
-            const float2 sa = Suf[pa * W + PLc + D0 + (fa ? 1 : 0) + lane];
-            const float2 pv = Pre[pb * W + PLc + E0 + (fb ? 1 : 0) + lane];
-            const float2 md = fa ? (fb ? mid[1][1] : mid[1][0]) : (fb ? mid[0][1] : mid[0][0]);
-            const float uu = max3f(sa.x, pv.x, md.x);
-            const float ll = min3f(sa.y, pv.y, md.y);
-            if (t < cnt_in) acc2 = acc_dist<P>(acc2, Qv.yr[MT > 0 ? t : 0], ll, uu);
+        if constexpr (MT > 0) {
+            const float2 *sufb = Suf + PLc + D0 + lane;
+            const float2 *preb = Pre + PLc + E0 + lane;
+            switch (pa0) {
+#define LBI_PASS3_CASE(A)                                                                          \
+    case A:                                                                                        \
+        if constexpr (A < MT) acc2 = lbi_pass3<P, MT, A>(sufb, preb, W, mid, Qv, cnt_in);          \
+        break;
+                LBI_PASS3_CASE(0) LBI_PASS3_CASE(1) LBI_PASS3_CASE(2) LBI_PASS3_CASE(3)
+                LBI_PASS3_CASE(4) LBI_PASS3_CASE(5) LBI_PASS3_CASE(6) LBI_PASS3_CASE(7)
+#undef LBI_PASS3_CASE
+                default: break;
+            }
         }
     } else {
 #pragma unroll 1
