@@ -60,6 +60,14 @@ def parse():
     ap.add_argument("--parts", type=int, default=0, help="piecewise-sum parts (0: default n/8, -1: off)")
     ap.add_argument("--no-p2", action="store_true", help="skip the DTW_2 side measurement")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU baseline sample")
+    ap.add_argument("--workload", choices=["retrieval", "batched"], default="retrieval",
+                    help="retrieval: one length, one knn_search per step (default); batched: mixed-length "
+                         "batches against length buckets through the index")
+    ap.add_argument("--bucket-N", type=int, default=20_000, help="batched: series per length bucket")
+    ap.add_argument("--batch-Q", type=int, default=4096, help="batched: queries per batch")
+    ap.add_argument("--batch-ks", default="1,10", help="batched: neighbour counts, one run each")
+    ap.add_argument("--batch-arms", default="graph,streams,serial,per_query",
+                    help="batched: execution arms to time")
     return ap.parse_args()
 
 
@@ -364,6 +372,112 @@ def run_ours(a):
     return out
 
 
+def run_batched(a):
+    """Mixed-length batches through the index: 11 length buckets 64 * 2^(j/2)
+    (64 .. 2048) of `bucket_N` random walks each, `batch_Q` queries per batch
+    with lengths log-uniform in [64, 2048] snapped to the nearest bucket in log
+    space, w = floor(n / 10), DTW_2, one run per k.  Arms: the batch as one
+    CUDA graph (groups on concurrent streams, autotuned parameters), the same
+    without the graph, the groups serially, and one cascade per query (the
+    unbatched baseline)."""
+    import torch
+
+    from paper_0811_3301_gb300 import build
+
+    build.build()
+    from paper_0811_3301_gb300 import api
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    buckets = synth.bucket_lengths(64, 2048)
+    ix = api.DtwIndex(2)
+    for n in buckets:
+        ix.add_bucket(torch.from_numpy(synth.random_walks(a.bucket_N, n, seed=a.seed + 1000 + n)).to(dev))
+    lens = synth.snap_to_buckets(synth.log_uniform_lengths(a.batch_Q, 64, 2048, seed=a.seed), buckets)
+    qs = synth.mixed_queries(lens, seed=a.seed)
+    ws = lens // 10
+    flat_h = np.ascontiguousarray(np.concatenate(qs), dtype=np.float32)
+    flat = torch.from_numpy(flat_h).to(dev)
+    flush = torch.empty(256 * 2**20 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    arms_wanted = [x for x in a.batch_arms.split(",") if x]
+    arm_kw = {"graph": {"graph": True}, "streams": {}, "serial": {"serial": True}, "per_query": {"per_query": True}}
+    sampler = ClockSampler(0)
+    t_wall0 = time.time()
+    per_k = {}
+    launches = 0
+    for k in [int(x) for x in a.batch_ks.split(",") if x]:
+        t0 = time.perf_counter()
+        ref_i, ref_d = ix.search_flat(flat, lens, ws, k, autotune=True)
+        torch.cuda.synchronize()
+        tune_s = time.perf_counter() - t0
+        arms = {}
+        for arm in arms_wanted:
+            kw = arm_kw[arm]
+            steps = a.steps if arm != "per_query" else max(1, min(a.steps, 3))
+            for _ in range(a.warmup):
+                ix.search_flat(flat, lens, ws, k, **kw)
+            torch.cuda.synchronize()
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+            for i in range(steps):
+                flush.fill_(float(i))
+                evs[i][0].record(stream)
+                oi, od = ix.search_flat(flat, lens, ws, k, **kw)
+                evs[i][1].record(stream)
+            torch.cuda.synchronize()
+            ms = sum(x.elapsed_time(y) for x, y in evs)
+            same = bool(torch.equal(oi, ref_i) and torch.equal(od, ref_d))
+            arms[arm] = {"value": a.batch_Q * steps / (ms / 1e3), "unit": "queries/s", "ms_per_step": ms / steps,
+                         "steps": steps, "same_result_as_first_run": same}
+        # end to end: queries from pinned host memory, results to pinned host memory
+        fpin = torch.from_numpy(flat_h).pin_memory()
+        oi_h = torch.empty((a.batch_Q, k), dtype=torch.int64).pin_memory()
+        od_h = torch.empty((a.batch_Q, k), dtype=torch.float32).pin_memory()
+        for _ in range(a.warmup):
+            ix.search_flat(fpin, lens, ws, k, graph=True, out_idx=oi_h, out_dist=od_h)
+        e2e_s = 0.0
+        for i in range(a.steps):
+            flush.fill_(float(i))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ix.search_flat(fpin, lens, ws, k, graph=True, out_idx=oi_h, out_dist=od_h)
+            e2e_s += time.perf_counter() - t0
+        _, _, st = ix.search_flat(flat, lens, ws, k, return_stats=True)
+        tuning = {int(n): ix.get_tuning(int(n), int(n) // 10, k) for n in buckets}
+        per_k[k] = {"arms": arms, "autotune_seconds": tune_s, "tuning": tuning, "stats": st,
+                    "e2e": {"value": a.batch_Q * a.steps / e2e_s, "unit": "queries/s",
+                            "h2d_bytes_per_step": int(flat_h.nbytes) + a.batch_Q * 12,
+                            "d2h_bytes_per_step": a.batch_Q * k * 12}}
+    t_wall1 = time.time()
+    clocks = sampler.summary(t_wall0, t_wall1)
+    sampler.stop()
+    info = ix.info()
+    ks = sorted(per_k)
+    tot_q = sum(a.batch_Q * per_k[k]["arms"]["graph"]["steps"] for k in ks) if "graph" in arms_wanted else 0
+    tot_s = sum(per_k[k]["arms"]["graph"]["ms_per_step"] * per_k[k]["arms"]["graph"]["steps"] / 1e3 for k in ks) \
+        if "graph" in arms_wanted else 0
+    value = tot_q / tot_s if tot_s else None
+    e2e_v = len(ks) / sum(1.0 / per_k[k]["e2e"]["value"] for k in ks)
+    out = {
+        "metric": "exact k-NN DTW queries/s, mixed-length batches (LB_Improved cascade, one graph per batch)",
+        "value": value, "unit": "queries/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": (tot_s * 1e3 / sum(per_k[k]["arms"]["graph"]["steps"] for k in ks)) if tot_s else None,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded random walks)",
+        "config": {"workload": "batched mixed-length k-NN: %d queries/batch, lengths log-uniform in [64, 2048] "
+                               "snapped to 11 buckets of %d random walks, w = floor(n/10), DTW_2, k in %s"
+                               % (a.batch_Q, a.bucket_N, ks),
+                   "buckets": buckets, "queries_per_bucket": {int(n): int((lens == n).sum()) for n in buckets},
+                   "l2": "flushed between timed steps (256 MiB write)"},
+        "e2e": {"value": e2e_v, "unit": "queries/s",
+                "h2d_bytes_per_step": per_k[ks[0]]["e2e"]["h2d_bytes_per_step"],
+                "d2h_bytes_per_step": per_k[ks[0]]["e2e"]["d2h_bytes_per_step"]},
+        "vs_per_query": {k: (per_k[k]["arms"]["graph"]["value"] / per_k[k]["arms"]["per_query"]["value"])
+                         for k in ks if "graph" in per_k[k]["arms"] and "per_query" in per_k[k]["arms"]},
+        "per_k": per_k, "index": info, "clocks": clocks,
+    }
+    return out
+
+
 def run_reference(a):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -397,7 +511,12 @@ def run_reference(a):
 
 def main():
     a = parse()
-    out = run_reference(a) if a.impl == "reference" else run_ours(a)
+    if a.impl == "reference":
+        out = run_reference(a)
+    elif a.workload == "batched":
+        out = run_batched(a)
+    else:
+        out = run_ours(a)
     if out is not None:
         print(json.dumps(out))
     if int(os.environ.get("WORLD_SIZE", "1")) > 1 and a.impl == "ours":

@@ -204,6 +204,105 @@ dtw_status dtw_band_noalloc(const float *x, const float *y, int64_t N, int32_t y
                             int32_t n, int32_t w, int32_t p, float threshold, float *out,
                             void *stream);
 
+/*
+ * Multi-length index.  The paper states the search for one query length; a
+ * database holding series of several lengths is searched bucket by bucket,
+ * since LB_Keogh, LB_Improved and the band DTW of Sec. 4-8 compare series of
+ * equal length only.  An index owns one bucket per length (copied into
+ * device memory it allocates) and answers batches of queries of mixed
+ * length n, band w and neighbour count k.  Each query gets exactly the result
+ * knn_search gives for it against its bucket with the index's options
+ * (same neighbours, same distances); batching, streams, graphs and tuning
+ * change only the speed.
+ *
+ * Batch execution: queries of equal (n, w, k) form a group; each group is one
+ * cascade run (the stages of knn_search for a block of queries), and the
+ * groups run concurrently on a pool of streams forked from and joined back
+ * to the caller's stream.  Flags:
+ *   DTW_BATCH_GRAPH     capture the batch's device work as a CUDA graph the
+ *                       first time a batch of the same group shapes (lengths,
+ *                       bands, k, queries per group, tuning) is seen, and
+ *                       replay it afterwards; up to 16 graphs are cached.
+ *   DTW_BATCH_AUTOTUNE  before running, time candidate parameters (Sec. 9
+ *                       parts, seeds, filter segment length) on up to 256 of
+ *                       the group's own queries for every (n, w, k) that has
+ *                       no tuning yet, and keep the fastest (synchronous).
+ *   DTW_BATCH_SERIAL    run the groups one after another on the caller's stream.
+ *   DTW_BATCH_PER_QUERY run every query as its own cascade (one query per
+ *                       launch of each stage), one after another: the
+ *                       unbatched baseline.  GRAPH is ignored with it.
+ * Memory: the index grows a device arena for the largest batch seen (growth
+ * synchronises the device and drops the cached graphs) and a pinned host map
+ * of one entry per query.  Calls on one index are serialised by a mutex, and
+ * the device work of successive searches is ordered on the index's side.
+ */
+typedef struct dtw_index dtw_index;
+
+enum {
+    DTW_BATCH_GRAPH = 1,
+    DTW_BATCH_AUTOTUNE = 2,
+    DTW_BATCH_SERIAL = 4,
+    DTW_BATCH_PER_QUERY = 8
+};
+
+/* Cascade parameters of one (n, w, k); see dtw_options for parts and seeds.
+ * seg_len: candidates per filter segment (512, 1024 or 2048). ms: time of the
+ * tuning sample in milliseconds, or -1 when the values are the defaults. */
+typedef struct {
+    int32_t parts;
+    int32_t seeds;
+    int32_t seg_len;
+    float ms;
+} dtw_tuning;
+
+typedef struct {
+    int32_t buckets;
+    int32_t graphs_cached;
+    int64_t resident_bytes; /* bucket series and their part sums */
+    int64_t arena_bytes;    /* batch workspace */
+    int64_t graph_captures;
+    int64_t graph_replays;
+} dtw_index_stats;
+
+/* Creates an empty index for DTW_p on the current device.  opt (nullable)
+ * gives the cascade mode, slack and the default seeds and parts. */
+dtw_status dtw_index_create(int32_t p, const dtw_options *opt, dtw_index **out);
+
+/* Adds the bucket of length n: db [N][n], host or device memory, is copied
+ * into memory the index owns (synchronous).  One bucket per length. */
+dtw_status dtw_index_add_bucket(dtw_index *ix, const float *db, int64_t N, int32_t n);
+
+/* Times candidate parameters on sample [count][n] (host or device) and stores
+ * the fastest for (n, w, k); out (nullable) receives them.  Synchronous. */
+dtw_status dtw_index_tune(dtw_index *ix, const float *sample, int64_t count, int32_t n,
+                          int32_t w, int32_t k, dtw_tuning *out);
+
+/* Reads (defaults when untuned) or sets the parameters used for (n, w, k). */
+dtw_status dtw_index_get_tuning(dtw_index *ix, int32_t n, int32_t w, int32_t k, dtw_tuning *out);
+dtw_status dtw_index_set_tuning(dtw_index *ix, int32_t n, int32_t w, int32_t k, const dtw_tuning *t);
+
+/*
+ * Batched exact k-NN: query i has length q_len[i], band q_w[i] and
+ * neighbour count q_k[i] (host arrays of Q entries); the queries' values are
+ * concatenated in order in `queries` (sum of q_len floats, host or device).
+ * out_idx [Q][k_stride] (int64) and out_dist [Q][k_stride] (fp32, root taken),
+ * both host or both device memory, receive each query's neighbours ordered by
+ * (distance, index); entries past q_k[i], and past the bucket size, are
+ * idx -1, distance +INF.  1 <= q_k[i] <= k_stride <= DTW_MAX_K.  A query whose
+ * length has no bucket fails the call with DTW_ERR_NO_BUCKET before any work.
+ * stats (nullable) receives the counters summed over the batch; stats and host
+ * outputs make the call synchronous.
+ */
+dtw_status dtw_index_search(dtw_index *ix, const float *queries, int64_t Q,
+                            const int32_t *q_len, const int32_t *q_w, const int32_t *q_k,
+                            int32_t k_stride, int32_t flags, int64_t *out_idx,
+                            float *out_dist, dtw_stats *stats, void *stream);
+
+dtw_status dtw_index_info(dtw_index *ix, dtw_index_stats *out);
+
+/* Frees the index (waits for its work). */
+dtw_status dtw_index_destroy(dtw_index *ix);
+
 /* Message of the last failed call on this host thread ("" if none). */
 const char *dtw_last_error(void);
 

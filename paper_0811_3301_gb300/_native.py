@@ -69,6 +69,26 @@ class Options(ctypes.Structure):
                 ("parts", ctypes.c_int32)]
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("parts", ctypes.c_int32), ("seeds", ctypes.c_int32), ("seg_len", ctypes.c_int32),
+                ("ms", ctypes.c_float)]
+
+    def as_dict(self) -> dict:
+        return {"parts": int(self.parts), "seeds": int(self.seeds), "seg_len": int(self.seg_len),
+                "ms": float(self.ms)}
+
+
+class IndexStats(ctypes.Structure):
+    _fields_ = [("buckets", ctypes.c_int32), ("graphs_cached", ctypes.c_int32),
+                ("resident_bytes", ctypes.c_int64), ("arena_bytes", ctypes.c_int64),
+                ("graph_captures", ctypes.c_int64), ("graph_replays", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
+BATCH_GRAPH, BATCH_AUTOTUNE, BATCH_SERIAL, BATCH_PER_QUERY = 1, 2, 4, 8
+
 _vp = ctypes.c_void_p
 _i64 = ctypes.c_int64
 _i32 = ctypes.c_int32
@@ -87,6 +107,14 @@ SIGNATURES = {
     "dtw_profile_read": [ctypes.c_void_p, _i32],
     "knn_search_ex": [_vp, _i64, _vp, _i64, _i32, _i32, _i32, _i32, ctypes.POINTER(Options), _vp, _vp,
                       ctypes.POINTER(Stats), _vp],
+    "dtw_index_create": [_i32, ctypes.POINTER(Options), ctypes.POINTER(_vp)],
+    "dtw_index_add_bucket": [_vp, _vp, _i64, _i32],
+    "dtw_index_tune": [_vp, _vp, _i64, _i32, _i32, _i32, ctypes.POINTER(Tuning)],
+    "dtw_index_get_tuning": [_vp, _i32, _i32, _i32, ctypes.POINTER(Tuning)],
+    "dtw_index_set_tuning": [_vp, _i32, _i32, _i32, ctypes.POINTER(Tuning)],
+    "dtw_index_search": [_vp, _vp, _i64, _vp, _vp, _vp, _i32, _i32, _vp, _vp, ctypes.POINTER(Stats), _vp],
+    "dtw_index_info": [_vp, ctypes.POINTER(IndexStats)],
+    "dtw_index_destroy": [_vp],
 }
 
 

@@ -11,12 +11,13 @@ from __future__ import annotations
 import ctypes
 import math
 
+import numpy as np
 import torch
 
 from . import _native as N
 
-__all__ = ["dtw_envelope", "lb_keogh", "lb_piecewise", "lb_improved", "dtw_band", "knn_search", "DtwError",
-           "version"]
+__all__ = ["dtw_envelope", "lb_keogh", "lb_piecewise", "lb_improved", "dtw_band", "knn_search", "DtwIndex",
+           "DtwError", "version"]
 
 DtwError = N.DtwError
 version = N.version
@@ -156,3 +157,123 @@ def knn_search(db: torch.Tensor, queries: torch.Tensor, w: int, p: int, k: int =
     if return_stats:
         return out_idx, out_dist, st.as_dict()
     return out_idx, out_dist
+
+
+def _i32_host(v, Q: int, name: str) -> np.ndarray:
+    a = np.asarray(v, dtype=np.int64)
+    if a.ndim == 0:
+        a = np.full(Q, int(a), dtype=np.int64)
+    if a.shape != (Q,):
+        raise ValueError("%s must be a scalar or have one entry per query" % name)
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+class DtwIndex:
+    """Length buckets resident on the device and batched k-NN search over
+    queries of mixed length, band and k (the dtw_index_* calls).
+
+    Every query gets the result knn_search gives it against the bucket of its
+    length; grouping, concurrent streams, CUDA graphs and autotuning only
+    change the speed.
+    """
+
+    def __init__(self, p: int, *, mode: str = "improved", slack: float = 1e-6, seeds: int = 0, parts: int = 0):
+        if mode not in _MODES:
+            raise ValueError("mode must be one of %s" % sorted(_MODES))
+        opt = N.Options(_MODES[mode], float(slack), int(seeds), int(parts))
+        h = ctypes.c_void_p()
+        N.check(N.lib.dtw_index_create(int(p), ctypes.byref(opt), ctypes.byref(h)))
+        self._h = h
+        self.p = int(p)
+        self.lengths: list[int] = []
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            N.check(N.lib.dtw_index_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def add_bucket(self, db: torch.Tensor) -> None:
+        """Adds the bucket of length n = db.shape[1] (db [N, n], host or CUDA; copied)."""
+        db = _f32(db, "db")
+        if db.dim() != 2:
+            raise ValueError("db must be [N, n]")
+        N.check(N.lib.dtw_index_add_bucket(self._h, _ptr(db), db.shape[0], db.shape[1]))
+        self.lengths.append(int(db.shape[1]))
+
+    def tune(self, sample: torch.Tensor, w: int, k: int) -> dict:
+        """Times candidate parameters on sample [count, n] and keeps the fastest for (n, w, k)."""
+        sample = _f32(sample, "sample")
+        t = N.Tuning()
+        N.check(N.lib.dtw_index_tune(self._h, _ptr(sample), sample.shape[0], sample.shape[1], int(w), int(k),
+                                     ctypes.byref(t)))
+        return t.as_dict()
+
+    def get_tuning(self, n: int, w: int, k: int) -> dict:
+        t = N.Tuning()
+        N.check(N.lib.dtw_index_get_tuning(self._h, int(n), int(w), int(k), ctypes.byref(t)))
+        return t.as_dict()
+
+    def set_tuning(self, n: int, w: int, k: int, *, parts: int, seeds: int, seg_len: int) -> None:
+        t = N.Tuning(int(parts), int(seeds), int(seg_len), -1.0)
+        N.check(N.lib.dtw_index_set_tuning(self._h, int(n), int(w), int(k), ctypes.byref(t)))
+
+    def info(self) -> dict:
+        st = N.IndexStats()
+        N.check(N.lib.dtw_index_info(self._h, ctypes.byref(st)))
+        return st.as_dict()
+
+    def search_flat(self, flat: torch.Tensor, lengths, w, k, *, k_stride: int | None = None, graph: bool = False,
+                    autotune: bool = False, serial: bool = False, per_query: bool = False,
+                    out_idx: torch.Tensor | None = None, out_dist: torch.Tensor | None = None,
+                    return_stats: bool = False):
+        """Batched search over queries concatenated in `flat` (1-D float32, host or CUDA).
+
+        lengths, w and k are per-query sequences (or scalars for w and k).
+        Returns (idx int64 [Q, k_stride], dist float32 [Q, k_stride]) on the
+        device of `flat`; entries past a query's k are -1 / +inf.
+        """
+        flat = _f32(flat, "flat").reshape(-1)
+        lens = np.ascontiguousarray(np.asarray(lengths, dtype=np.int64), dtype=np.int32)
+        Q = lens.shape[0]
+        ws = _i32_host(w, Q, "w")
+        ks = _i32_host(k, Q, "k")
+        if int(lens.astype(np.int64).sum()) != flat.numel():
+            raise ValueError("sum of lengths (%d) must equal the number of values (%d)" % (int(lens.sum()), flat.numel()))
+        ks_max = int(ks.max()) if Q else 1
+        k_stride = ks_max if k_stride is None else int(k_stride)
+        dev = flat.device
+        pin = not flat.is_cuda and torch.cuda.is_available()
+        if out_idx is None:
+            out_idx = torch.empty((Q, k_stride), dtype=torch.int64, device=dev, pin_memory=pin)
+        if out_dist is None:
+            out_dist = torch.empty((Q, k_stride), dtype=torch.float32, device=dev, pin_memory=pin)
+        flags = ((N.BATCH_GRAPH if graph else 0) | (N.BATCH_AUTOTUNE if autotune else 0) |
+                 (N.BATCH_SERIAL if serial else 0) | (N.BATCH_PER_QUERY if per_query else 0))
+        st = N.Stats()
+        N.check(N.lib.dtw_index_search(self._h, _ptr(flat) if flat.numel() else None, Q,
+                                       lens.ctypes.data, ws.ctypes.data, ks.ctypes.data, k_stride, flags,
+                                       _ptr(out_idx), _ptr(out_dist),
+                                       ctypes.byref(st) if return_stats else None, _stream()))
+        if return_stats:
+            return out_idx, out_dist, st.as_dict()
+        return out_idx, out_dist
+
+    def search(self, queries, w, k, **kw):
+        """Batched search over a list of 1-D query tensors of mixed length (see search_flat)."""
+        qs = [_f32(q, "query").reshape(-1) for q in queries]
+        if not qs:
+            raise ValueError("no queries")
+        lengths = [q.numel() for q in qs]
+        return self.search_flat(torch.cat(qs), lengths, w, k, **kw)

@@ -8,8 +8,7 @@
 #include <mutex>
 #include <vector>
 
-#include "common.cuh"
-#include "dtw.cuh"
+#include "cascade_host.cuh"
 
 namespace dtwk {
 
@@ -86,19 +85,6 @@ static dtw_status workspace_get(size_t bytes, void **out) {
     return DTW_OK;
 }
 
-// Bump allocator over a workspace block; sizes are rounded to 256 bytes.
-struct Carve {
-    size_t off = 0;
-    char *base = nullptr;
-    template <typename T>
-    T *take(size_t count) {
-        size_t bytes = (count * sizeof(T) + 255) & ~size_t(255);
-        T *p = reinterpret_cast<T *>(base ? base + off : nullptr);
-        off += bytes;
-        return p;
-    }
-};
-
 static bool is_device_ptr(const void *p) {
     cudaPointerAttributes a;
     cudaError_t e = cudaPointerGetAttributes(&a, p);
@@ -123,40 +109,6 @@ static dtw_status check_band(int32_t n, int32_t w) {
     return DTW_OK;
 }
 
-// ---------------------------------------------------------------------------
-// stage timing (dtw_profile_enable / dtw_profile_read)
-// ---------------------------------------------------------------------------
-struct StageEvents {
-    int stage;
-    cudaEvent_t a, b;
-};
-static bool g_prof_on = false;
-static std::mutex g_prof_mu;
-static std::vector<StageEvents> g_prof_events;
-
-struct StageTimer {
-    StageEvents ev{};
-    bool on = false;
-    cudaStream_t s;
-    StageTimer(int stage, cudaStream_t st) : s(st) {
-        on = g_prof_on;
-        if (!on) return;
-        ev.stage = stage;
-        if (cudaEventCreate(&ev.a) != cudaSuccess || cudaEventCreate(&ev.b) != cudaSuccess) {
-            cudaGetLastError();
-            on = false;
-            return;
-        }
-        cudaEventRecord(ev.a, s);
-    }
-    ~StageTimer() {
-        if (!on) return;
-        cudaEventRecord(ev.b, s);
-        std::lock_guard<std::mutex> lk(g_prof_mu);
-        g_prof_events.push_back(ev);
-    }
-};
-
 static cudaError_t launch_dtw(const DtwJob &j, const DtwGeom &g, cudaStream_t s) {
     return j.p == 1 ? launch_dtw_p1(j, g, s) : launch_dtw_p2(j, g, s);
 }
@@ -171,32 +123,14 @@ const char *dtw_last_error(void) { return g_err; }
 
 dtw_status dtw_profile_enable(int32_t on) {
     g_err[0] = 0;
-    g_prof_on = on != 0;
+    profile_set(on != 0);
     return DTW_OK;
 }
 
 dtw_status dtw_profile_read(dtw_profile *out, int32_t reset) {
     g_err[0] = 0;
     if (!out) return fail(DTW_ERR_INVALID_ARG, "null pointer");
-    std::lock_guard<std::mutex> lk(g_prof_mu);
-    for (auto &ev : g_prof_events) {
-        cudaError_t e = cudaEventSynchronize(ev.b);
-        if (e != cudaSuccess) return fail(DTW_ERR_CUDA, "cudaEventSynchronize: %s", cudaGetErrorString(e));
-        float ms = 0.0f;
-        e = cudaEventElapsedTime(&ms, ev.a, ev.b);
-        if (e != cudaSuccess) return fail(DTW_ERR_CUDA, "cudaEventElapsedTime: %s", cudaGetErrorString(e));
-        if (ev.stage >= 0 && ev.stage < DTW_NUM_STAGES) {
-            out->ms[ev.stage] += ms;
-            out->launches[ev.stage] += 1;
-        }
-    }
-    if (reset) {
-        for (auto &ev : g_prof_events) {
-            cudaEventDestroy(ev.a);
-            cudaEventDestroy(ev.b);
-        }
-        g_prof_events.clear();
-    }
+    CUDA_TRY(profile_collect(out->ms, out->launches, reset != 0));
     return DTW_OK;
 }
 
@@ -325,256 +259,72 @@ dtw_status knn_search_ex(const float *db, int64_t N, const float *queries, int64
     if (!queries || !out_idx || !out_dist || (N > 0 && !db)) return fail(DTW_ERR_INVALID_ARG, "null pointer");
     cudaStream_t s = (cudaStream_t)stream;
 
-    const int we = w < n - 1 ? w : n - 1;
-    const DtwGeom g = dtw_geom(n, we);
-    const float slack = fmaxf(o.slack, auto_slack(n));
-    // piecewise-sum pre-filter (Sec. 9): d parts
-    const int parts = o.parts == 0 ? (n >= 64 ? n / 8 : -1) : o.parts;
-    const bool summary = parts > 0 && N > 0;
-    const PartGeom pg = part_geom(n, summary ? parts : 1);
-    int S = o.seeds > 0 ? o.seeds : 16;
-    if (S < k) S = k;
-    if (S > 32) S = 32;
-    if (S > N) S = (int)N;
-    if (S < 1) S = 1;
-
+    const CascadePlan pl = make_plan(N, Q, n, w, p, k, o);
     const bool db_dev = N == 0 || is_device_ptr(db);
     const bool q_dev = is_device_ptr(queries);
     const bool oi_dev = is_device_ptr(out_idx);
     const bool od_dev = is_device_ptr(out_dist);
+    const int64_t Qc = pl.Qc;
 
-    // query chunk: bounds the Q*N-sized buffers
-    const int64_t pair_budget = (int64_t)1 << 27;
-    int64_t Qc = N > 0 ? pair_budget / N : Q;
-    if (Qc < 1) Qc = 1;
-    if (Qc > 32768) Qc = 32768;  // grid.y limit of the per-query kernels
-    if (Qc > Q) Qc = Q;
-    const int seg_len = 1024;
-    const int filter_warps = lbi_filter_warps(n, we, S, seg_len);
-    // sub-segments per query: candidate segments x filter warps
-    const int nseg = N > 0 ? (int)((N + seg_len - 1) / seg_len) * filter_warps : 1;
-    const int64_t Nc = N > 0 ? N : 1;
-
-    auto layout = [&](Carve &cv) {
-        struct L {
-            float *db, *q, *U, *L, *copies, *lb, *seed_res, *pair_lbi, *pair_res, *out_dist, *lbi_u, *PX, *PU, *PL;
-            Pair *seed_pairs, *pairs, *pairs_u;
-            int32_t *qcount, *qstart;
-            uint32_t *gmin, *bsf;
-            int32_t *seg_start, *seg_count;
-            unsigned long long *misc, *tile_min;
-            int64_t *out_idx;
-        } l;
-        l.db = db_dev ? nullptr : cv.take<float>((size_t)N * n);
-        l.q = cv.take<float>((size_t)Qc * n);
-        l.U = cv.take<float>((size_t)Qc * n);
-        l.L = cv.take<float>((size_t)Qc * n);
-        l.copies = cv.take<float>((size_t)Qc * 4 * g.ylen);
-        l.lb = cv.take<float>((size_t)Qc * Nc);
-        l.PX = summary ? cv.take<float>((size_t)N * parts) : nullptr;
-        l.PU = summary ? cv.take<float>((size_t)Qc * parts) : nullptr;
-        l.PL = summary ? cv.take<float>((size_t)Qc * parts) : nullptr;
-        l.tile_min = cv.take<unsigned long long>((size_t)Qc * lbk_tiles((int)Nc));
-        l.seed_pairs = cv.take<Pair>((size_t)Qc * S);
-        l.seed_res = cv.take<float>((size_t)Qc * S);
-        l.gmin = cv.take<uint32_t>((size_t)Qc * k);
-        l.bsf = cv.take<uint32_t>((size_t)Qc);
-        l.pairs_u = cv.take<Pair>((size_t)Qc * Nc);
-        l.lbi_u = cv.take<float>((size_t)Qc * Nc);
-        l.qcount = cv.take<int32_t>((size_t)Qc);
-        l.qstart = cv.take<int32_t>((size_t)Qc);
-
-        l.pairs = cv.take<Pair>((size_t)Qc * Nc);
-        l.pair_lbi = cv.take<float>((size_t)Qc * Nc);
-        l.pair_res = cv.take<float>((size_t)Qc * Nc);
-        l.seg_start = cv.take<int32_t>((size_t)Qc * nseg);
-        l.seg_count = cv.take<int32_t>((size_t)Qc * nseg);
-        l.misc = cv.take<unsigned long long>(32);
-        l.out_idx = oi_dev ? nullptr : cv.take<int64_t>((size_t)Q * k);
-        l.out_dist = od_dev ? nullptr : cv.take<float>((size_t)Q * k);
-        return l;
+    struct Extra {
+        float *db, *q, *PX, *out_dist;
+        int64_t *out_idx;
+        unsigned long long *counters, *xmax;
+    };
+    auto layout = [&](Carve &cv, Extra &x) {
+        x.db = db_dev ? nullptr : cv.take<float>((size_t)N * n);
+        x.q = q_dev ? nullptr : cv.take<float>((size_t)Qc * n);
+        x.PX = pl.summary ? cv.take<float>((size_t)N * pl.parts) : nullptr;
+        x.counters = cv.take<unsigned long long>(2 * CNT_NUM);
+        x.xmax = cv.take<unsigned long long>(1);
+        x.out_idx = oi_dev ? nullptr : cv.take<int64_t>((size_t)Q * k);
+        x.out_dist = od_dev ? nullptr : cv.take<float>((size_t)Q * k);
+        return carve_ws(pl, cv);
     };
     Carve sizing;
-    layout(sizing);
-    void *ws = nullptr;
-    if ((st = workspace_get(sizing.off, &ws)) != DTW_OK) return st;
+    Extra x{};
+    layout(sizing, x);
+    void *wsp = nullptr;
+    if ((st = workspace_get(sizing.off, &wsp)) != DTW_OK) return st;
     Carve cv;
-    cv.base = (char *)ws;
-    auto l = layout(cv);
+    cv.base = (char *)wsp;
+    const CascadeWs ws = layout(cv, x);
 
     const float *dbd = db;
     if (!db_dev) {
-        CUDA_TRY(cudaMemcpyAsync(l.db, db, (size_t)N * n * sizeof(float), cudaMemcpyHostToDevice, s));
-        dbd = l.db;
+        CUDA_TRY(cudaMemcpyAsync(x.db, db, (size_t)N * n * sizeof(float), cudaMemcpyHostToDevice, s));
+        dbd = x.db;
     }
-    int64_t *oidx = oi_dev ? out_idx : l.out_idx;
-    float *odist = od_dev ? out_dist : l.out_dist;
-    unsigned long long *pair_count = l.misc + 0;
-    unsigned long long *cur_seed = l.misc + 1;
-    unsigned long long *cur_pairs = l.misc + 2;
-    unsigned long long *counters = l.misc + 8;
-    unsigned long long *seed_counters = l.misc + 16;
-    CUDA_TRY(cudaMemsetAsync(counters, 0, 2 * CNT_NUM * sizeof(unsigned long long), s));
-    unsigned *xmax_bits = reinterpret_cast<unsigned *>(l.misc + 24);
-    if (summary) {
+    int64_t *oidx = oi_dev ? out_idx : x.out_idx;
+    float *odist = od_dev ? out_dist : x.out_dist;
+    CUDA_TRY(cudaMemsetAsync(x.counters, 0, 2 * CNT_NUM * sizeof(unsigned long long), s));
+    unsigned *xmax_bits = reinterpret_cast<unsigned *>(x.xmax);
+    if (pl.summary) {
         // part sums of the database rows, once per call
         CUDA_TRY(cudaMemsetAsync(xmax_bits, 0, sizeof(unsigned long long), s));
-        CUDA_TRY(launch_summarize(dbd, N, n, parts, l.PX, xmax_bits, s));
+        CUDA_TRY(launch_summarize(dbd, N, n, pl.parts, x.PX, xmax_bits, s));
     }
-
     for (int64_t q0 = 0; q0 < Q; q0 += Qc) {
         const int qn = (int)((Q - q0) < Qc ? (Q - q0) : Qc);
         const float *qd;
         if (q_dev) {
             qd = queries + q0 * n;
         } else {
-            CUDA_TRY(cudaMemcpyAsync(l.q, queries + q0 * n, (size_t)qn * n * sizeof(float),
+            CUDA_TRY(cudaMemcpyAsync(x.q, queries + q0 * n, (size_t)qn * n * sizeof(float),
                                      cudaMemcpyHostToDevice, s));
-            qd = l.q;
+            qd = x.q;
         }
-        CUDA_TRY(cudaMemsetAsync(l.misc, 0, 8 * sizeof(unsigned long long), s));
-        QueryCopies qc;
-        qc.data = l.copies;
-        qc.padl = g.padl;
-        qc.ylen = g.ylen;
-        {
-            StageTimer tm(DTW_STAGE_ENVELOPE, s);
-            CUDA_TRY(launch_envelope(qd, qn, n, we, l.U, l.L, qc, g.padl, s));
-        }
-
-        CascadeBufs b{};
-        b.db = dbd;
-        b.queries = qd;
-        b.U = l.U;
-        b.L = l.L;
-        b.qc = qc;
-        b.N = (int)N;
-        b.Q = qn;
-        b.n = n;
-        b.w = we;
-        b.p = p;
-        b.k = k;
-        b.mode = o.mode;
-        b.slack = slack;
-        b.lb = l.lb;
-        b.tile_min = l.tile_min;
-        b.ntiles = lbk_tiles((int)Nc);
-        b.S = N > 0 ? S : 0;
-        b.seed_pairs = l.seed_pairs;
-        b.seed_res = l.seed_res;
-        b.gmin = l.gmin;
-        b.bsf = l.bsf;
-        b.pairs_u = l.pairs_u;
-        b.lbi_u = l.lbi_u;
-        b.qcount = l.qcount;
-        b.qstart = l.qstart;
-        b.pair_total = l.misc + 4;
-        b.lbi_inline = o.mode == DTW_MODE_IMPROVED ? 1 : 0;
-        b.summary = summary ? 1 : 0;
-        b.summary_scale = (summary && p == 2) ? (float)pg.smax : 1.0f;
-        b.pairs = l.pairs;
-        b.pair_lbi = l.pair_lbi;
-        b.pair_res = l.pair_res;
-        b.pair_cap = (int64_t)qn * Nc;
-        b.pair_count = pair_count;
-        b.seg_len = seg_len;
-        b.nseg = N > 0 ? nseg : 0;
-        b.seg_start = l.seg_start;
-        b.seg_count = l.seg_count;
-        b.cursor = cur_pairs;
-        b.counters = counters;
-        b.out_idx = oidx + q0 * k;
-        b.out_dist = odist + q0 * k;
-
-        if (N > 0) {
-            {
-                StageTimer tm(DTW_STAGE_LB_KEOGH, s);
-                if (summary) {
-                    // piecewise-sum bound of every pair (the tile kernel on the d part sums)
-                    CUDA_TRY(launch_query_summary(l.U, l.L, qn, n, parts, xmax_bits, l.PU, l.PL, 1, s));
-                    CUDA_TRY(launch_lbk_tile(l.PX, (int)N, l.PU, l.PL, qn, parts, p, l.lb, l.tile_min, s));
-                } else {
-                    CUDA_TRY(launch_lbk_tile(dbd, (int)N, l.U, l.L, qn, n, p, l.lb, l.tile_min, s));
-                }
-            }
-            {
-                StageTimer tm(DTW_STAGE_SEED_SELECT, s);
-                CUDA_TRY(launch_seed_select(b, s));
-            }
-            DtwJob js{};
-            js.db = dbd;
-            js.n = n;
-            js.w = we;
-            js.p = p;
-            js.k = k;
-            js.qc = qc;
-            js.pairs = l.seed_pairs;
-            js.npairs = (int64_t)qn * S;
-            js.slack = slack;
-            js.bsf = l.bsf;
-            js.gmin = l.gmin;
-            js.abandon = 0;
-            js.res = l.seed_res;
-            js.cursor = cur_seed;
-            js.counters = seed_counters;
-            {
-                StageTimer tm(DTW_STAGE_SEED_DTW, s);
-                CUDA_TRY(launch_dtw(js, g, s));
-            }
-            {
-                StageTimer tm(DTW_STAGE_SEED_KTH, s);
-                CUDA_TRY(launch_seed_kth(b, s));
-            }
-            {
-                StageTimer tm(DTW_STAGE_LB_IMPROVED, s);
-                CUDA_TRY(cudaMemsetAsync(l.qcount, 0, (size_t)qn * sizeof(int32_t), s));
-                CUDA_TRY(launch_lbi_filter(b, s));
-                CUDA_TRY(launch_group_by_query(b, s));
-            }
-            DtwJob jp = js;
-            jp.pairs = l.pairs;
-            jp.npairs = (int64_t)qn * Nc;
-            jp.npairs_dev = b.pair_total;
-            jp.pair_lbi = o.mode == DTW_MODE_NOPRUNE ? nullptr : l.pair_lbi;
-            jp.abandon = o.mode == DTW_MODE_NOPRUNE ? 0 : 1;
-            jp.res = l.pair_res;
-            jp.cursor = cur_pairs;
-            jp.counters = counters;
-            {
-                StageTimer tm(DTW_STAGE_DTW, s);
-                CUDA_TRY(launch_dtw(jp, g, s));
-            }
-        }
-        {
-            StageTimer tm(DTW_STAGE_FINALIZE, s);
-            CUDA_TRY(launch_finalize(b, s));
-        }
+        CUDA_TRY(cascade_run(pl, ws, dbd, x.PX, xmax_bits, qd, qn, oidx + q0 * k, odist + q0 * k, x.counters, s));
     }
     if (!oi_dev)
-        CUDA_TRY(cudaMemcpyAsync(out_idx, l.out_idx, (size_t)Q * k * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaMemcpyAsync(out_idx, x.out_idx, (size_t)Q * k * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     if (!od_dev)
-        CUDA_TRY(cudaMemcpyAsync(out_dist, l.out_dist, (size_t)Q * k * sizeof(float), cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaMemcpyAsync(out_dist, x.out_dist, (size_t)Q * k * sizeof(float), cudaMemcpyDeviceToHost, s));
     if (stats || !oi_dev || !od_dev) {
         unsigned long long h[2 * CNT_NUM];
-        if (stats) CUDA_TRY(cudaMemcpyAsync(h, counters, sizeof(h), cudaMemcpyDeviceToHost, s));
+        if (stats) CUDA_TRY(cudaMemcpyAsync(h, x.counters, sizeof(h), cudaMemcpyDeviceToHost, s));
         CUDA_TRY(cudaStreamSynchronize(s));
-        if (stats) {
-            const int64_t seeds = N > 0 ? Q * (int64_t)S : 0;
-            stats->candidates = Q * N;
-            stats->seeds = seeds;
-            if (summary) {
-                stats->pruned_summary = Q * N - seeds - (int64_t)h[CNT_SUMMARY_PASS];
-                stats->pruned_keogh = (int64_t)h[CNT_SUMMARY_PASS] - (int64_t)h[CNT_KEOGH_PASS];
-            } else {
-                stats->pruned_summary = 0;
-                stats->pruned_keogh = Q * N - seeds - (int64_t)h[CNT_KEOGH_PASS];
-            }
-            stats->pruned_improved = (int64_t)h[CNT_KEOGH_PASS] - (int64_t)h[CNT_LBI_PASS] + (int64_t)h[CNT_DTW_SKIP];
-            stats->dtw_computed = (int64_t)h[CNT_DTW_COMPUTED];
-            stats->dtw_abandoned = (int64_t)h[CNT_DTW_ABANDONED];
-            stats->dtw_cells = (int64_t)h[CNT_DTW_ROWS] * (2 * we + 1);
-            stats->seed_cells = (int64_t)h[CNT_NUM + CNT_DTW_ROWS] * (2 * we + 1);
-        }
+        if (stats) cascade_stats(pl, Q, h, stats);
     }
     return DTW_OK;
 }

@@ -1,0 +1,313 @@
+// Host side of one cascade run (Algorithms 2/3 over a batch of queries of one
+// length against one database): the plan (sizes and parameters), the
+// workspace layout and the launch sequence.  Used by knn_search and by the
+// multi-length index.  All launches are asynchronous on one stream and
+// allocate nothing, so a run can be captured in a CUDA graph.
+#include <cmath>
+#include <mutex>
+#include <vector>
+
+#include "cascade_host.cuh"
+
+namespace dtwk {
+
+// ---------------------------------------------------------------------------
+// stage timing
+// ---------------------------------------------------------------------------
+static bool g_prof_on = false;
+static std::mutex g_prof_mu;
+struct StageEvents {
+    int stage;
+    cudaEvent_t a, b;
+};
+static std::vector<StageEvents> g_prof_events;
+
+void profile_set(bool on) { g_prof_on = on; }
+
+cudaError_t profile_collect(double *ms, int64_t *launches, bool reset) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (auto &ev : g_prof_events) {
+        cudaError_t e = cudaEventSynchronize(ev.b);
+        if (e != cudaSuccess) return e;
+        float t = 0.0f;
+        e = cudaEventElapsedTime(&t, ev.a, ev.b);
+        if (e != cudaSuccess) return e;
+        if (ev.stage >= 0 && ev.stage < DTW_NUM_STAGES) {
+            ms[ev.stage] += t;
+            launches[ev.stage] += 1;
+        }
+    }
+    if (reset) {
+        for (auto &ev : g_prof_events) {
+            cudaEventDestroy(ev.a);
+            cudaEventDestroy(ev.b);
+        }
+        g_prof_events.clear();
+    }
+    return cudaSuccess;
+}
+
+// Records a pair of events around a stage when profiling is on and the
+// stream is not being captured.
+struct StageTimer {
+    StageEvents ev{};
+    bool on = false;
+    cudaStream_t s;
+    StageTimer(int stage, cudaStream_t st) : s(st) {
+        if (!g_prof_on) return;
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+            cudaGetLastError();
+            return;
+        }
+        ev.stage = stage;
+        if (cudaEventCreate(&ev.a) != cudaSuccess || cudaEventCreate(&ev.b) != cudaSuccess) {
+            cudaGetLastError();
+            return;
+        }
+        on = true;
+        cudaEventRecord(ev.a, s);
+    }
+    ~StageTimer() {
+        if (!on) return;
+        cudaEventRecord(ev.b, s);
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        g_prof_events.push_back(ev);
+    }
+};
+
+#define RUN_TRY(expr)                   \
+    do {                                \
+        cudaError_t e_ = (expr);        \
+        if (e_ != cudaSuccess) return e_; \
+    } while (0)
+
+static cudaError_t launch_dtw_any(const DtwJob &j, const DtwGeom &g, cudaStream_t s) {
+    return j.p == 1 ? launch_dtw_p1(j, g, s) : launch_dtw_p2(j, g, s);
+}
+
+// ---------------------------------------------------------------------------
+// plan and workspace
+// ---------------------------------------------------------------------------
+CascadePlan make_plan(int64_t N, int64_t Qmax, int n, int w, int p, int k, const dtw_options &o, int seg_len) {
+    CascadePlan pl{};
+    pl.N = N;
+    pl.n = n;
+    pl.we = w < n - 1 ? w : n - 1;
+    pl.p = p;
+    pl.k = k;
+    pl.mode = o.mode;
+    pl.g = dtw_geom(n, pl.we);
+    pl.slack = fmaxf(o.slack, auto_slack(n));
+    pl.parts = o.parts == 0 ? (n >= 64 ? n / 8 : -1) : o.parts;
+    if (pl.parts > n) pl.parts = n;
+    if (N <= 0) pl.parts = -1;
+    pl.summary = pl.parts > 0;
+    pl.pg = part_geom(n, pl.summary ? pl.parts : 1);
+    int S = o.seeds > 0 ? o.seeds : 16;
+    if (S < k) S = k;
+    if (S > 32) S = 32;
+    if (S > N) S = (int)N;
+    if (S < 1) S = 1;
+    pl.S = N > 0 ? S : 0;
+    // query chunk: bounds the Q*N-sized buffers
+    const int64_t pair_budget = (int64_t)1 << 27;
+    int64_t Qc = N > 0 ? pair_budget / N : Qmax;
+    if (Qc < 1) Qc = 1;
+    if (Qc > 32768) Qc = 32768;  // grid limit of the per-query kernels
+    if (Qc > Qmax) Qc = Qmax;
+    if (Qc < 1) Qc = 1;
+    pl.Qc = Qc;
+    pl.seg_len = seg_len;
+    pl.filter_warps = lbi_filter_warps(n, pl.we, std::max(pl.S, 1), pl.seg_len);
+    pl.nseg = N > 0 ? (int)((N + pl.seg_len - 1) / pl.seg_len) * pl.filter_warps : 1;
+    return pl;
+}
+
+CascadeWs carve_ws(const CascadePlan &pl, Carve &cv) {
+    CascadeWs l{};
+    const int64_t Qc = pl.Qc;
+    const int64_t Nc = pl.N > 0 ? pl.N : 1;
+    const int n = pl.n;
+    l.U = cv.take<float>((size_t)Qc * n);
+    l.L = cv.take<float>((size_t)Qc * n);
+    l.copies = cv.take<float>((size_t)Qc * 4 * pl.g.ylen);
+    l.lb = cv.take<float>((size_t)Qc * Nc);
+    l.PU = pl.summary ? cv.take<float>((size_t)Qc * pl.parts) : nullptr;
+    l.PL = pl.summary ? cv.take<float>((size_t)Qc * pl.parts) : nullptr;
+    l.tile_min = cv.take<unsigned long long>((size_t)Qc * lbk_tiles((int)Nc));
+    l.seed_pairs = cv.take<Pair>((size_t)Qc * std::max(pl.S, 1));
+    l.seed_res = cv.take<float>((size_t)Qc * std::max(pl.S, 1));
+    l.gmin = cv.take<uint32_t>((size_t)Qc * pl.k);
+    l.bsf = cv.take<uint32_t>((size_t)Qc);
+    l.pairs_u = cv.take<Pair>((size_t)Qc * Nc);
+    l.lbi_u = cv.take<float>((size_t)Qc * Nc);
+    l.qcount = cv.take<int32_t>((size_t)Qc);
+    l.qstart = cv.take<int32_t>((size_t)Qc);
+    l.pairs = cv.take<Pair>((size_t)Qc * Nc);
+    l.pair_lbi = cv.take<float>((size_t)Qc * Nc);
+    l.pair_res = cv.take<float>((size_t)Qc * Nc);
+    l.seg_start = cv.take<int32_t>((size_t)Qc * pl.nseg);
+    l.seg_count = cv.take<int32_t>((size_t)Qc * pl.nseg);
+    l.misc = cv.take<unsigned long long>(8);
+    return l;
+}
+
+size_t cascade_ws_bytes(const CascadePlan &pl) {
+    Carve cv;
+    carve_ws(pl, cv);
+    return cv.off;
+}
+
+// ---------------------------------------------------------------------------
+// one run over qn <= Qc queries
+// ---------------------------------------------------------------------------
+cudaError_t cascade_run(const CascadePlan &pl, const CascadeWs &l, const float *db, const float *PX,
+                        const unsigned *xmax_bits, const float *q, int qn, int64_t *out_idx, float *out_dist,
+                        unsigned long long *counters, cudaStream_t s) {
+    const int n = pl.n, we = pl.we, p = pl.p, k = pl.k;
+    const int64_t N = pl.N;
+    const int64_t Nc = N > 0 ? N : 1;
+    unsigned long long *pair_count = l.misc + 0;
+    unsigned long long *cur_seed = l.misc + 1;
+    unsigned long long *cur_pairs = l.misc + 2;
+    unsigned long long *pair_total = l.misc + 4;
+    unsigned long long *seed_counters = counters + CNT_NUM;
+    RUN_TRY(cudaMemsetAsync(l.misc, 0, 8 * sizeof(unsigned long long), s));
+    QueryCopies qc;
+    qc.data = l.copies;
+    qc.padl = pl.g.padl;
+    qc.ylen = pl.g.ylen;
+    {
+        StageTimer tm(DTW_STAGE_ENVELOPE, s);
+        RUN_TRY(launch_envelope(q, qn, n, we, l.U, l.L, qc, pl.g.padl, s));
+    }
+    CascadeBufs b{};
+    b.db = db;
+    b.queries = q;
+    b.U = l.U;
+    b.L = l.L;
+    b.qc = qc;
+    b.N = (int)N;
+    b.Q = qn;
+    b.n = n;
+    b.w = we;
+    b.p = p;
+    b.k = k;
+    b.mode = pl.mode;
+    b.slack = pl.slack;
+    b.lb = l.lb;
+    b.tile_min = l.tile_min;
+    b.ntiles = lbk_tiles((int)Nc);
+    b.S = pl.S;
+    b.seed_pairs = l.seed_pairs;
+    b.seed_res = l.seed_res;
+    b.gmin = l.gmin;
+    b.bsf = l.bsf;
+    b.pairs_u = l.pairs_u;
+    b.lbi_u = l.lbi_u;
+    b.qcount = l.qcount;
+    b.qstart = l.qstart;
+    b.pair_total = pair_total;
+    b.lbi_inline = pl.mode == DTW_MODE_IMPROVED ? 1 : 0;
+    b.summary = pl.summary ? 1 : 0;
+    b.summary_scale = (pl.summary && p == 2) ? (float)pl.pg.smax : 1.0f;
+    b.pairs = l.pairs;
+    b.pair_lbi = l.pair_lbi;
+    b.pair_res = l.pair_res;
+    b.pair_cap = (int64_t)qn * Nc;
+    b.pair_count = pair_count;
+    b.seg_len = pl.seg_len;
+    b.nseg = N > 0 ? pl.nseg : 0;
+    b.seg_start = l.seg_start;
+    b.seg_count = l.seg_count;
+    b.cursor = cur_pairs;
+    b.counters = counters;
+    b.out_idx = out_idx;
+    b.out_dist = out_dist;
+
+    if (N > 0) {
+        {
+            StageTimer tm(DTW_STAGE_LB_KEOGH, s);
+            if (pl.summary) {
+                // piecewise-sum bound of every pair: the tile kernel on the d part sums
+                RUN_TRY(launch_query_summary(l.U, l.L, qn, n, pl.parts, xmax_bits, l.PU, l.PL, 1, s));
+                RUN_TRY(launch_lbk_tile(PX, (int)N, l.PU, l.PL, qn, pl.parts, p, l.lb, l.tile_min, s));
+            } else {
+                RUN_TRY(launch_lbk_tile(db, (int)N, l.U, l.L, qn, n, p, l.lb, l.tile_min, s));
+            }
+        }
+        {
+            StageTimer tm(DTW_STAGE_SEED_SELECT, s);
+            RUN_TRY(launch_seed_select(b, s));
+        }
+        DtwJob js{};
+        js.db = db;
+        js.n = n;
+        js.w = we;
+        js.p = p;
+        js.k = k;
+        js.qc = qc;
+        js.pairs = l.seed_pairs;
+        js.npairs = (int64_t)qn * pl.S;
+        js.slack = pl.slack;
+        js.bsf = l.bsf;
+        js.gmin = l.gmin;
+        js.abandon = 0;
+        js.res = l.seed_res;
+        js.cursor = cur_seed;
+        js.counters = seed_counters;
+        {
+            StageTimer tm(DTW_STAGE_SEED_DTW, s);
+            RUN_TRY(launch_dtw_any(js, pl.g, s));
+        }
+        {
+            StageTimer tm(DTW_STAGE_SEED_KTH, s);
+            RUN_TRY(launch_seed_kth(b, s));
+        }
+        {
+            StageTimer tm(DTW_STAGE_LB_IMPROVED, s);
+            RUN_TRY(cudaMemsetAsync(l.qcount, 0, (size_t)qn * sizeof(int32_t), s));
+            RUN_TRY(launch_lbi_filter(b, s));
+            RUN_TRY(launch_group_by_query(b, s));
+        }
+        DtwJob jp = js;
+        jp.pairs = l.pairs;
+        jp.npairs = (int64_t)qn * Nc;
+        jp.npairs_dev = pair_total;
+        jp.pair_lbi = pl.mode == DTW_MODE_NOPRUNE ? nullptr : l.pair_lbi;
+        jp.abandon = pl.mode == DTW_MODE_NOPRUNE ? 0 : 1;
+        jp.res = l.pair_res;
+        jp.cursor = cur_pairs;
+        jp.counters = counters;
+        {
+            StageTimer tm(DTW_STAGE_DTW, s);
+            RUN_TRY(launch_dtw_any(jp, pl.g, s));
+        }
+    }
+    {
+        StageTimer tm(DTW_STAGE_FINALIZE, s);
+        RUN_TRY(launch_finalize(b, s));
+    }
+    return cudaSuccess;
+}
+
+void cascade_stats(const CascadePlan &pl, int64_t Q, const unsigned long long *h, dtw_stats *st) {
+    const int64_t N = pl.N;
+    const int64_t seeds = N > 0 ? Q * (int64_t)pl.S : 0;
+    st->candidates += Q * N;
+    st->seeds += seeds;
+    if (pl.summary) {
+        st->pruned_summary += Q * N - seeds - (int64_t)h[CNT_SUMMARY_PASS];
+        st->pruned_keogh += (int64_t)h[CNT_SUMMARY_PASS] - (int64_t)h[CNT_KEOGH_PASS];
+    } else {
+        st->pruned_keogh += Q * N - seeds - (int64_t)h[CNT_KEOGH_PASS];
+    }
+    st->pruned_improved += (int64_t)h[CNT_KEOGH_PASS] - (int64_t)h[CNT_LBI_PASS] + (int64_t)h[CNT_DTW_SKIP];
+    st->dtw_computed += (int64_t)h[CNT_DTW_COMPUTED];
+    st->dtw_abandoned += (int64_t)h[CNT_DTW_ABANDONED];
+    st->dtw_cells += (int64_t)h[CNT_DTW_ROWS] * (2 * pl.we + 1);
+    st->seed_cells += (int64_t)h[CNT_NUM + CNT_DTW_ROWS] * (2 * pl.we + 1);
+}
+
+}  // namespace dtwk

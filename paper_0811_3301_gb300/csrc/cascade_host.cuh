@@ -1,0 +1,76 @@
+// Host-side plan, workspace layout and launch sequence of one cascade run
+// (Algorithms 2/3 for a batch of equal-length queries against one database).
+// Internal: the public ABI is include/dtwknn.h.
+#pragma once
+
+#include "common.cuh"
+#include "dtw.cuh"
+
+namespace dtwk {
+
+// Bump allocator over a workspace block; sizes are rounded to 256 bytes.  With
+// base == nullptr it only measures.
+struct Carve {
+    size_t off = 0;
+    char *base = nullptr;
+    template <typename T>
+    T *take(size_t count) {
+        size_t bytes = (count * sizeof(T) + 255) & ~size_t(255);
+        T *p = reinterpret_cast<T *>(base ? base + off : nullptr);
+        off += bytes;
+        return p;
+    }
+};
+
+// Sizes and parameters of one run: database of N rows of length n, at most Qc
+// queries per run, band w (clamped to n-1), k neighbours.
+struct CascadePlan {
+    int64_t N;
+    int n, we, p, k, mode;
+    DtwGeom g;
+    float slack;
+    int parts;       // piecewise-sum parts d, or -1 (pre-filter off)
+    bool summary;    // parts > 0
+    PartGeom pg;
+    int S;           // seeds per query
+    int64_t Qc;      // queries per run
+    int seg_len;     // candidates per filter segment
+    int filter_warps;
+    int nseg;        // sub-segments per query
+};
+
+// Device buffers of one run, carved from a workspace.
+struct CascadeWs {
+    float *U, *L, *copies, *lb, *PU, *PL, *seed_res, *lbi_u, *pair_lbi, *pair_res;
+    unsigned long long *tile_min, *misc;
+    Pair *seed_pairs, *pairs_u, *pairs;
+    uint32_t *gmin, *bsf;
+    int32_t *qcount, *qstart, *seg_start, *seg_count;
+};
+
+// o.parts: 0 = default (n/8 for n >= 64, else off), -1 = off, else d.
+// o.seeds: 0 = default (16); clamped to [k, 32] and to N.
+CascadePlan make_plan(int64_t N, int64_t Qmax, int n, int w, int p, int k, const dtw_options &o,
+                      int seg_len = 1024);
+CascadeWs carve_ws(const CascadePlan &pl, Carve &cv);
+size_t cascade_ws_bytes(const CascadePlan &pl);
+
+// One run over qn <= pl.Qc queries q [qn][n] (device).  PX [N][parts] and
+// xmax_bits are the database part sums and max |x| (launch_summarize), used
+// when pl.summary.  counters: 2 * CNT_NUM device counters (run counters, then
+// seed-stage counters), accumulated, zeroed by the caller.  Outputs
+// out_idx/out_dist [qn][k] (device).  Asynchronous on s; allocates nothing.
+cudaError_t cascade_run(const CascadePlan &pl, const CascadeWs &ws, const float *db, const float *PX,
+                        const unsigned *xmax_bits, const float *q, int qn, int64_t *out_idx, float *out_dist,
+                        unsigned long long *counters, cudaStream_t s);
+
+// Adds the statistics of Q queries run under pl, from the host copy of the
+// 2 * CNT_NUM counters, to st.
+void cascade_stats(const CascadePlan &pl, int64_t Q, const unsigned long long *h, dtw_stats *st);
+
+// Stage timing (dtw_profile_enable / dtw_profile_read).  Stages launched while
+// a stream is being captured are not timed.
+void profile_set(bool on);
+cudaError_t profile_collect(double *ms, int64_t *launches, bool reset);
+
+}  // namespace dtwk

@@ -132,3 +132,30 @@ def log_uniform_lengths(count: int, lo: int, hi: int, seed: int, stream: int = S
     g = _rng(seed, stream, 1 << 20)
     v = np.exp(g.uniform(np.log(lo), np.log(hi), size=count))
     return np.clip(np.rint(v), lo, hi).astype(np.int64)
+
+
+def snap_to_buckets(lengths, buckets) -> np.ndarray:
+    """Each length replaced by the bucket nearest to it in log space (int64)."""
+    lb = np.log(np.asarray(buckets, dtype=np.float64))
+    ll = np.log(np.asarray(lengths, dtype=np.float64))
+    j = np.argmin(np.abs(ll[:, None] - lb[None, :]), axis=1)
+    return np.asarray(buckets, dtype=np.int64)[j]
+
+
+def mixed_queries(lengths, seed: int, stream: int = STREAM_QUERY) -> list[np.ndarray]:
+    """One random walk per requested length (fp32 1-D arrays), drawn per length
+    bucket in order of appearance so that the values do not depend on the batch."""
+    lengths = np.asarray(lengths, dtype=np.int64)
+    out: list[np.ndarray] = [None] * len(lengths)  # type: ignore[list-item]
+    for n in np.unique(lengths):
+        pos = np.flatnonzero(lengths == n)
+        rows = random_walks(len(pos), int(n), seed=seed * 7919 + int(n), stream=stream)
+        for r, i in enumerate(pos):
+            out[i] = rows[r]
+    return out
+
+
+def poisson_arrivals(count: int, rate: float, seed: int, stream: int = STREAM_QUERY) -> np.ndarray:
+    """Arrival times (seconds, float64, increasing) of a Poisson process of the given rate."""
+    g = _rng(seed, stream, (1 << 20) + 1)
+    return np.cumsum(g.exponential(1.0 / rate, size=count))

@@ -105,3 +105,17 @@ def test_profile_api_without_gpu(native):
     native.profile_enable(False)
     prof = native.profile_read(reset=True)
     assert set(prof) == set(native.STAGE_NAMES)
+
+
+def test_index_rejects_bad_arguments_on_host(native):
+    h = ctypes.c_void_p()
+    st, text = _status(native, lambda: native.lib.dtw_index_create(3, None, ctypes.byref(h)))
+    assert st == 1 and "p=3" in text
+    opt = native.Options(7, 1e-6, 0, 0)
+    st, text = _status(native, lambda: native.lib.dtw_index_create(1, ctypes.byref(opt), ctypes.byref(h)))
+    assert st == 1 and "mode" in text
+    st, text = _status(native, lambda: native.lib.dtw_index_search(None, None, 0, None, None, None, 1, 0, None, None,
+                                                                   None, None))
+    assert st == 1 and "null" in text
+    st, text = _status(native, lambda: native.lib.dtw_index_destroy(None))
+    assert st == 0
