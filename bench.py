@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--seed", type=int, default=2)
     ap.add_argument("--seeds", type=int, default=0, help="seed DTWs per query (0: library default)")
     ap.add_argument("--parts", type=int, default=0, help="piecewise-sum parts (0: default n/8, -1: off)")
+    ap.add_argument("--dtw-path", type=int, default=0, help="DTW kernel: 0 auto, 1 thread per pair, 2 warp per pair")
     ap.add_argument("--no-p2", action="store_true", help="skip the DTW_2 side measurement")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU baseline sample")
     ap.add_argument("--workload", choices=["retrieval", "batched"], default="retrieval",
@@ -258,7 +259,7 @@ def run_ours(a):
             dist.barrier()
             torch.cuda.synchronize()
 
-    kw = {"seeds": a.seeds, "parts": a.parts}
+    kw = {"seeds": a.seeds, "parts": a.parts, "dtw_path": a.dtw_path}
 
     def step(p):
         return api.knn_search(db, qs, a.w, p, a.k, **kw)

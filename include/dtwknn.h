@@ -79,6 +79,9 @@ typedef struct {
                       before LB_Keogh, which then runs only on its survivors; 0 selects
                       the default (n / 8 when n >= 64, else off), -1 disables it (LB_Keogh
                       of every pair), otherwise 1 <= d <= n */
+    int32_t dtw_path; /* DTW kernel of the cascade's DTW stages: 0 chooses (one warp per
+                         pair for long series or wide bands, else one thread per pair),
+                         1 one thread per pair where the band fits, 2 one warp per pair */
 } dtw_options;
 
 /*
@@ -245,7 +248,7 @@ enum {
     DTW_BATCH_PER_QUERY = 8
 };
 
-/* Cascade parameters of one (n, w, k); see dtw_options for parts and seeds.
+/* Cascade parameters of one (n, w, k); see dtw_options for parts, seeds and dtw_path.
  * seg_len: candidates per filter segment (512, 1024 or 2048). ms: time of the
  * tuning sample in milliseconds, or -1 when the values are the defaults. */
 typedef struct {
@@ -253,6 +256,7 @@ typedef struct {
     int32_t seeds;
     int32_t seg_len;
     float ms;
+    int32_t dtw_path; /* as in dtw_options */
 } dtw_tuning;
 
 typedef struct {

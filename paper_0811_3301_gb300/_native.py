@@ -66,16 +66,16 @@ class Profile(ctypes.Structure):
 
 class Options(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("slack", ctypes.c_float), ("seeds", ctypes.c_int32),
-                ("parts", ctypes.c_int32)]
+                ("parts", ctypes.c_int32), ("dtw_path", ctypes.c_int32)]
 
 
 class Tuning(ctypes.Structure):
     _fields_ = [("parts", ctypes.c_int32), ("seeds", ctypes.c_int32), ("seg_len", ctypes.c_int32),
-                ("ms", ctypes.c_float)]
+                ("ms", ctypes.c_float), ("dtw_path", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {"parts": int(self.parts), "seeds": int(self.seeds), "seg_len": int(self.seg_len),
-                "ms": float(self.ms)}
+                "ms": float(self.ms), "dtw_path": int(self.dtw_path)}
 
 
 class IndexStats(ctypes.Structure):

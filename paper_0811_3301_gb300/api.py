@@ -125,7 +125,8 @@ def dtw_band(x: torch.Tensor, y: torch.Tensor, w: int, p: int, threshold: float 
 
 
 def knn_search(db: torch.Tensor, queries: torch.Tensor, w: int, p: int, k: int = 1, *, mode: str = "improved",
-               slack: float = 1e-6, seeds: int = 0, parts: int = 0, out_idx: torch.Tensor | None = None,
+               slack: float = 1e-6, seeds: int = 0, parts: int = 0, dtw_path: int = 0,
+               out_idx: torch.Tensor | None = None,
                out_dist: torch.Tensor | None = None, return_stats: bool = False):
     """Exact k nearest neighbours of each query row under DTW_p with band w (Sec. 7-8).
 
@@ -149,7 +150,7 @@ def knn_search(db: torch.Tensor, queries: torch.Tensor, w: int, p: int, k: int =
         out_dist = torch.empty((Q, k), dtype=torch.float32, device=dev, pin_memory=not queries.is_cuda and torch.cuda.is_available())
     if mode not in _MODES:
         raise ValueError("mode must be one of %s" % sorted(_MODES))
-    opt = N.Options(_MODES[mode], float(slack), int(seeds), int(parts))
+    opt = N.Options(_MODES[mode], float(slack), int(seeds), int(parts), int(dtw_path))
     st = N.Stats()
     N.check(N.lib.knn_search_ex(_ptr(db), db.shape[0], _ptr(queries), Q, n, int(w), int(p), int(k),
                                 ctypes.byref(opt), _ptr(out_idx), _ptr(out_dist),
@@ -177,10 +178,11 @@ class DtwIndex:
     change the speed.
     """
 
-    def __init__(self, p: int, *, mode: str = "improved", slack: float = 1e-6, seeds: int = 0, parts: int = 0):
+    def __init__(self, p: int, *, mode: str = "improved", slack: float = 1e-6, seeds: int = 0, parts: int = 0,
+                 dtw_path: int = 0):
         if mode not in _MODES:
             raise ValueError("mode must be one of %s" % sorted(_MODES))
-        opt = N.Options(_MODES[mode], float(slack), int(seeds), int(parts))
+        opt = N.Options(_MODES[mode], float(slack), int(seeds), int(parts), int(dtw_path))
         h = ctypes.c_void_p()
         N.check(N.lib.dtw_index_create(int(p), ctypes.byref(opt), ctypes.byref(h)))
         self._h = h
@@ -225,8 +227,8 @@ class DtwIndex:
         N.check(N.lib.dtw_index_get_tuning(self._h, int(n), int(w), int(k), ctypes.byref(t)))
         return t.as_dict()
 
-    def set_tuning(self, n: int, w: int, k: int, *, parts: int, seeds: int, seg_len: int) -> None:
-        t = N.Tuning(int(parts), int(seeds), int(seg_len), -1.0)
+    def set_tuning(self, n: int, w: int, k: int, *, parts: int, seeds: int, seg_len: int, dtw_path: int = 0) -> None:
+        t = N.Tuning(int(parts), int(seeds), int(seg_len), -1.0, int(dtw_path))
         N.check(N.lib.dtw_index_set_tuning(self._h, int(n), int(w), int(k), ctypes.byref(t)))
 
     def info(self) -> dict:

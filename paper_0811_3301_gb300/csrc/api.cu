@@ -247,13 +247,14 @@ dtw_status knn_search_ex(const float *db, int64_t N, const float *queries, int64
     if (N < 0 || N > INT32_MAX / 2) return fail(DTW_ERR_INVALID_ARG, "N=%lld out of range", (long long)N);
     if (Q < 0 || Q > INT32_MAX / 2) return fail(DTW_ERR_INVALID_ARG, "Q=%lld out of range", (long long)Q);
     if (k < 1 || k > DTW_MAX_K) return fail(DTW_ERR_INVALID_ARG, "k=%d outside [1, %d]", k, DTW_MAX_K);
-    dtw_options o{DTW_MODE_IMPROVED, 1e-6f, 0, 0};
+    dtw_options o{DTW_MODE_IMPROVED, 1e-6f, 0, 0, 0};
     if (opt) o = *opt;
     if (o.parts < -1 || o.parts > n) return fail(DTW_ERR_INVALID_ARG, "parts=%d outside [-1, n=%d]", o.parts, n);
     if (o.mode < DTW_MODE_IMPROVED || o.mode > DTW_MODE_NOPRUNE)
         return fail(DTW_ERR_INVALID_ARG, "mode=%d unknown", o.mode);
     if (!(o.slack >= 0.0f) || std::isinf(o.slack)) return fail(DTW_ERR_INVALID_ARG, "slack must be finite and >= 0");
     if (o.seeds < 0) return fail(DTW_ERR_INVALID_ARG, "seeds=%d must be >= 0", o.seeds);
+    if (o.dtw_path < 0 || o.dtw_path > 2) return fail(DTW_ERR_INVALID_ARG, "dtw_path=%d outside [0, 2]", o.dtw_path);
     if (stats) memset(stats, 0, sizeof(*stats));
     if (Q == 0) return DTW_OK;
     if (!queries || !out_idx || !out_dist || (N > 0 && !db)) return fail(DTW_ERR_INVALID_ARG, "null pointer");

@@ -22,7 +22,8 @@ __device__ __forceinline__ unsigned long long pack_key(float d, int c) {
 // the bulk of the candidates is filtered; this is the GPU counterpart of
 // visiting candidates in order of their lower bound.  One CTA per query;
 // each thread keeps a sorted list of its kSeedMax best keys, then S rounds of
-// a block-wide minimum pop the global best.
+// a block-wide minimum pop the global best.  The seed of rank s of query q is
+// stored at s * Q + q, so the k best-bounded seeds of every query come first.
 // Also resets the query's thresholds to +INF.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_seed_select(CascadeBufs b) {
@@ -67,8 +68,8 @@ __global__ void __launch_bounds__(256) k_seed_select(CascadeBufs b) {
             for (int v = 1; v < (int)(blockDim.x >> 5); ++v) best = wmin[v] < best ? wmin[v] : best;
             winner = best;
             int c = (best == ~0ull) ? -1 : (int)(unsigned)(best & 0xffffffffull);
-            b.seed_pairs[(int64_t)q * b.S + s] = Pair{q, c};
-            b.seed_res[(int64_t)q * b.S + s] = kInf;
+            b.seed_pairs[(int64_t)s * b.Q + q] = Pair{q, c};
+            b.seed_res[(int64_t)s * b.Q + q] = kInf;
         }
         __syncthreads();
         if (key[0] == winner && winner != ~0ull) {
@@ -94,8 +95,8 @@ __global__ void k_seed_kth(CascadeBufs b) {
     if (q >= b.Q) return;
     unsigned long long mine = ~0ull;
     if (lane < b.S) {
-        Pair pr = b.seed_pairs[(int64_t)q * b.S + lane];
-        float d = b.seed_res[(int64_t)q * b.S + lane];
+        Pair pr = b.seed_pairs[(int64_t)lane * b.Q + q];
+        float d = b.seed_res[(int64_t)lane * b.Q + q];
         if (pr.c >= 0 && d < kInf) mine = pack_key(d, pr.c);
     }
     int rank = 0;
@@ -130,8 +131,8 @@ __global__ void __launch_bounds__(256) k_finalize(CascadeBufs b) {
     for (int r = 0; r < b.k; ++r) {
         unsigned long long m = ~0ull;
         for (int s = t; s < b.S; s += blockDim.x) {
-            Pair pr = b.seed_pairs[(int64_t)q * b.S + s];
-            float d = b.seed_res[(int64_t)q * b.S + s];
+            Pair pr = b.seed_pairs[(int64_t)s * b.Q + q];
+            float d = b.seed_res[(int64_t)s * b.Q + q];
             if (pr.c >= 0 && d < kInf && d <= bq) {
                 unsigned long long v = pack_key(d, pr.c);
                 if ((first || v > last) && v < m) m = v;

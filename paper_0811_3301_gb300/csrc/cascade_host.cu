@@ -86,6 +86,22 @@ static cudaError_t launch_dtw_any(const DtwJob &j, const DtwGeom &g, cudaStream_
     return j.p == 1 ? launch_dtw_p1(j, g, s) : launch_dtw_p2(j, g, s);
 }
 
+// One warp per pair (dtw_lanes.cuh) or one thread per pair for a DTW stage of
+// at most `npairs` pairs.  A thread-per-pair DTW of a long series takes
+// n (2w+1) dependent cell updates, so when the pairs are too few to fill the
+// GPU (about 2^17 threads) the stage time is that latency; the warp path
+// shortens it many-fold.  That is the case of the seeds of long series.  The
+// main stage lists many pairs, where one thread per pair has the higher
+// throughput, unless the caller (or the autotuner) asks for the warp path.
+// Bands wider than one thread's registers always take the warp path.
+static int use_lanes(const CascadePlan &pl, int64_t npairs, bool main_stage) {
+    if (dtw_lanes_cl(pl.n, pl.we) == 0) return 0;
+    if (pl.dtw_path == 2) return 1;
+    if (pl.dtw_path == 1) return 0;
+    if (main_stage) return 0;
+    return (pl.n >= 512 && npairs < ((int64_t)1 << 17)) ? 1 : 0;
+}
+
 // ---------------------------------------------------------------------------
 // plan and workspace
 // ---------------------------------------------------------------------------
@@ -119,6 +135,7 @@ CascadePlan make_plan(int64_t N, int64_t Qmax, int n, int w, int p, int k, const
     if (Qc < 1) Qc = 1;
     pl.Qc = Qc;
     pl.seg_len = seg_len;
+    pl.dtw_path = o.dtw_path;
     pl.filter_warps = lbi_filter_warps(n, pl.we, std::max(pl.S, 1), pl.seg_len);
     pl.nseg = N > 0 ? (int)((N + pl.seg_len - 1) / pl.seg_len) * pl.filter_warps : 1;
     return pl;
@@ -241,6 +258,12 @@ cudaError_t cascade_run(const CascadePlan &pl, const CascadeWs &l, const float *
             StageTimer tm(DTW_STAGE_SEED_SELECT, s);
             RUN_TRY(launch_seed_select(b, s));
         }
+        // Seeds.  On the warp path, where each warp computes its seeds one
+        // after another, they run with early abandoning against the live
+        // threshold, which the seeds that complete first set and lower (an
+        // abandoned seed's DTW exceeds a threshold that is itself at least the
+        // final k-th best distance, so it cannot be a neighbour).  One thread
+        // per pair runs all seeds at once, so there the checks would only cost.
         DtwJob js{};
         js.db = db;
         js.n = n;
@@ -253,10 +276,11 @@ cudaError_t cascade_run(const CascadePlan &pl, const CascadeWs &l, const float *
         js.slack = pl.slack;
         js.bsf = l.bsf;
         js.gmin = l.gmin;
-        js.abandon = 0;
         js.res = l.seed_res;
         js.cursor = cur_seed;
         js.counters = seed_counters;
+        js.lanes = use_lanes(pl, js.npairs, false);
+        js.abandon = (js.lanes && pl.mode != DTW_MODE_NOPRUNE) ? 1 : 0;
         {
             StageTimer tm(DTW_STAGE_SEED_DTW, s);
             RUN_TRY(launch_dtw_any(js, pl.g, s));
@@ -280,6 +304,7 @@ cudaError_t cascade_run(const CascadePlan &pl, const CascadeWs &l, const float *
         jp.res = l.pair_res;
         jp.cursor = cur_pairs;
         jp.counters = counters;
+        jp.lanes = use_lanes(pl, jp.npairs, true);
         {
             StageTimer tm(DTW_STAGE_DTW, s);
             RUN_TRY(launch_dtw_any(jp, pl.g, s));

@@ -57,6 +57,20 @@ inline DtwGeom dtw_geom(int n, int w) {
     return g;
 }
 
+// Warp path (dtw_lanes.cuh): slots per lane CL for the band 2w+1, from the
+// instantiated set, or 0 when the band needs more than 32 * 32 slots.
+inline int dtw_lanes_cl(int n, int w) {
+    w = w < n - 1 ? w : n - 1;
+    const int need = (2 * w + 1 + 31) / 32;
+    const int set[] = {2, 3, 4, 5, 6, 7, 8, 10, 12, 13, 16, 20, 24, 32};
+    for (int c : set)
+        if (c >= need) return c;
+    return 0;
+}
+
+cudaError_t launch_dtw_lanes_p1(const DtwJob &j, const DtwGeom &g, int cl, cudaStream_t s);
+cudaError_t launch_dtw_lanes_p2(const DtwJob &j, const DtwGeom &g, int cl, cudaStream_t s);
+
 cudaError_t launch_dtw_p1(const DtwJob &j, const DtwGeom &g, cudaStream_t s);
 cudaError_t launch_dtw_p2(const DtwJob &j, const DtwGeom &g, cudaStream_t s);
 

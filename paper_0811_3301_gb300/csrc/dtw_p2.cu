@@ -18,6 +18,8 @@ int blocks_for(K kernel, int64_t warps_needed) {
 
 cudaError_t launch_dtw_p2(const DtwJob &j, const DtwGeom &g, cudaStream_t s) {
     if (j.npairs <= 0) return cudaSuccess;
+    const int cl = dtw_lanes_cl(j.n, j.w);
+    if ((j.lanes || g.wide) && cl > 0) return launch_dtw_lanes_p2(j, g, cl, s);
     if (!g.wide && g.C <= kDtwGroupMaxC) {
         const int64_t warps = (j.npairs + 31) / 32;
         const bool xvec = (j.n % 4 == 0) && ((reinterpret_cast<uintptr_t>(j.db) & 15) == 0);

@@ -205,6 +205,7 @@ Tuning tuning_for(const dtw_index *ix, int n, int w, int k) {
     t.seeds = ix->opt.seeds;
     t.seg_len = 1024;
     t.ms = -1.0f;
+    t.dtw_path = ix->opt.dtw_path;
     return t;
 }
 
@@ -213,6 +214,7 @@ CascadePlan plan_for(const dtw_index *ix, int b, int w, int k, int64_t qmax, con
     dtw_options o = ix->opt;
     o.parts = t.parts;
     o.seeds = t.seeds;
+    o.dtw_path = t.dtw_path;
     return make_plan(bk.N, qmax, bk.n, w, ix->p, k, o, t.seg_len);
 }
 
@@ -394,7 +396,8 @@ static cudaError_t enqueue_batch(dtw_index *ix, Slot &sl, const Batch &bt, const
 static std::vector<int64_t> graph_key(const Batch &bt) {
     std::vector<int64_t> key{bt.Q, bt.k_stride, bt.total, bt.flags, (int64_t)bt.groups.size()};
     for (const auto &gr : bt.groups) {
-        key.insert(key.end(), {gr.bucket, gr.w, gr.k, gr.qn, gr.pl.parts, gr.pl.S, gr.pl.seg_len, gr.stream});
+        key.insert(key.end(),
+                   {gr.bucket, gr.w, gr.k, gr.qn, gr.pl.parts, gr.pl.S, gr.pl.seg_len, gr.pl.dtw_path, gr.stream});
     }
     return key;
 }
@@ -488,8 +491,8 @@ size_t batch_bytes(const Batch &bt) {
 // Times candidate parameter sets on `qn` queries (device) of bucket b and
 // keeps the fastest.  The result of the search does not depend on the
 // parameters (the cascade is exact); only its speed does.  Coordinate descent:
-// parts, then seeds, then the filter segment length, each with the others at
-// their best so far.
+// parts, then seeds, then the filter segment length, then the DTW kernel
+// (thread or warp per pair), each with the others at their best so far.
 dtw_status tune_group(dtw_index *ix, int b, int w, int k, const float *qdev, int qn, Tuning *out) {
     const Bucket &bk = ix->buckets[b];
     const int n = bk.n;
@@ -504,13 +507,15 @@ dtw_status tune_group(dtw_index *ix, int b, int w, int k, const float *qdev, int
     for (int sd : {std::max(k, 4), 8, 16, 32})
         if (sd >= k && sd <= 32 && std::find(seeds_c.begin(), seeds_c.end(), sd) == seeds_c.end()) seeds_c.push_back(sd);
     const std::vector<int> seg_c{512, 1024, 2048};
+    std::vector<int> path_c{1};
+    if (dtw_lanes_cl(n, we) > 0) path_c.push_back(2);
 
     // scratch sized for the largest candidate plan
     size_t ws_max = 0;
     for (int pc : parts_c)
         for (int sd : seeds_c)
             for (int sg : seg_c) {
-                Tuning t{pc, sd, sg, 0.0f};
+                Tuning t{pc, sd, sg, 0.0f, 0};
                 ws_max = std::max(ws_max, cascade_ws_bytes(plan_for(ix, b, we, k, qn, t)));
             }
     Carve cv0;
@@ -569,16 +574,20 @@ dtw_status tune_group(dtw_index *ix, int b, int w, int k, const float *qdev, int
     best.parts = ix->opt.parts == 0 ? (n >= 64 ? n / 8 : -1) : ix->opt.parts;
     best.seeds = ix->opt.seeds > 0 ? ix->opt.seeds : 16;
     best.seg_len = 1024;
+    best.dtw_path = ix->opt.dtw_path;
     float best_ms = INFINITY;
     if ((st = time_one(best, &best_ms)) != DTW_OK) goto done;
-    for (int axis = 0; axis < 3; ++axis) {
-        const std::vector<int> &cands = axis == 0 ? parts_c : axis == 1 ? seeds_c : seg_c;
+    for (int axis = 0; axis < 4; ++axis) {
+        const std::vector<int> &cands = axis == 0 ? parts_c : axis == 1 ? seeds_c : axis == 2 ? seg_c : path_c;
         for (int v : cands) {
             Tuning t = best;
             if (axis == 0) t.parts = v;
             if (axis == 1) t.seeds = v;
             if (axis == 2) t.seg_len = v;
-            if (t.parts == best.parts && t.seeds == best.seeds && t.seg_len == best.seg_len) continue;
+            if (axis == 3) t.dtw_path = v;
+            if (t.parts == best.parts && t.seeds == best.seeds && t.seg_len == best.seg_len &&
+                t.dtw_path == best.dtw_path)
+                continue;
             float ms = INFINITY;
             if ((st = time_one(t, &ms)) != DTW_OK) goto done;
             if (ms < best_ms) {
@@ -662,13 +671,14 @@ dtw_status dtw_index_create(int32_t p, const dtw_options *opt, dtw_index **out) 
     if (!out) return ix_fail(DTW_ERR_INVALID_ARG, "null pointer");
     *out = nullptr;
     if (p != 1 && p != 2) return ix_fail(DTW_ERR_INVALID_ARG, "p=%d must be 1 or 2", p);
-    dtw_options o{DTW_MODE_IMPROVED, 1e-6f, 0, 0};
+    dtw_options o{DTW_MODE_IMPROVED, 1e-6f, 0, 0, 0};
     if (opt) o = *opt;
     if (o.mode < DTW_MODE_IMPROVED || o.mode > DTW_MODE_NOPRUNE)
         return ix_fail(DTW_ERR_INVALID_ARG, "mode=%d unknown", o.mode);
     if (!(o.slack >= 0.0f) || std::isinf(o.slack)) return ix_fail(DTW_ERR_INVALID_ARG, "slack must be finite and >= 0");
     if (o.seeds < 0) return ix_fail(DTW_ERR_INVALID_ARG, "seeds=%d must be >= 0", o.seeds);
     if (o.parts < -1) return ix_fail(DTW_ERR_INVALID_ARG, "parts=%d must be >= -1", o.parts);
+    if (o.dtw_path < 0 || o.dtw_path > 2) return ix_fail(DTW_ERR_INVALID_ARG, "dtw_path=%d outside [0, 2]", o.dtw_path);
     auto *ix = new dtw_index();
     ix->p = p;
     ix->opt = o;
@@ -746,6 +756,7 @@ dtw_status dtw_index_tune(dtw_index *ix, const float *sample, int64_t count, int
         out->seeds = t.seeds;
         out->seg_len = t.seg_len;
         out->ms = t.ms;
+        out->dtw_path = t.dtw_path;
     }
     return st;
 }
@@ -761,6 +772,7 @@ dtw_status dtw_index_get_tuning(dtw_index *ix, int32_t n, int32_t w, int32_t k, 
     out->seeds = t.seeds;
     out->seg_len = t.seg_len;
     out->ms = t.ms;
+    out->dtw_path = t.dtw_path;
     return DTW_OK;
 }
 
@@ -768,13 +780,14 @@ dtw_status dtw_index_set_tuning(dtw_index *ix, int32_t n, int32_t w, int32_t k, 
     set_error_message("");
     if (!ix || !t) return ix_fail(DTW_ERR_INVALID_ARG, "null pointer");
     if (t->parts < -1 || t->parts > n || t->seeds < 0 || t->seeds > 32 ||
-        (t->seg_len != 512 && t->seg_len != 1024 && t->seg_len != 2048))
-        return ix_fail(DTW_ERR_INVALID_ARG, "tuning out of range (parts in [-1, n], seeds in [0, 32], seg_len 512/1024/2048)");
+        (t->seg_len != 512 && t->seg_len != 1024 && t->seg_len != 2048) || t->dtw_path < 0 || t->dtw_path > 2)
+        return ix_fail(DTW_ERR_INVALID_ARG,
+                       "tuning out of range (parts in [-1, n], seeds in [0, 32], seg_len 512/1024/2048, dtw_path 0-2)");
     if (w < 0 || k < 1 || k > DTW_MAX_K) return ix_fail(DTW_ERR_INVALID_ARG, "w or k out of range");
     std::lock_guard<std::mutex> lk(ix->mu);
     if (find_bucket(ix, n) < 0) return ix_fail(DTW_ERR_NO_BUCKET, "no bucket of length %d", n);
     const int we = w < n - 1 ? w : n - 1;
-    ix->tuned[TuneKey{n, we, k}] = Tuning{t->parts, t->seeds, t->seg_len, t->ms};
+    ix->tuned[TuneKey{n, we, k}] = Tuning{t->parts, t->seeds, t->seg_len, t->ms, t->dtw_path};
     return DTW_OK;
 }
 

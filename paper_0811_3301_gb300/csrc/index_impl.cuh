@@ -67,7 +67,8 @@ struct TuneKey {
 
 struct Tuning {
     int parts, seeds, seg_len;
-    float ms;  // time of the tuning sample, -1 if not tuned
+    float ms;      // time of the tuning sample, -1 if not tuned
+    int dtw_path;  // as in dtw_options
 };
 
 // Queries of one batch with equal (bucket, w, k).

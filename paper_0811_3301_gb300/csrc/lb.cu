@@ -713,7 +713,7 @@ __global__ void __launch_bounds__(256, 3) k_lbi_filter(CascadeBufs b, bool vec) 
     int32_t *seeds = reinterpret_cast<int32_t *>(scratch_all + (size_t)nw * lbi_scratch_floats(n, w));
     int32_t *surv_c = seeds + b.S + (size_t)wid * 2 * per_warp_cap;
     float *surv_v = reinterpret_cast<float *>(surv_c + per_warp_cap);
-    for (int t = threadIdx.x; t < b.S; t += blockDim.x) seeds[t] = b.seed_pairs[(int64_t)q * b.S + t].c;
+    for (int t = threadIdx.x; t < b.S; t += blockDim.x) seeds[t] = b.seed_pairs[(int64_t)t * b.Q + q].c;
     LbiQuery<MT> Qv;
     if (b.lbi_inline || b.summary) {
         lbi_load_query<MT>(Qv, b.queries + (int64_t)q * n, b.U + (int64_t)q * n, b.L + (int64_t)q * n, n, sq);

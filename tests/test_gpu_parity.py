@@ -239,6 +239,24 @@ def test_knn_seed_count(api, seeds):
     _knn_case(api, db, qs, 6, 1, 3, seeds=seeds)
 
 
+WARP_CASES = [(1, 0, 3), (33, 0, 1), (40, 3, 2), (96, 9, 1), (128, 12, 10), (256, 25, 1), (512, 51, 3),
+              (1024, 102, 1), (700, 150, 2), (1024, 204, 1), (900, 400, 1)]
+
+
+@pytest.mark.parametrize("p", [1, 2])
+@pytest.mark.parametrize("n,w,k", WARP_CASES)
+def test_knn_warp_dtw_path(api, p, n, w, k):
+    # one warp per pair (two pairs per warp, wavefront abandoning) for every
+    # DTW stage; the thread-per-pair kernels evaluate the same cells with the
+    # same fp32 operations, so both paths give identical results
+    N = 400 if n >= 512 else 900
+    db = synth.random_walks(N, n, seed=30 + n)
+    qs = synth.random_walks(4, n, seed=30 + n, stream=synth.STREAM_QUERY)
+    wi, wd, _ = _knn_case(api, db, qs, w, p, k, dtw_path=2)
+    ti, td = api.knn_search(cuda(db), cuda(qs), w, p, k, dtw_path=1)
+    assert torch.equal(wi, ti) and torch.equal(wd, td)
+
+
 def test_knn_edge_cases(api):
     # k > N pads with -1 / +inf; N = 1; n = 1; odd n (scalar load path); w = 0; w >= n
     db = synth.random_walks(5, 33, seed=5)
