@@ -61,7 +61,7 @@ def parse():
     ap.add_argument("--dtw-path", type=int, default=0, help="DTW kernel: 0 auto, 1 thread per pair, 2 warp per pair")
     ap.add_argument("--no-p2", action="store_true", help="skip the DTW_2 side measurement")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU baseline sample")
-    ap.add_argument("--workload", choices=["retrieval", "batched"], default="retrieval",
+    ap.add_argument("--workload", choices=["retrieval", "batched", "serve"], default="retrieval",
                     help="retrieval: one length, one knn_search per step (default); batched: mixed-length "
                          "batches against length buckets through the index")
     ap.add_argument("--bucket-N", type=int, default=20_000, help="batched: series per length bucket")
@@ -69,6 +69,12 @@ def parse():
     ap.add_argument("--batch-ks", default="1,10", help="batched: neighbour counts, one run each")
     ap.add_argument("--batch-arms", default="graph,streams,serial,per_query",
                     help="batched: execution arms to time")
+    ap.add_argument("--serve-rates", default="1000,5000,20000", help="serve: Poisson arrival rates (queries/s)")
+    ap.add_argument("--serve-seconds", type=float, default=2.0, help="serve: arrival window per rate")
+    ap.add_argument("--serve-scale", type=float, default=1.0,
+                    help="serve: database size factor (1.0: 1,000,000 x 256 + 200,000 x 1024)")
+    ap.add_argument("--serve-secondary", action="store_true",
+                    help="serve: also run with small buckets for lengths 128, 512 and 2048")
     return ap.parse_args()
 
 
@@ -479,6 +485,119 @@ def run_batched(a):
     return out
 
 
+def serve_run(api, ix, lens, queries, ks, arrivals, **cfg):
+    """Submits requests at their arrival times (seconds from start) to a new
+    server and collects completions; returns latency and throughput figures."""
+    import threading as th
+
+    srv = api.DtwServer(ix, **cfg)
+    Q = len(lens)
+    tickets = [0] * Q
+    got = {}
+    done_flag = th.Event()
+
+    def poller():
+        while not done_flag.is_set() or len(got) < Q:
+            for c in srv.poll(wait_ms=20):
+                got[c["ticket"]] = c
+            if done_flag.is_set() and len(got) >= Q:
+                break
+
+    pt = th.Thread(target=poller, daemon=True)
+    pt.start()
+    t0 = api.monotonic_ns() + 20_000_000
+    sched = t0 + (np.asarray(arrivals) * 1e9).astype(np.int64)
+    for i in range(Q):
+        while api.monotonic_ns() < sched[i]:
+            pass
+        tickets[i] = srv.submit(queries[i], int(lens[i]) // 10, int(ks[i]), arrival_ns=int(sched[i]))
+    deadline = time.time() + 600
+    while len(got) < Q and time.time() < deadline:
+        time.sleep(0.005)
+    done_flag.set()
+    pt.join(timeout=5)
+    info = srv.info()
+    srv.close()
+    comp = [got[t] for t in tickets if t in got]
+    lat = np.array([(c["done_ns"] - c["arrival_ns"]) / 1e6 for c in comp])
+    wait = np.array([(c["admit_ns"] - c["arrival_ns"]) / 1e6 for c in comp])
+    first = min(c["arrival_ns"] for c in comp)
+    last = max(c["done_ns"] for c in comp)
+    return {"offered_qps": Q / float(arrivals[-1]) if Q > 1 else None, "requests": Q, "completed": len(comp),
+            "failed": sum(1 for c in comp if c["status"] != 0),
+            "throughput_qps": len(comp) / ((last - first) / 1e9),
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(lat.mean()), "queue_p50_ms": float(np.percentile(wait, 50)),
+            "queue_p99_ms": float(np.percentile(wait, 99)), "batches": info["batches"],
+            "mean_batch": len(comp) / max(1, info["batches"]), "max_batch": info["max_batch_seen"],
+            "max_inflight_batches": info["max_inflight_batches"]}, comp
+
+
+def run_serve(a):
+    """Poisson arrivals of single k-NN queries (DTW_1, half 1-NN and half
+    10-NN, w = floor(n/10)) against a resident database of 1,000,000 random
+    walks of length 256 and 200,000 of length 1024; query lengths drawn from
+    {256, 1024} (the lengths with a bucket).  The continuous-batching server
+    (4 slots, admission by a per-slot workspace of 8 GiB) is compared with the
+    same server restricted to one query per launch, one at a time."""
+    import torch
+
+    from paper_0811_3301_gb300 import build
+
+    build.build()
+    from paper_0811_3301_gb300 import api
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    sizes = {256: int(1_000_000 * a.serve_scale), 1024: int(200_000 * a.serve_scale)}
+    lengths = [256, 1024]
+    if a.serve_secondary:
+        for n in (128, 512, 2048):
+            sizes[n] = int(100_000 * a.serve_scale)
+        lengths = [128, 256, 512, 1024, 2048]
+    ix = api.DtwIndex(1)
+    for n in sorted(sizes):
+        ix.add_bucket(torch.from_numpy(synth.random_walks(sizes[n], n, seed=a.seed + 5000 + n)).to(dev))
+    torch.cuda.synchronize()
+    sampler = ClockSampler(0)
+    t_wall0 = time.time()
+    runs = []
+    for rate in [float(x) for x in a.serve_rates.split(",") if x]:
+        Q = max(50, int(rate * a.serve_seconds))
+        g = np.random.default_rng([a.seed, int(rate)])
+        lens = g.choice(lengths, size=Q)
+        ks = g.choice([1, 10], size=Q)
+        qs = [np.ascontiguousarray(x) for x in synth.mixed_queries(lens, seed=a.seed + int(rate))]
+        arr = synth.poisson_arrivals(Q, rate, seed=a.seed + int(rate))
+        # warm-up: a few requests through a throwaway server
+        serve_run(api, ix, lens[:64], qs[:64], ks[:64], np.linspace(0.0, 0.01, 64), slots=4, max_batch=512,
+                  slot_bytes=8 << 30)
+        res, comp = serve_run(api, ix, lens, qs, ks, arr, slots=4, max_batch=512, slot_bytes=8 << 30)
+        # the plain arm: one query per launch of each stage, one query at a time,
+        # on a bounded prefix of the same stream (it saturates far below these rates)
+        Qp = min(Q, max(50, int(2.0 * 300)))
+        plain, pcomp = serve_run(api, ix, lens[:Qp], qs[:Qp], ks[:Qp], arr[:Qp], slots=1, max_batch=1,
+                                 per_query=True, slot_bytes=8 << 30)
+        same = all(np.array_equal(x["idx"], y["idx"]) and np.array_equal(x["dist"], y["dist"])
+                   for x, y in zip(comp[:Qp], pcomp))
+        runs.append({"rate_qps": rate, "batched": res, "plain": plain, "plain_same_results": bool(same)})
+    t_wall1 = time.time()
+    clocks = sampler.summary(t_wall0, t_wall1)
+    sampler.stop()
+    best = max(runs, key=lambda r: r["batched"]["throughput_qps"])
+    return {
+        "metric": "exact k-NN DTW queries/s and p50/p99 latency, Poisson arrivals, continuous batching",
+        "value": best["batched"]["throughput_qps"], "unit": "queries/s", "n_gpus": 1,
+        "p50_ms": best["batched"]["p50_ms"], "p99_ms": best["batched"]["p99_ms"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded random walks)",
+        "config": {"workload": "serving: Poisson arrivals at %s q/s, query lengths from %s, resident random walks %s, "
+                               "w = floor(n/10), DTW_1, 1-NN/10-NN mixed 50/50"
+                               % (a.serve_rates, lengths, {int(k): v for k, v in sizes.items()}),
+                   "server": {"slots": 4, "max_batch": 512, "slot_bytes": 8 << 30}},
+        "runs": runs, "index": ix.info(), "clocks": clocks,
+    }
+
+
 def run_reference(a):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -516,6 +635,8 @@ def main():
         out = run_reference(a)
     elif a.workload == "batched":
         out = run_batched(a)
+    elif a.workload == "serve":
+        out = run_serve(a)
     else:
         out = run_ours(a)
     if out is not None:

@@ -307,6 +307,71 @@ dtw_status dtw_index_info(dtw_index *ix, dtw_index_stats *out);
 /* Frees the index (waits for its work). */
 dtw_status dtw_index_destroy(dtw_index *ix);
 
+/*
+ * Request server: continuous batching of k-NN queries over an index.  Each
+ * request (one query of any length that has a bucket, its band w and k) is
+ * queued on arrival.  A scheduler thread owns `slots` batch slots; each slot
+ * has its own device arena of slot_bytes (reserved at creation, never grown),
+ * pinned staging buffers and streams.  Whenever a slot is free it admits the
+ * oldest waiting requests, as many as the arena holds (admission by memory)
+ * and at most max_batch, and launches them as one batch (dtw_index_search's
+ * execution); batches of different slots run on the device at the same time,
+ * so requests that arrive while others are on the GPU start as soon as a slot
+ * frees.  max_wait_us > 0 lets a partial batch wait that long for more
+ * arrivals while another batch is running.  Each request's result equals
+ * what knn_search gives it alone.  The paper has no counterpart: this is the
+ * deployment layer around its method.
+ */
+typedef struct dtw_server dtw_server;
+
+typedef struct {
+    int32_t slots;      /* batches in flight at once, 1..16 (default 4) */
+    int32_t max_batch;  /* requests per batch, 1..65536 (default 512) */
+    int64_t slot_bytes; /* device arena per slot; 0: 2 GiB */
+    int32_t max_wait_us;
+    int32_t flags;      /* DTW_BATCH_GRAPH, DTW_BATCH_SERIAL or DTW_BATCH_PER_QUERY for every batch */
+} dtw_server_config;
+
+typedef struct {
+    uint64_t ticket;
+    int32_t status;     /* DTW_OK, or the error that ended the request's batch */
+    int32_t k;
+    int64_t arrival_ns; /* dtw_monotonic_ns clock */
+    int64_t admit_ns;   /* its batch was formed */
+    int64_t done_ns;    /* its results were in the caller's buffers */
+} dtw_completion;
+
+typedef struct {
+    int64_t submitted, completed, failed, batches;
+    int64_t max_inflight_batches, max_batch_seen;
+    int64_t pending, inflight_batches;
+} dtw_server_stats;
+
+/* Starts a server on ix (which must outlive it); cfg may be NULL (defaults).
+ * Reserves slots * slot_bytes of device memory. */
+dtw_status dtw_server_create(dtw_index *ix, const dtw_server_config *cfg, dtw_server **out);
+
+/* Queues one request: query [n] (host, copied), band w, k neighbours.  Its
+ * result is written to out_idx [k] and out_dist [k] (host memory that must
+ * stay valid until the request's completion is polled).  arrival_ns (0: now)
+ * is the request's arrival time on the dtw_monotonic_ns clock.  Fails with
+ * DTW_ERR_NO_BUCKET when no bucket has length n, DTW_ERR_OOM when a batch of
+ * this request alone does not fit slot_bytes. */
+dtw_status dtw_server_submit(dtw_server *srv, const float *query, int32_t n, int32_t w, int32_t k,
+                             int64_t *out_idx, float *out_dist, int64_t arrival_ns, uint64_t *ticket);
+
+/* Takes up to max completion records (waiting up to wait_ms for the first). */
+dtw_status dtw_server_poll(dtw_server *srv, dtw_completion *out, int32_t max, int32_t *count,
+                           int32_t wait_ms);
+
+dtw_status dtw_server_info(dtw_server *srv, dtw_server_stats *out);
+
+/* Completes every queued request, then stops the scheduler and frees the server. */
+dtw_status dtw_server_destroy(dtw_server *srv);
+
+/* The server's clock (CLOCK_MONOTONIC), nanoseconds. */
+int64_t dtw_monotonic_ns(void);
+
 /* Message of the last failed call on this host thread ("" if none). */
 const char *dtw_last_error(void);
 

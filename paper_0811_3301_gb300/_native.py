@@ -89,6 +89,25 @@ class IndexStats(ctypes.Structure):
 
 BATCH_GRAPH, BATCH_AUTOTUNE, BATCH_SERIAL, BATCH_PER_QUERY = 1, 2, 4, 8
 
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("slot_bytes", ctypes.c_int64),
+                ("max_wait_us", ctypes.c_int32), ("flags", ctypes.c_int32)]
+
+
+class Completion(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_uint64), ("status", ctypes.c_int32), ("k", ctypes.c_int32),
+                ("arrival_ns", ctypes.c_int64), ("admit_ns", ctypes.c_int64), ("done_ns", ctypes.c_int64)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_int64) for name in ("submitted", "completed", "failed", "batches",
+                                                     "max_inflight_batches", "max_batch_seen", "pending",
+                                                     "inflight_batches")]
+
+    def as_dict(self) -> dict:
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
 _vp = ctypes.c_void_p
 _i64 = ctypes.c_int64
 _i32 = ctypes.c_int32
@@ -115,6 +134,11 @@ SIGNATURES = {
     "dtw_index_search": [_vp, _vp, _i64, _vp, _vp, _vp, _i32, _i32, _vp, _vp, ctypes.POINTER(Stats), _vp],
     "dtw_index_info": [_vp, ctypes.POINTER(IndexStats)],
     "dtw_index_destroy": [_vp],
+    "dtw_server_create": [_vp, ctypes.POINTER(ServerConfig), ctypes.POINTER(_vp)],
+    "dtw_server_submit": [_vp, _vp, _i32, _i32, _i32, _vp, _vp, _i64, ctypes.POINTER(ctypes.c_uint64)],
+    "dtw_server_poll": [_vp, _vp, _i32, ctypes.POINTER(_i32), _i32],
+    "dtw_server_info": [_vp, ctypes.POINTER(ServerStats)],
+    "dtw_server_destroy": [_vp],
 }
 
 
@@ -130,6 +154,8 @@ def _load():
     lib.dtw_last_error.restype = ctypes.c_char_p
     lib.dtw_version.argtypes = []
     lib.dtw_version.restype = ctypes.c_char_p
+    lib.dtw_monotonic_ns.argtypes = []
+    lib.dtw_monotonic_ns.restype = ctypes.c_int64
     return lib
 
 

@@ -17,7 +17,7 @@ import torch
 from . import _native as N
 
 __all__ = ["dtw_envelope", "lb_keogh", "lb_piecewise", "lb_improved", "dtw_band", "knn_search", "DtwIndex",
-           "DtwError", "version"]
+           "DtwServer", "DtwError", "monotonic_ns", "version"]
 
 DtwError = N.DtwError
 version = N.version
@@ -279,3 +279,77 @@ class DtwIndex:
             raise ValueError("no queries")
         lengths = [q.numel() for q in qs]
         return self.search_flat(torch.cat(qs), lengths, w, k, **kw)
+
+
+def monotonic_ns() -> int:
+    """The request server's clock (CLOCK_MONOTONIC), in nanoseconds."""
+    return int(N.lib.dtw_monotonic_ns())
+
+
+class DtwServer:
+    """Continuous-batching request server over a DtwIndex (the dtw_server_* calls).
+
+    submit() queues one query and returns a ticket; poll() returns finished
+    requests with their neighbours and their arrival, admission and
+    completion times.  The index must outlive the server and must not change
+    while it runs.
+    """
+
+    def __init__(self, index: DtwIndex, *, slots: int = 4, max_batch: int = 512, slot_bytes: int = 0,
+                 max_wait_us: int = 0, graph: bool = False, serial: bool = False, per_query: bool = False):
+        flags = ((N.BATCH_GRAPH if graph else 0) | (N.BATCH_SERIAL if serial else 0) |
+                 (N.BATCH_PER_QUERY if per_query else 0))
+        cfg = N.ServerConfig(int(slots), int(max_batch), int(slot_bytes), int(max_wait_us), flags)
+        h = ctypes.c_void_p()
+        N.check(N.lib.dtw_server_create(index._h, ctypes.byref(cfg), ctypes.byref(h)))
+        self._h = h
+        self._index = index  # keeps the index alive
+        self._out: dict[int, tuple] = {}
+        self._buf = (N.Completion * 4096)()
+
+    def submit(self, query, w: int, k: int, arrival_ns: int = 0) -> int:
+        """Queues one query (1-D float32, host); returns its ticket."""
+        q = np.ascontiguousarray(np.asarray(query, dtype=np.float32).reshape(-1))
+        oi = np.empty(int(k), np.int64)
+        od = np.empty(int(k), np.float32)
+        t = ctypes.c_uint64()
+        N.check(N.lib.dtw_server_submit(self._h, q.ctypes.data, q.shape[0], int(w), int(k), oi.ctypes.data,
+                                        od.ctypes.data, int(arrival_ns), ctypes.byref(t)))
+        self._out[int(t.value)] = (oi, od)
+        return int(t.value)
+
+    def poll(self, max_items: int = 4096, wait_ms: int = 0) -> list[dict]:
+        """Finished requests: dicts with ticket, status, k, arrival/admit/done ns, idx, dist."""
+        cnt = ctypes.c_int32()
+        m = min(int(max_items), len(self._buf))
+        N.check(N.lib.dtw_server_poll(self._h, self._buf, m, ctypes.byref(cnt), int(wait_ms)))
+        out = []
+        for i in range(cnt.value):
+            c = self._buf[i]
+            oi, od = self._out.pop(int(c.ticket))
+            out.append({"ticket": int(c.ticket), "status": int(c.status), "k": int(c.k),
+                        "arrival_ns": int(c.arrival_ns), "admit_ns": int(c.admit_ns), "done_ns": int(c.done_ns),
+                        "idx": oi, "dist": od})
+        return out
+
+    def info(self) -> dict:
+        st = N.ServerStats()
+        N.check(N.lib.dtw_server_info(self._h, ctypes.byref(st)))
+        return st.as_dict()
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            N.check(N.lib.dtw_server_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -15,7 +15,7 @@ HEADER = os.path.join(ROOT, "include", "dtwknn.h")
 def _declared_functions():
     text = open(HEADER).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"^\s*(?:dtw_status|const char\s*\*)\s*(\w+)\s*\(", text, flags=re.M)))
+    return sorted(set(re.findall(r"^\s*(?:dtw_status|const char\s*\*|int64_t)\s*(\w+)\s*\(", text, flags=re.M)))
 
 
 @pytest.fixture(scope="module")
@@ -42,7 +42,7 @@ def test_library_exports_every_declared_symbol(native):
 
 
 def test_binding_covers_every_declared_symbol(native):
-    bound = set(native.SIGNATURES) | {"dtw_last_error", "dtw_version"}
+    bound = set(native.SIGNATURES) | {"dtw_last_error", "dtw_version", "dtw_monotonic_ns"}
     assert set(_declared_functions()) <= bound
 
 
@@ -119,3 +119,17 @@ def test_index_rejects_bad_arguments_on_host(native):
     assert st == 1 and "null" in text
     st, text = _status(native, lambda: native.lib.dtw_index_destroy(None))
     assert st == 0
+
+
+def test_server_rejects_bad_arguments_on_host(native):
+    h = ctypes.c_void_p()
+    st, text = _status(native, lambda: native.lib.dtw_server_create(None, None, ctypes.byref(h)))
+    assert st == 1 and "null" in text
+    st, text = _status(native, lambda: native.lib.dtw_server_submit(None, None, 8, 1, 1, None, None, 0, None))
+    assert st == 1 and "null" in text
+    cnt = ctypes.c_int32()
+    st, text = _status(native, lambda: native.lib.dtw_server_poll(None, None, 0, ctypes.byref(cnt), 0))
+    assert st == 1
+    assert native.lib.dtw_server_destroy(None) == 0
+    t0 = native.lib.dtw_monotonic_ns()
+    assert native.lib.dtw_monotonic_ns() >= t0 > 0
