@@ -443,14 +443,51 @@ __device__ __forceinline__ float lbi_pass3(const float2 *sufb, const float2 *pre
     return acc2;
 }
 
-// Returns LB_Improved^p, or LB_Keogh^p alone when !do_lbi or when LB_Keogh^p
-// already exceeds keogh_thr (the second pass is then skipped); *lbk_out
-// receives LB_Keogh^p.
+// Widened-window test (MT > 0, pa0 = PA0): the window of position t,
+// [i - w, i + w], widened outward to whole chunks, is chunks
+// lane + D0 + fa .. lane + E0 + fb; cw[fa][fb] holds the (max, min) of the
+// projection over those chunks.  The envelope over a window that contains
+// the true one bounds U(H) from above and L(H) from below, so the second sum
+// taken with it is at most LB_Keogh(y, H)^p, and LB_Keogh^p plus it is a
+// lower bound of LB_Improved^p (Sec. 8): a cheap first test of the second pass.
+template <int P, int MT, int PA0>
+__device__ __forceinline__ float lbi_coarse(const float2 (&cw)[2][2], const LbiQuery<MT> &Qv, int cnt_in) {
+    constexpr int PB0 = (MT - PA0) & (MT - 1);
+    float acc = 0.0f;
+#pragma unroll
+    for (int t = 0; t < MT; ++t) {
+        const bool fa = PA0 + t >= MT, fb = PB0 + t >= MT;
+        const float2 e = cw[fa ? 1 : 0][fb ? 1 : 0];
+        if (t < cnt_in) acc = acc_dist<P>(acc, Qv.yr[t], e.y, e.x);
+    }
+    return acc;
+}
+
+// (max, min) over the chunks lo .. hi (clamped to the 32 chunks; chunks past
+// the series hold neutral totals) from the table T_j[c] = chunks c .. c+2^j-1.
+__device__ __forceinline__ float2 lbi_chunk_range(const float2 *T, int lo, int hi) {
+    lo = max(lo, 0);
+    hi = min(hi, 31);
+    float2 r = make_float2(-kInf, kInf);
+    if (lo <= hi) {
+        const int k = 31 - __clz(hi - lo + 1);
+        const float2 t1 = T[k * 32 + lo], t2 = T[k * 32 + hi - (1 << k) + 1];
+        r = make_float2(fmaxf(t1.x, t2.x), fminf(t1.y, t2.y));
+    }
+    return r;
+}
+
+// Returns LB_Improved^p, or a smaller bound when the pair fails a test:
+// LB_Keogh^p alone when !do_lbi or when it already exceeds keogh_thr, and
+// LB_Keogh^p plus the widened-window second sum when that exceeds
+// keogh_thr.  *lbk_out receives LB_Keogh^p.  lbk_known >= 0: LB_Keogh^p of
+// the pair, already computed and tested by the caller (the first sum is then
+// not formed again).
 template <int P, int MT>
 __device__ __forceinline__ float warp_lb_improved(const float *__restrict__ x, const LbiQuery<MT> &Qv, int n, int w,
                                                   float *scratch, bool vec, const LbiChunk<MT> *pre = nullptr,
                                                   bool do_lbi = true, float keogh_thr = kInf,
-                                                  float *lbk_out = nullptr) {
+                                                  float *lbk_out = nullptr, float lbk_known = -1.0f) {
     const int lane = threadIdx.x & 31;
     const LbiGeom g = lbi_geom(n);
     const int m = MT > 0 ? MT : g.m;
@@ -464,11 +501,13 @@ __device__ __forceinline__ float warp_lb_improved(const float *__restrict__ x, c
     const float NEG = -kInf, POS = kInf;
     const int i0 = lane * m;
     const int cnt_in = max(0, min(m, n - i0));
+    const int pa0 = (-w) & (m - 1), D0 = (-w) >> lg;
+    const int E0 = w >> lg;
     float acc1 = 0.0f;
-    float pmax = NEG, pmin = POS;
-    float tmax, tmin;
+    float cmax = NEG, cmin = POS;  // chunk totals of the projection
+    float h[MT > 0 ? MT : 1];
+    // first pass: projection H (Eq. 1) and LB_Keogh^p
     if constexpr (MT > 0) {
-        float h[MT];
         LbiChunk<MT> own;
         if (pre == nullptr) lbi_load_chunk<MT>(own, x, n, vec);
         const float *xv = pre ? pre->v : own.v;
@@ -479,21 +518,93 @@ __device__ __forceinline__ float warp_lb_improved(const float *__restrict__ x, c
             if (t < cnt_in) {
                 acc1 = (P == 1) ? acc1 + d : fmaf(d, d, acc1);
                 h[t] = hv;
+                cmax = fmaxf(cmax, hv);
+                cmin = fminf(cmin, hv);
             } else {
                 h[t] = NEG;
             }
         }
-        {
-            const float lbk = warp_sum(acc1);
-            if (lbk_out) *lbk_out = lbk;
-            if (!do_lbi || lbk > keogh_thr) return lbk;
-            acc1 = (lane == 0) ? lbk : 0.0f;
+    } else {
+        for (int t = 0; t < m; ++t) {
+            float hv = NEG;
+            if (t < cnt_in) {
+                const float xv = __ldg(x + i0 + t);
+                hv = fminf(fmaxf(xv, Qv.L(t, lane, m)), Qv.U(t, lane, m));
+                const float d = fabsf(xv - hv);
+                acc1 = (P == 1) ? acc1 + d : fmaf(d, d, acc1);
+                cmax = fmaxf(cmax, hv);
+                cmin = fminf(cmin, hv);
+            }
+            Hs[t * 32 + lane] = hv;
         }
-        if (2 * w < MT) {
+    }
+    if (lbk_known >= 0.0f) {
+        acc1 = (lane == 0) ? lbk_known : 0.0f;
+    } else {
+        const float lbk = warp_sum(acc1);
+        if (lbk_out) *lbk_out = lbk;
+        if (!do_lbi || lbk > keogh_thr) return lbk;
+        acc1 = (lane == 0) ? lbk : 0.0f;
+    }
+    // table over chunk totals: T_j[c] = max/min of chunks c .. c + 2^j - 1
+    {
+        float tmax = cmax, tmin = cmin;
+        T[lane] = make_float2(tmax, tmin);
+#pragma unroll
+        for (int j = 1; j < 6; ++j) {
+            const int hh = 1 << (j - 1);
+            const float omax = __shfl_down_sync(0xffffffffu, tmax, hh);
+            const float omin = __shfl_down_sync(0xffffffffu, tmin, hh);
+            if (lane + hh < 32) {
+                tmax = fmaxf(tmax, omax);
+                tmin = fminf(tmin, omin);
+            }
+            T[j * 32 + lane] = make_float2(tmax, tmin);
+        }
+    }
+    __syncwarp();
+    const bool windows_span_chunks = 2 * w >= m;
+    if (windows_span_chunks && keogh_thr < kInf) {
+        // widened-window test
+        float2 cw[2][2];
+#pragma unroll
+        for (int fa = 0; fa < 2; ++fa)
+#pragma unroll
+            for (int fb = 0; fb < 2; ++fb) cw[fa][fb] = lbi_chunk_range(T, lane + D0 + fa, lane + E0 + fb);
+        float acc2 = 0.0f;
+        if constexpr (MT > 0) {
+            switch (pa0) {
+#define LBI_COARSE_CASE(A)                                                          \
+    case A:                                                                         \
+        if constexpr (A < MT) acc2 = lbi_coarse<P, MT, A>(cw, Qv, cnt_in);          \
+        break;
+                LBI_COARSE_CASE(0) LBI_COARSE_CASE(1) LBI_COARSE_CASE(2) LBI_COARSE_CASE(3)
+                LBI_COARSE_CASE(4) LBI_COARSE_CASE(5) LBI_COARSE_CASE(6) LBI_COARSE_CASE(7)
+#undef LBI_COARSE_CASE
+                default: break;
+            }
+        } else {
+            const int pb0 = w & (m - 1);
+            for (int t = 0; t < cnt_in; ++t) {
+                const bool fa = pa0 + t >= m, fb = pb0 + t >= m;
+                const float2 e = fa ? (fb ? cw[1][1] : cw[1][0]) : (fb ? cw[0][1] : cw[0][0]);
+                acc2 = acc_dist<P>(acc2, Qv.Y(t, lane, m), e.y, e.x);
+            }
+        }
+        const float wide = warp_sum(acc1 + acc2);
+        if (wide > keogh_thr) {
+            __syncwarp();  // scratch is reused by the next pair
+            return wide;
+        }
+    }
+    // second pass, exact windows: prefix and suffix (max, min) of each chunk
+    if constexpr (MT > 0) {
+        if (!windows_span_chunks) {
             // windows can lie inside a chunk: keep h for the direct scan
 #pragma unroll
             for (int t = 0; t < MT; ++t) Hs[t * 32 + lane] = h[t];
         }
+        float pmax = NEG, pmin = POS;
 #pragma unroll
         for (int t = 0; t < MT; ++t) {
             pmax = fmaxf(pmax, h[t]);
@@ -508,24 +619,14 @@ __device__ __forceinline__ float warp_lb_improved(const float *__restrict__ x, c
             Suf[t * W + PLc + lane] = make_float2(smax, smin);
         }
     } else {
+        float pmax = NEG, pmin = POS;
         for (int t = 0; t < m; ++t) {
-            float hv = NEG;
             if (t < cnt_in) {
-                const float xv = __ldg(x + i0 + t);
-                hv = fminf(fmaxf(xv, Qv.L(t, lane, m)), Qv.U(t, lane, m));
-                const float d = fabsf(xv - hv);
-                acc1 = (P == 1) ? acc1 + d : fmaf(d, d, acc1);
+                const float hv = Hs[t * 32 + lane];
                 pmax = fmaxf(pmax, hv);
                 pmin = fminf(pmin, hv);
             }
-            Hs[t * 32 + lane] = hv;
             Pre[t * W + lane] = make_float2(pmax, pmin);
-        }
-        {
-            const float lbk = warp_sum(acc1);
-            if (lbk_out) *lbk_out = lbk;
-            if (!do_lbi || lbk > keogh_thr) return lbk;
-            acc1 = (lane == 0) ? lbk : 0.0f;
         }
         float smax = NEG, smin = POS;
         for (int t = m - 1; t >= 0; --t) {
@@ -537,24 +638,9 @@ __device__ __forceinline__ float warp_lb_improved(const float *__restrict__ x, c
             Suf[t * W + lane] = make_float2(smax, smin);
         }
     }
-    // table over chunk totals: T_j[c] = max/min of chunks c .. c + 2^j - 1
-    tmax = pmax;
-    tmin = pmin;
-    T[lane] = make_float2(tmax, tmin);
-#pragma unroll
-    for (int j = 1; j < 6; ++j) {
-        const int hh = 1 << (j - 1);
-        const float omax = __shfl_down_sync(0xffffffffu, tmax, hh);
-        const float omin = __shfl_down_sync(0xffffffffu, tmin, hh);
-        if (lane + hh < 32) {
-            tmax = fmaxf(tmax, omax);
-            tmin = fminf(tmin, omin);
-        }
-        T[j * 32 + lane] = make_float2(tmax, tmin);
-    }
     __syncwarp();
     float acc2 = 0.0f;
-    if (MT > 0 && 2 * w >= m) {
+    if (MT > 0 && windows_span_chunks) {
         // Window of i = lane*M + t: [a, b] = [i - w, i + w]; chunk(a) = lane + da_t
         // at position pa_t and chunk(b) = lane + db_t at position pb_t, where
         // da_t = D0 + fa_t and db_t = E0 + fb_t with 0/1 flags that depend on t
@@ -562,21 +648,13 @@ __device__ __forceinline__ float warp_lb_improved(const float *__restrict__ x, c
         // prefix/suffix lookups need no clamping.  The whole chunks strictly
         // between take one of four ranges per lane; their max/min come from the
         // chunk table once per pair and are selected per position.
-        const int pa0 = (-w) & (m - 1), D0 = (-w) >> lg;
-        const int pb0 = w & (m - 1), E0 = w >> lg;
         float2 mid[2][2];
 #pragma unroll
         for (int fa = 0; fa < 2; ++fa)
 #pragma unroll
             for (int fb = 0; fb < 2; ++fb) {
-                const int lo = max(lane + D0 + fa + 1, 0), hi = min(lane + E0 + fb - 1, 31);
-                float2 r = make_float2(NEG, POS);
-                if (lo <= hi) {
-                    const int k = 31 - __clz(hi - lo + 1);
-                    const float2 t1 = T[k * 32 + lo], t2 = T[k * 32 + hi - (1 << k) + 1];
-                    r = make_float2(fmaxf(t1.x, t2.x), fminf(t1.y, t2.y));
-                }
-                mid[fa][fb] = r;
+                const int lo = lane + D0 + fa + 1, hi = lane + E0 + fb - 1;
+                mid[fa][fb] = (lo <= hi) ? lbi_chunk_range(T, lo, hi) : make_float2(NEG, POS);
             }
         if constexpr (MT > 0) {
             const float2 *sufb = Suf + PLc + D0 + lane;
@@ -755,22 +833,26 @@ __global__ void __launch_bounds__(256, 3) k_lbi_filter(CascadeBufs b, bool vec) 
     }
     __syncwarp();
     const unsigned long long pk = (unsigned long long)cnt1;
-    // phase 2: LB_Improved of each survivor, the next candidate's chunk
-    // prefetched while the current one is processed; survivors are kept in
-    // place (write index <= read index)
+    const bool lbk_done = !b.summary;  // the survivors carry LB_Keogh^p
+    unsigned long long kp = 0;         // LB_Keogh survivors (summary mode)
+    // phase 2: LB_Improved of each survivor (warp per pair), the next
+    // candidate's chunk prefetched while the current one is processed;
+    // survivors are kept in place (write index <= read index).  With the
+    // piecewise-sum pre-filter the matrix held that bound, and LB_Keogh is
+    // formed here first; otherwise the matrix value is LB_Keogh^p itself.
     int cnt = 0;
-    unsigned long long kp = 0;  // LB_Keogh survivors (summary mode)
-    if (b.lbi_inline || b.summary) {
+    if (b.lbi_inline || !lbk_done) {
         LbiChunk<MT> cur, nxt;
         if (cnt1 > 0) lbi_load_chunk<MT>(nxt, b.db + (int64_t)surv_c[0] * n, n, vec);
         for (int e = 0; e < cnt1; ++e) {
             const int cc = surv_c[e];
+            const float known = lbk_done ? surv_v[e] : -1.0f;
             cur = nxt;
             if (e + 1 < cnt1) lbi_load_chunk<MT>(nxt, b.db + (int64_t)surv_c[e + 1] * n, n, vec);
-            float lbk = 0.0f;
+            float lbk = known;
             const float v = warp_lb_improved<P, MT>(b.db + (int64_t)cc * n, Qv, n, w, scratch, vec,
-                                                    MT > 0 ? &cur : nullptr, b.lbi_inline != 0, thr, &lbk);
-            kp += (lbk <= thr) ? 1 : 0;
+                                                    MT > 0 ? &cur : nullptr, b.lbi_inline != 0, thr, &lbk, known);
+            if (!lbk_done) kp += (lbk <= thr) ? 1 : 0;
             if (v <= thr) {
                 if (lane == 0) {
                     surv_c[cnt] = cc;
