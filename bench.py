@@ -11,6 +11,8 @@ LB_Improved of the LB_Keogh survivors, DTW of the LB_Improved survivors and
 the ordered top-k.  The same step under DTW_2 is reported beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py --workload batched   # mixed-length batches through the index
+  python bench.py --workload serve     # Poisson arrivals through the request server
 
 Under torchrun each rank holds the whole database and runs its own batch of
 queries (weak scaling; the only collectives are the timing barrier and the
@@ -40,6 +42,11 @@ if ROOT not in sys.path:
 import synth  # noqa: E402
 
 METRIC = "exact 1-NN DTW queries/s (LB_Improved cascade)"
+# DRAM bytes per launch of the filter kernel at the default workload, from one
+# ncu capture (dram__bytes_read.sum + dram__bytes_write.sum); valid for that
+# workload and the kernel as captured (profiles/k_lbi_filter_traffic_*.md)
+FILTER_TRAFFIC = {"workload": (100_000, 256, 25, 1000), "bytes": 524.79e6,
+                  "source": "profiles/k_lbi_filter_traffic_rw100k_n256_w25_q1000.md"}
 L2_BYTES = 129 * 2**20
 
 
@@ -223,8 +230,12 @@ def roofline(prof, a, steps, peaks, stats):
         lbk_surv = pd_surv - stats.get("pruned_keogh", 0)
         ops = scanned * 1.0 + pd_surv * a.n * 4.0 + lbk_surv * a.n * 7.0
         achieved = ops / 1e12 / (ms / 1e3) if scanned > 0 else None
+        traffic = FILTER_TRAFFIC["bytes"] if (a.N, a.n, a.w, a.Q) == FILTER_TRAFFIC["workload"] else None
         return {"kernel": "k_lbi_filter", "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Top/s",
-                "frac": (achieved / alu_peak) if achieved else None, "traffic": None, "ms_per_launch": ms,
+                "frac": (achieved / alu_peak) if achieved else None, "traffic": traffic,
+                "traffic_note": ("DRAM bytes per launch, %s; algorithmic bytes 502.4 MB (bound matrix 400 MB + "
+                                 "database 102.4 MB)" % FILTER_TRAFFIC["source"]) if traffic else None,
+                "hbm_gbs": (traffic / 1e9 / (ms / 1e3)) if traffic else None, "ms_per_launch": ms,
                 "lb_keogh_pairs": pd_surv, "lb_improved_pairs": lbk_surv, "stage_share": share,
                 "peak_note": "%d SMs x 128 fp32 lanes x %.0f MHz (max SM clock)" % (sms, clock / 1e6)}
     return {"kernel": dom, "bound": "alu", "achieved": None, "peak": alu_peak, "unit": "Top/s", "frac": None,
