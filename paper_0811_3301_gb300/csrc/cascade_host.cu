@@ -137,7 +137,13 @@ CascadePlan make_plan(int64_t N, int64_t Qmax, int n, int w, int p, int k, const
     pl.seg_len = seg_len;
     pl.dtw_path = o.dtw_path;
     pl.filter_warps = lbi_filter_warps(n, pl.we, std::max(pl.S, 1), pl.seg_len);
-    pl.nseg = N > 0 ? (int)((N + pl.seg_len - 1) / pl.seg_len) * pl.filter_warps : 1;
+    const int64_t nsegs = N > 0 ? (N + pl.seg_len - 1) / pl.seg_len : 1;
+    pl.nseg = (int)nsegs * pl.filter_warps;
+    // filter CTAs: about eight waves of four CTAs per SM; each takes enough
+    // consecutive segments of its query to amortise the query staging
+    const int64_t target = (int64_t)device_sm_count() * 32;
+    int64_t spc = (Qc * nsegs) / target;
+    pl.seg_per_cta = (int)std::max<int64_t>(1, std::min<int64_t>(spc, nsegs));
     return pl;
 }
 
@@ -235,6 +241,7 @@ cudaError_t cascade_run(const CascadePlan &pl, const CascadeWs &l, const float *
     b.pair_cap = (int64_t)qn * Nc;
     b.pair_count = pair_count;
     b.seg_len = pl.seg_len;
+    b.seg_per_cta = pl.seg_per_cta;
     b.nseg = N > 0 ? pl.nseg : 0;
     b.seg_start = l.seg_start;
     b.seg_count = l.seg_count;

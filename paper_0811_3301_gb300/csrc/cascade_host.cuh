@@ -37,6 +37,7 @@ struct CascadePlan {
     int seg_len;     // candidates per filter segment
     int filter_warps;
     int nseg;        // sub-segments per query
+    int seg_per_cta; // filter segments per CTA
     int dtw_path;    // 0 auto, 1 thread per pair, 2 warp per pair (main DTW stage)
 };
 

@@ -163,6 +163,7 @@ struct CascadeBufs {
     int64_t pair_cap;
     unsigned long long *pair_count;
     int seg_len, nseg;    // nseg: sub-segments per query (segments x filter warps)
+    int seg_per_cta;      // consecutive segments one filter CTA handles
     int32_t *seg_start;   // [Q][nseg]
     int32_t *seg_count;   // [Q][nseg]
     // work cursors and counters

@@ -320,10 +320,12 @@ __host__ __device__ inline LbiCols lbi_cols(int n, int w) {
     return c;
 }
 // per-warp scratch in floats: prefix and suffix (max, min) pairs [M][width]
-// each, the chunk table (max, min) [6][32] and the chunk of h [M][32]
+// each, the chunk table (max, min) [6][32] and, where a window can lie inside
+// one chunk (runtime M, or 2w < M), the chunk of h [M][32]
 __host__ __device__ inline int lbi_scratch_floats(int n, int w) {
     const int m = lbi_geom(n).m;
-    return 2 * 2 * m * lbi_cols(n, w).width + 2 * 6 * 32 + 32 * m;
+    const bool keep_h = m > kLbiRegM || 2 * w < m;
+    return 2 * 2 * m * lbi_cols(n, w).width + 2 * 6 * 32 + (keep_h ? 32 * m : 0);
 }
 // per-query staging: y in [t][32] layout, and for runtime M also U and L
 __host__ __device__ inline int lbi_query_floats(int n) {
@@ -782,7 +784,7 @@ __global__ void __launch_bounds__(256, 3) k_lbi_filter(CascadeBufs b, bool vec) 
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // CTAs in flight share a candidate segment (consecutive CTAs are queries),
     // so the segment's rows stay in L2 for all the queries that test them
-    const int q = blockIdx.x, sg = blockIdx.y;
+    const int q = blockIdx.x;
     const int n = b.n, w = b.w;
     const int per_warp_cap = b.seg_len / nw + 32;  // candidates one warp scans, rounded up
     float *sq = reinterpret_cast<float *>(smraw);
@@ -799,14 +801,20 @@ __global__ void __launch_bounds__(256, 3) k_lbi_filter(CascadeBufs b, bool vec) 
     }
     __syncthreads();
 
-    // From here on each warp works alone: it scans its share of the segment,
-    // keeps its survivors in its own shared buffer and writes them as one
-    // contiguous block of the pair list (sub-segment (q, sg, wid)).
+    // From here on each warp works alone: for each of the CTA's segments it
+    // scans its share of the segment, keeps its survivors in its own shared
+    // buffer and writes them as one contiguous block of the pair list
+    // (sub-segment (q, sg, wid)).  The query staging above is shared by the
+    // CTA's seg_per_cta consecutive segments.
     const float bq = (b.mode == DTW_MODE_NOPRUNE) ? kInf : load_threshold(b.bsf + q);
     const float thr = bq * (1.0f + b.slack);
     // the matrix holds LB_Keogh^p, or the piecewise-sum bound in the units of
     // sum_j D_j^p (for p = 2 the bound is that sum over max_j |C_j|)
     const float thr_m = b.summary ? thr * b.summary_scale : thr;
+    const int nsegs = b.nseg / nw;
+    for (int sj = 0; sj < b.seg_per_cta; ++sj) {
+    const int sg = blockIdx.y * b.seg_per_cta + sj;
+    if (sg >= nsegs) break;
     const int c0 = sg * b.seg_len;
     const int c1 = min(b.N, c0 + b.seg_len);
     const float *lbrow = b.lb + (int64_t)q * b.N;
@@ -868,7 +876,7 @@ __global__ void __launch_bounds__(256, 3) k_lbi_filter(CascadeBufs b, bool vec) 
     unsigned long long base = 0;
     if (lane == 0 && cnt > 0) base = atomicAdd(b.pair_count, (unsigned long long)cnt);
     base = __shfl_sync(0xffffffffu, base, 0);
-    const int64_t sub = ((int64_t)q * gridDim.y + sg) * nw + wid;
+    const int64_t sub = ((int64_t)q * nsegs + sg) * nw + wid;
     if (lane == 0) {
         b.seg_start[sub] = (int32_t)base;
         b.seg_count[sub] = cnt;
@@ -890,6 +898,8 @@ __global__ void __launch_bounds__(256, 3) k_lbi_filter(CascadeBufs b, bool vec) 
         b.pairs_u[o] = Pair{q, surv_c[t]};
         b.lbi_u[o] = surv_v[t];
     }
+    __syncwarp();  // the survivor buffer is refilled by the next segment
+    }  // segments of this CTA
 }
 
 int lbi_filter_warps(int n, int w, int S, int seg_len) {
@@ -908,8 +918,12 @@ static void lbi_filter_go(const CascadeBufs &b, bool vec, cudaStream_t s) {
     const int64_t per_warp = (int64_t)lbi_scratch_floats(b.n, b.w) * sizeof(float);
     const int64_t per_query = (int64_t)lbi_query_floats(b.n) * sizeof(float);
     const size_t smem = (size_t)per_query + (size_t)b.S * 4 + 64 + (size_t)nw * (per_warp + 8 * (b.seg_len / nw + 32));
-    const dim3 grid(b.Q, b.nseg / nw);
+    const int nsegs = b.nseg / nw;
+    const dim3 grid(b.Q, (nsegs + b.seg_per_cta - 1) / b.seg_per_cta);
     cudaFuncSetAttribute(k_lbi_filter<P, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // the CTAs per SM are limited by shared memory: prefer it over L1
+    cudaFuncSetAttribute(k_lbi_filter<P, MT>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         (int)cudaSharedmemCarveoutMaxShared);
     k_lbi_filter<P, MT><<<grid, nw * 32, smem, s>>>(b, vec);
 }
 
