@@ -68,7 +68,7 @@ def parse():
     ap.add_argument("--dtw-path", type=int, default=0, help="DTW kernel: 0 auto, 1 thread per pair, 2 warp per pair")
     ap.add_argument("--no-p2", action="store_true", help="skip the DTW_2 side measurement")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU baseline sample")
-    ap.add_argument("--workload", choices=["retrieval", "batched", "serve"], default="retrieval",
+    ap.add_argument("--workload", choices=["retrieval", "batched", "serve", "triangle"], default="retrieval",
                     help="retrieval: one length, one knn_search per step (default); batched: mixed-length "
                          "batches against length buckets through the index")
     ap.add_argument("--bucket-N", type=int, default=20_000, help="batched: series per length bucket")
@@ -609,6 +609,61 @@ def run_serve(a):
     }
 
 
+def run_triangle(a):
+    """App. B: DTW_p(x,z) / (DTW_p(x,y) + DTW_p(y,z)) over 100,000 triples of
+    100-sample series (white noise, random walks, shape-like series standing
+    in for Cylinder-Bell-Funnel), no time constraint, p = 1 and 2: the share of
+    triples that violate the triangle inequality, and the DTW rate."""
+    import torch
+
+    from paper_0811_3301_gb300 import build
+
+    build.build()
+    from paper_0811_3301_gb300 import api
+
+    N, n = 100_000, 100
+    w = n - 1
+    gens = {"white_noise": synth.white_noise, "random_walk": synth.random_walks, "shapes": synth.shapes}
+    flush = torch.empty(256 * 2**20 // 4, dtype=torch.float32, device="cuda")
+    cells_per_pair = n * (2 * w + 1) - w * (w + 1)
+    res = {}
+    total_ms = 0.0
+    total_pairs = 0
+    for kind, g in gens.items():
+        x, y, z = (torch.from_numpy(g(N, n, seed=a.seed + 90 + s)).cuda() for s in range(3))
+        for p in (1, 2):
+            for _ in range(a.warmup):
+                api.dtw_triangle(x, y, z, w, p)
+            torch.cuda.synchronize()
+            ms = 0.0
+            for i in range(a.steps):
+                flush.fill_(float(i))
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                r = api.dtw_triangle(x, y, z, w, p)
+                e1.record()
+                torch.cuda.synchronize()
+                ms += e0.elapsed_time(e1)
+            rc = r.cpu().numpy()
+            hist, edges = np.histogram(rc, bins=30, range=(0.0, 1.5))
+            res["%s_p%d" % (kind, p)] = {"violations": float((rc > 1.0).mean()), "max_ratio": float(rc.max()),
+                                         "ms_per_call": ms / a.steps,
+                                         "histogram": {"edges": edges.tolist(), "counts": hist.tolist()}}
+            total_ms += ms
+            total_pairs += 3 * N * a.steps
+    return {
+        "metric": "DTW pairs/s, App. B triangle-inequality experiment (dense batched DTW, no band)",
+        "value": total_pairs / (total_ms / 1e3), "unit": "DTW pairs/s", "n_gpus": 1, "steps": a.steps,
+        "warmup": a.warmup, "cells_per_s": total_pairs * cells_per_pair / (total_ms / 1e3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded white noise, random walks, shape-like series)",
+        "config": {"workload": "App. B: %d triples of n = %d, w = %d (no constraint), p in {1, 2}" % (N, n, w),
+                   "paper": "no violation for white noise and Cylinder-Bell-Funnel; 20 %% (DTW_1) and 15 %% "
+                            "(DTW_2) of random-walk triples violate the triangle inequality"},
+        "results": res,
+    }
+
+
 def run_reference(a):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -648,6 +703,8 @@ def main():
         out = run_batched(a)
     elif a.workload == "serve":
         out = run_serve(a)
+    elif a.workload == "triangle":
+        out = run_triangle(a)
     else:
         out = run_ours(a)
     if out is not None:

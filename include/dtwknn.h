@@ -156,6 +156,17 @@ dtw_status knn_search(const float *db, int64_t N, const float *queries, int64_t 
                       int32_t n, int32_t w, int32_t p, int32_t k, int64_t *out_idx,
                       float *out_dist, dtw_stats *stats, void *stream);
 
+/*
+ * Triangle-inequality experiment of App. B: for N triples (x_i, y_i, z_i)
+ * (x, y, z each [N][n]), ratio[i] = DTW_p(x_i, z_i) / (DTW_p(x_i, y_i) +
+ * DTW_p(y_i, z_i)) with band w (the paper uses no constraint: w >= n - 1).
+ * A ratio above 1 is a violation of the triangle inequality; 0 / 0 gives 0
+ * and c / 0 (c > 0) gives +INF.  dist3 (nullable, [3][N]) receives the three
+ * distances DTW_p(x,y), DTW_p(y,z), DTW_p(x,z).  Uses the workspace.
+ */
+dtw_status dtw_triangle(const float *x, const float *y, const float *z, int64_t N, int32_t n,
+                        int32_t w, int32_t p, float *ratio, float *dist3, void *stream);
+
 /* knn_search with a cascade mode, slack and seed count (opt may be NULL). */
 dtw_status knn_search_ex(const float *db, int64_t N, const float *queries, int64_t Q,
                          int32_t n, int32_t w, int32_t p, int32_t k,

@@ -121,6 +121,7 @@ SIGNATURES = {
     "lb_improved": [_vp, _i64, _vp, _vp, _vp, _i32, _i32, _i32, _vp, _vp],
     "dtw_band": [_vp, _vp, _i64, _i32, _i32, _i32, _i32, _f32, _vp, _vp],
     "dtw_band_noalloc": [_vp, _vp, _i64, _i32, _i32, _i32, _i32, _f32, _vp, _vp],
+    "dtw_triangle": [_vp, _vp, _vp, _i64, _i32, _i32, _i32, _vp, _vp, _vp],
     "knn_search": [_vp, _i64, _vp, _i64, _i32, _i32, _i32, _i32, _vp, _vp, ctypes.POINTER(Stats), _vp],
     "dtw_profile_enable": [_i32],
     "dtw_profile_read": [ctypes.c_void_p, _i32],

@@ -16,7 +16,8 @@ import torch
 
 from . import _native as N
 
-__all__ = ["dtw_envelope", "lb_keogh", "lb_piecewise", "lb_improved", "dtw_band", "knn_search", "DtwIndex",
+__all__ = ["dtw_envelope", "lb_keogh", "lb_piecewise", "lb_improved", "dtw_band", "dtw_triangle", "knn_search",
+           "DtwIndex",
            "DtwServer", "DtwError", "monotonic_ns", "version"]
 
 DtwError = N.DtwError
@@ -122,6 +123,22 @@ def dtw_band(x: torch.Tensor, y: torch.Tensor, w: int, p: int, threshold: float 
     N.check(N.lib.dtw_band(_ptr(x), _ptr(y), x.shape[0], stride, n, int(w), int(p), float(threshold),
                            _ptr(out), _stream()))
     return out
+
+
+def dtw_triangle(x: torch.Tensor, y: torch.Tensor, z: torch.Tensor, w: int, p: int, with_distances: bool = False):
+    """Triangle-inequality ratios DTW_p(x,z) / (DTW_p(x,y) + DTW_p(y,z)) of the
+    rows of x, y, z ([N, n] each), App. B.  With with_distances also the
+    [3, N] distances (x,y), (y,z), (x,z)."""
+    x = _cuda_f32(x, "x")
+    y = _cuda_f32(y, "y")
+    z = _cuda_f32(z, "z")
+    if not (x.shape == y.shape == z.shape) or x.dim() != 2:
+        raise ValueError("x, y and z must be [N, n] of one shape")
+    N_, n = x.shape
+    ratio = torch.empty(N_, device=x.device, dtype=torch.float32)
+    d3 = torch.empty((3, N_), device=x.device, dtype=torch.float32) if with_distances else None
+    N.check(N.lib.dtw_triangle(_ptr(x), _ptr(y), _ptr(z), N_, n, int(w), int(p), _ptr(ratio), _ptr(d3), _stream()))
+    return (ratio, d3) if with_distances else ratio
 
 
 def knn_search(db: torch.Tensor, queries: torch.Tensor, w: int, p: int, k: int = 1, *, mode: str = "improved",

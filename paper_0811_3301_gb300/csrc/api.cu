@@ -237,6 +237,67 @@ dtw_status dtw_band(const float *x, const float *y, int64_t N, int32_t y_stride,
     return DTW_OK;
 }
 
+dtw_status dtw_triangle(const float *x, const float *y, const float *z, int64_t N, int32_t n, int32_t w, int32_t p,
+                        float *ratio, float *dist3, void *stream) {
+    g_err[0] = 0;
+    dtw_status st = check_common(n, w, p);
+    if (st != DTW_OK) return st;
+    if ((st = check_band(n, w)) != DTW_OK) return st;
+    if (N < 0 || N > INT32_MAX) return fail(DTW_ERR_INVALID_ARG, "N=%lld out of range", (long long)N);
+    if (N == 0) return DTW_OK;
+    if (!x || !y || !z || !ratio) return fail(DTW_ERR_INVALID_ARG, "null pointer");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int we = w < n - 1 ? w : n - 1;
+    const DtwGeom g = dtw_geom(n, we);
+    auto layout = [&](Carve &cv, QueryCopies &qc, float *&d3, unsigned long long *&cur) {
+        qc.data = cv.take<float>((size_t)N * 4 * g.ylen);
+        qc.padl = g.padl;
+        qc.ylen = g.ylen;
+        d3 = dist3 ? nullptr : cv.take<float>((size_t)3 * N);
+        cur = cv.take<unsigned long long>(3);
+    };
+    QueryCopies qc;
+    float *d3 = nullptr;
+    unsigned long long *cur = nullptr;
+    Carve sizing;
+    layout(sizing, qc, d3, cur);
+    void *ws = nullptr;
+    if ((st = workspace_get(sizing.off, &ws)) != DTW_OK) return st;
+    Carve cv;
+    cv.base = (char *)ws;
+    layout(cv, qc, d3, cur);
+    float *d = dist3 ? dist3 : d3;  // [3][N]: DTW_p(x,y), DTW_p(y,z), DTW_p(x,z)
+    CUDA_TRY(cudaMemsetAsync(cur, 0, 3 * sizeof(unsigned long long), s));
+    DtwJob j{};
+    j.n = n;
+    j.w = we;
+    j.p = p;
+    j.k = 1;
+    j.qc = qc;
+    j.npairs = N;
+    j.per_pair_y = 1;
+    j.fixed_thr = INFINITY;
+    j.root_out = 1;
+    // pairs (x_i, y_i)
+    CUDA_TRY(launch_query_copies(y, N, n, qc, s));
+    j.db = x;
+    j.res = d;
+    j.cursor = cur;
+    CUDA_TRY(launch_dtw(j, g, s));
+    // pairs (y_i, z_i) and (x_i, z_i) share the copies of z
+    CUDA_TRY(launch_query_copies(z, N, n, qc, s));
+    j.db = y;
+    j.res = d + N;
+    j.cursor = cur + 1;
+    CUDA_TRY(launch_dtw(j, g, s));
+    j.db = x;
+    j.res = d + 2 * N;
+    j.cursor = cur + 2;
+    CUDA_TRY(launch_dtw(j, g, s));
+    CUDA_TRY(launch_triangle_ratio(d, d + N, d + 2 * N, N, ratio, s));
+    return DTW_OK;
+}
+
 dtw_status knn_search_ex(const float *db, int64_t N, const float *queries, int64_t Q, int32_t n,
                          int32_t w, int32_t p, int32_t k, const dtw_options *opt, int64_t *out_idx,
                          float *out_dist, dtw_stats *stats, void *stream) {

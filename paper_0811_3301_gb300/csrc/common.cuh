@@ -223,4 +223,7 @@ enum {
 
 int device_sm_count();
 
+cudaError_t launch_triangle_ratio(const float *dxy, const float *dyz, const float *dxz, int64_t N, float *out,
+                                  cudaStream_t s);
+
 }  // namespace dtwk

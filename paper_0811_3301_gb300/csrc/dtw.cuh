@@ -57,19 +57,34 @@ inline DtwGeom dtw_geom(int n, int w) {
     return g;
 }
 
-// Warp path (dtw_lanes.cuh): slots per lane CL for the band 2w+1, from the
-// instantiated set, or 0 when the band needs more than 32 * 32 slots.
-inline int dtw_lanes_cl(int n, int w) {
+// Warp path (dtw_lanes.cuh): G lanes per pair and CL slots per lane for the
+// band 2w+1 (from the instantiated sets), or cl = 0 when the band needs more
+// than 32 x 32 slots.  Groups of 32 give each pair the shortest chain of
+// dependent steps (for launches of few pairs, where that latency sets the
+// time); groups of 16, two per warp, halve the per-pair cost of the steps'
+// bookkeeping (for launches of many pairs, where throughput does).
+struct LanesShape {
+    int g, cl;
+};
+inline LanesShape dtw_lanes_shape(int n, int w, bool many_pairs = false) {
     w = w < n - 1 ? w : n - 1;
-    const int need = (2 * w + 1 + 31) / 32;
-    const int set[] = {2, 3, 4, 5, 6, 7, 8, 10, 12, 13, 16, 20, 24, 32};
-    for (int c : set)
-        if (c >= need) return c;
-    return 0;
+    const int bw = 2 * w + 1;
+    if (many_pairs && bw <= 16 * 32) {
+        const int need = (bw + 15) / 16;
+        const int set16[] = {4, 7, 10, 13, 16, 20, 26, 32};
+        for (int c : set16)
+            if (c >= need) return LanesShape{16, c};
+    }
+    const int need = (bw + 31) / 32;
+    const int set32[] = {2, 3, 4, 5, 6, 7, 8, 10, 13, 16, 20, 24, 32};
+    for (int c : set32)
+        if (c >= need) return LanesShape{32, c};
+    return LanesShape{0, 0};
 }
+inline int dtw_lanes_cl(int n, int w) { return dtw_lanes_shape(n, w).cl; }
 
-cudaError_t launch_dtw_lanes_p1(const DtwJob &j, const DtwGeom &g, int cl, cudaStream_t s);
-cudaError_t launch_dtw_lanes_p2(const DtwJob &j, const DtwGeom &g, int cl, cudaStream_t s);
+cudaError_t launch_dtw_lanes_p1(const DtwJob &j, const DtwGeom &g, LanesShape ls, cudaStream_t s);
+cudaError_t launch_dtw_lanes_p2(const DtwJob &j, const DtwGeom &g, LanesShape ls, cudaStream_t s);
 
 cudaError_t launch_dtw_p1(const DtwJob &j, const DtwGeom &g, cudaStream_t s);
 cudaError_t launch_dtw_p2(const DtwJob &j, const DtwGeom &g, cudaStream_t s);

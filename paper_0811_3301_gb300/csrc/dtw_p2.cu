@@ -18,8 +18,12 @@ int blocks_for(K kernel, int64_t warps_needed) {
 
 cudaError_t launch_dtw_p2(const DtwJob &j, const DtwGeom &g, cudaStream_t s) {
     if (j.npairs <= 0) return cudaSuccess;
-    const int cl = dtw_lanes_cl(j.n, j.w);
-    if ((j.lanes || g.wide) && cl > 0) return launch_dtw_lanes_p2(j, g, cl, s);
+    const bool many = j.npairs_dev == nullptr && j.npairs >= 65536;
+    const LanesShape ls = dtw_lanes_shape(j.n, j.w, many);
+    // one query per pair: a thread per pair would read its own band-wide query
+    // window every row, the warp path one value per row and lane
+    const bool per_pair_wide = j.per_pair_y && j.n >= 64 && 2 * j.w + 1 > 32;
+    if ((j.lanes || g.wide || per_pair_wide) && ls.cl > 0) return launch_dtw_lanes_p2(j, g, ls, s);
     if (!g.wide && g.C <= kDtwGroupMaxC) {
         const int64_t warps = (j.npairs + 31) / 32;
         const bool xvec = (j.n % 4 == 0) && ((reinterpret_cast<uintptr_t>(j.db) & 15) == 0);

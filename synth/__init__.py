@@ -103,6 +103,18 @@ def _shape_rows(g: np.random.Generator, rows: int, n: int) -> np.ndarray:
     return out
 
 
+def white_noise(count: int, n: int, seed: int, stream: int = STREAM_DB) -> np.ndarray:
+    """`count` white-noise series x_i = N(0, 1) of length `n` (App. B), fp32 [count, n]."""
+    if count < 0 or n < 1:
+        raise ValueError("count >= 0 and n >= 1 required")
+    out = np.empty((count, n), dtype=np.float32)
+    step = max(1, (1 << 22) // n)
+    for k, r0 in enumerate(range(0, count, step)):
+        r1 = min(count, r0 + step)
+        out[r0:r1] = _rng(seed, stream, (1 << 21) + k).standard_normal((r1 - r0, n))
+    return out
+
+
 def shapes(count: int, n: int, seed: int, stream: int = STREAM_DB) -> np.ndarray:
     """`count` shape-like series of length `n`, fp32 [count, n], z-normalised in fp64."""
     if count < 0 or n < 1:

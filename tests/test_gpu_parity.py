@@ -154,6 +154,23 @@ def test_dtw_band_per_pair_query(api, p, n, w):
 
 
 @pytest.mark.parametrize("p", [1, 2])
+@pytest.mark.parametrize("n,w", [(64, 20), (128, 60), (100, 99)])
+def test_dtw_band_per_pair_many_pairs(api, p, n, w):
+    # 70,000 pairs with one query each: the warp path with two 16-lane groups
+    # per warp; a short launch of the same pairs takes the 32-lane groups, and
+    # both evaluate the same cells with the same fp32 operations
+    N = 70_000
+    X = synth.random_walks(N, n, seed=500 + n)
+    Y = synth.random_walks(N, n, seed=600 + n, stream=synth.STREAM_QUERY)
+    d = api.dtw_band(cuda(X), cuda(Y), w, p).cpu().numpy()
+    head = api.dtw_band(cuda(X[:300]), cuda(Y[:300]), w, p).cpu().numpy()
+    np.testing.assert_array_equal(d[:300], head)
+    for c in list(range(0, N, 1400)) + [N - 1]:
+        ref = oracle.dtw(X[c], Y[c], w, p)
+        assert close(d[c], ref), (n, w, c, d[c], ref)
+
+
+@pytest.mark.parametrize("p", [1, 2])
 @pytest.mark.parametrize("n,w", [(128, 12), (1024, 204)])
 def test_dtw_band_threshold(api, p, n, w):
     N = 64
