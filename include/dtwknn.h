@@ -268,6 +268,7 @@ typedef struct {
     int32_t seg_len;
     float ms;
     int32_t dtw_path; /* as in dtw_options */
+    int32_t filter_warps; /* warps per LB_Improved filter CTA, 1..8; 0: chosen from occupancy */
 } dtw_tuning;
 
 typedef struct {

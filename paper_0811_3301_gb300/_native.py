@@ -71,11 +71,11 @@ class Options(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("parts", ctypes.c_int32), ("seeds", ctypes.c_int32), ("seg_len", ctypes.c_int32),
-                ("ms", ctypes.c_float), ("dtw_path", ctypes.c_int32)]
+                ("ms", ctypes.c_float), ("dtw_path", ctypes.c_int32), ("filter_warps", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {"parts": int(self.parts), "seeds": int(self.seeds), "seg_len": int(self.seg_len),
-                "ms": float(self.ms), "dtw_path": int(self.dtw_path)}
+                "ms": float(self.ms), "dtw_path": int(self.dtw_path), "filter_warps": int(self.filter_warps)}
 
 
 class IndexStats(ctypes.Structure):

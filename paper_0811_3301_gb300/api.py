@@ -244,8 +244,9 @@ class DtwIndex:
         N.check(N.lib.dtw_index_get_tuning(self._h, int(n), int(w), int(k), ctypes.byref(t)))
         return t.as_dict()
 
-    def set_tuning(self, n: int, w: int, k: int, *, parts: int, seeds: int, seg_len: int, dtw_path: int = 0) -> None:
-        t = N.Tuning(int(parts), int(seeds), int(seg_len), -1.0, int(dtw_path))
+    def set_tuning(self, n: int, w: int, k: int, *, parts: int, seeds: int, seg_len: int, dtw_path: int = 0,
+                   filter_warps: int = 0) -> None:
+        t = N.Tuning(int(parts), int(seeds), int(seg_len), -1.0, int(dtw_path), int(filter_warps))
         N.check(N.lib.dtw_index_set_tuning(self._h, int(n), int(w), int(k), ctypes.byref(t)))
 
     def info(self) -> dict:

@@ -105,7 +105,8 @@ static int use_lanes(const CascadePlan &pl, int64_t npairs, bool main_stage) {
 // ---------------------------------------------------------------------------
 // plan and workspace
 // ---------------------------------------------------------------------------
-CascadePlan make_plan(int64_t N, int64_t Qmax, int n, int w, int p, int k, const dtw_options &o, int seg_len) {
+CascadePlan make_plan(int64_t N, int64_t Qmax, int n, int w, int p, int k, const dtw_options &o, int seg_len,
+                      int filter_warps) {
     CascadePlan pl{};
     pl.N = N;
     pl.n = n;
@@ -136,7 +137,7 @@ CascadePlan make_plan(int64_t N, int64_t Qmax, int n, int w, int p, int k, const
     pl.Qc = Qc;
     pl.seg_len = seg_len;
     pl.dtw_path = o.dtw_path;
-    pl.filter_warps = lbi_filter_warps(n, pl.we, std::max(pl.S, 1), pl.seg_len);
+    pl.filter_warps = lbi_filter_warps(n, pl.we, std::max(pl.S, 1), pl.seg_len, p, filter_warps);
     const int64_t nsegs = N > 0 ? (N + pl.seg_len - 1) / pl.seg_len : 1;
     pl.nseg = (int)nsegs * pl.filter_warps;
     // filter CTAs: about eight waves of four CTAs per SM; each takes enough
@@ -242,6 +243,7 @@ cudaError_t cascade_run(const CascadePlan &pl, const CascadeWs &l, const float *
     b.pair_count = pair_count;
     b.seg_len = pl.seg_len;
     b.seg_per_cta = pl.seg_per_cta;
+    b.filter_warps = pl.filter_warps;
     b.nseg = N > 0 ? pl.nseg : 0;
     b.seg_start = l.seg_start;
     b.seg_count = l.seg_count;

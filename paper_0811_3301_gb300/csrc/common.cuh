@@ -164,6 +164,7 @@ struct CascadeBufs {
     unsigned long long *pair_count;
     int seg_len, nseg;    // nseg: sub-segments per query (segments x filter warps)
     int seg_per_cta;      // consecutive segments one filter CTA handles
+    int filter_warps;     // warps per filter CTA (one sub-segment each)
     int32_t *seg_start;   // [Q][nseg]
     int32_t *seg_count;   // [Q][nseg]
     // work cursors and counters
@@ -178,7 +179,9 @@ cudaError_t launch_seed_select(const CascadeBufs &b, cudaStream_t s);
 cudaError_t launch_seed_kth(const CascadeBufs &b, cudaStream_t s);
 cudaError_t launch_query_copies(const float *y, int64_t count, int n, QueryCopies qc, cudaStream_t s);
 cudaError_t launch_lbi_filter(const CascadeBufs &b, cudaStream_t s);
-int lbi_filter_warps(int n, int w, int S, int seg_len);  // warps per filter CTA (one sub-segment each)
+// warps per filter CTA (one sub-segment each): `want` (1..8) if its shared
+// memory fits a CTA, else fewer; want = 0 chooses from the occupancy
+int lbi_filter_warps(int n, int w, int S, int seg_len, int p, int want = 0);
 cudaError_t launch_finalize(const CascadeBufs &b, cudaStream_t s);
 cudaError_t launch_group_by_query(const CascadeBufs &b, cudaStream_t s);
 

@@ -206,6 +206,7 @@ Tuning tuning_for(const dtw_index *ix, int n, int w, int k) {
     t.seg_len = 1024;
     t.ms = -1.0f;
     t.dtw_path = ix->opt.dtw_path;
+    t.filter_warps = 0;
     return t;
 }
 
@@ -215,7 +216,7 @@ CascadePlan plan_for(const dtw_index *ix, int b, int w, int k, int64_t qmax, con
     o.parts = t.parts;
     o.seeds = t.seeds;
     o.dtw_path = t.dtw_path;
-    return make_plan(bk.N, qmax, bk.n, w, ix->p, k, o, t.seg_len);
+    return make_plan(bk.N, qmax, bk.n, w, ix->p, k, o, t.seg_len, t.filter_warps);
 }
 
 // ---------------------------------------------------------------------------
@@ -397,7 +398,8 @@ static std::vector<int64_t> graph_key(const Batch &bt) {
     std::vector<int64_t> key{bt.Q, bt.k_stride, bt.total, bt.flags, (int64_t)bt.groups.size()};
     for (const auto &gr : bt.groups) {
         key.insert(key.end(),
-                   {gr.bucket, gr.w, gr.k, gr.qn, gr.pl.parts, gr.pl.S, gr.pl.seg_len, gr.pl.dtw_path, gr.stream});
+                   {gr.bucket, gr.w, gr.k, gr.qn, gr.pl.parts, gr.pl.S, gr.pl.seg_len, gr.pl.dtw_path,
+                    gr.pl.filter_warps, gr.stream});
     }
     return key;
 }
@@ -509,13 +511,14 @@ dtw_status tune_group(dtw_index *ix, int b, int w, int k, const float *qdev, int
     const std::vector<int> seg_c{512, 1024, 2048};
     std::vector<int> path_c{1};
     if (dtw_lanes_cl(n, we) > 0) path_c.push_back(2);
+    const std::vector<int> fw_c{0, 4, 5, 6, 7, 8};
 
     // scratch sized for the largest candidate plan
     size_t ws_max = 0;
     for (int pc : parts_c)
         for (int sd : seeds_c)
             for (int sg : seg_c) {
-                Tuning t{pc, sd, sg, 0.0f, 0};
+                Tuning t{pc, sd, sg, 0.0f, 0, 0};
                 ws_max = std::max(ws_max, cascade_ws_bytes(plan_for(ix, b, we, k, qn, t)));
             }
     Carve cv0;
@@ -575,18 +578,21 @@ dtw_status tune_group(dtw_index *ix, int b, int w, int k, const float *qdev, int
     best.seeds = ix->opt.seeds > 0 ? ix->opt.seeds : 16;
     best.seg_len = 1024;
     best.dtw_path = ix->opt.dtw_path;
+    best.filter_warps = 0;
     float best_ms = INFINITY;
     if ((st = time_one(best, &best_ms)) != DTW_OK) goto done;
-    for (int axis = 0; axis < 4; ++axis) {
-        const std::vector<int> &cands = axis == 0 ? parts_c : axis == 1 ? seeds_c : axis == 2 ? seg_c : path_c;
+    for (int axis = 0; axis < 5; ++axis) {
+        const std::vector<int> &cands =
+            axis == 0 ? parts_c : axis == 1 ? seeds_c : axis == 2 ? seg_c : axis == 3 ? path_c : fw_c;
         for (int v : cands) {
             Tuning t = best;
             if (axis == 0) t.parts = v;
             if (axis == 1) t.seeds = v;
             if (axis == 2) t.seg_len = v;
             if (axis == 3) t.dtw_path = v;
+            if (axis == 4) t.filter_warps = v;
             if (t.parts == best.parts && t.seeds == best.seeds && t.seg_len == best.seg_len &&
-                t.dtw_path == best.dtw_path)
+                t.dtw_path == best.dtw_path && t.filter_warps == best.filter_warps)
                 continue;
             float ms = INFINITY;
             if ((st = time_one(t, &ms)) != DTW_OK) goto done;
@@ -757,6 +763,7 @@ dtw_status dtw_index_tune(dtw_index *ix, const float *sample, int64_t count, int
         out->seg_len = t.seg_len;
         out->ms = t.ms;
         out->dtw_path = t.dtw_path;
+        out->filter_warps = t.filter_warps;
     }
     return st;
 }
@@ -773,6 +780,7 @@ dtw_status dtw_index_get_tuning(dtw_index *ix, int32_t n, int32_t w, int32_t k, 
     out->seg_len = t.seg_len;
     out->ms = t.ms;
     out->dtw_path = t.dtw_path;
+    out->filter_warps = t.filter_warps;
     return DTW_OK;
 }
 
@@ -780,14 +788,15 @@ dtw_status dtw_index_set_tuning(dtw_index *ix, int32_t n, int32_t w, int32_t k, 
     set_error_message("");
     if (!ix || !t) return ix_fail(DTW_ERR_INVALID_ARG, "null pointer");
     if (t->parts < -1 || t->parts > n || t->seeds < 0 || t->seeds > 32 ||
-        (t->seg_len != 512 && t->seg_len != 1024 && t->seg_len != 2048) || t->dtw_path < 0 || t->dtw_path > 2)
-        return ix_fail(DTW_ERR_INVALID_ARG,
-                       "tuning out of range (parts in [-1, n], seeds in [0, 32], seg_len 512/1024/2048, dtw_path 0-2)");
+        (t->seg_len != 512 && t->seg_len != 1024 && t->seg_len != 2048) || t->dtw_path < 0 || t->dtw_path > 2 ||
+        t->filter_warps < 0 || t->filter_warps > 8)
+        return ix_fail(DTW_ERR_INVALID_ARG, "tuning out of range (parts in [-1, n], seeds in [0, 32], seg_len "
+                                            "512/1024/2048, dtw_path 0-2, filter_warps 0-8)");
     if (w < 0 || k < 1 || k > DTW_MAX_K) return ix_fail(DTW_ERR_INVALID_ARG, "w or k out of range");
     std::lock_guard<std::mutex> lk(ix->mu);
     if (find_bucket(ix, n) < 0) return ix_fail(DTW_ERR_NO_BUCKET, "no bucket of length %d", n);
     const int we = w < n - 1 ? w : n - 1;
-    ix->tuned[TuneKey{n, we, k}] = Tuning{t->parts, t->seeds, t->seg_len, t->ms, t->dtw_path};
+    ix->tuned[TuneKey{n, we, k}] = Tuning{t->parts, t->seeds, t->seg_len, t->ms, t->dtw_path, t->filter_warps};
     return DTW_OK;
 }
 

@@ -67,8 +67,9 @@ struct TuneKey {
 
 struct Tuning {
     int parts, seeds, seg_len;
-    float ms;      // time of the tuning sample, -1 if not tuned
-    int dtw_path;  // as in dtw_options
+    float ms;          // time of the tuning sample, -1 if not tuned
+    int dtw_path;      // as in dtw_options
+    int filter_warps;  // 0: from occupancy
 };
 
 // Queries of one batch with equal (bucket, w, k).

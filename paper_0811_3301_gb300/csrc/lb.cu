@@ -5,6 +5,10 @@
 //
 // where H(x, y) clamps x into the envelope of y.  All sums are fp32 in power
 // space; the root is taken only where a bound is returned to the caller.
+#include <array>
+#include <map>
+#include <mutex>
+
 #include "common.cuh"
 
 namespace dtwk {
@@ -902,22 +906,82 @@ __global__ void __launch_bounds__(256, 3) k_lbi_filter(CascadeBufs b, bool vec) 
     }  // segments of this CTA
 }
 
-int lbi_filter_warps(int n, int w, int S, int seg_len) {
+static size_t lbi_filter_smem(int n, int w, int S, int seg_len, int nw) {
     const int64_t per_warp = (int64_t)lbi_scratch_floats(n, w) * sizeof(float);
     const int64_t per_query = (int64_t)lbi_query_floats(n) * sizeof(float);
-    const int64_t fixed = per_query + (int64_t)S * 4 + 64;
-    // aim at 4 CTAs of up to 8 warps per SM when the scratch is small
-    int nw = 8;
-    while (nw > 1 && fixed + nw * (per_warp + 8 * (seg_len / nw + 32)) > 56 * 1024) --nw;
-    return nw;
+    return (size_t)(per_query + (int64_t)S * 4 + 64 + nw * (per_warp + 8 * (seg_len / nw + 32)));
+}
+
+// Warps per filter CTA.  Chunks in registers (n <= 256): as many as fit (up
+// to 8): measured fastest, as the CTA's query staging and its segments are
+// shared by more warps.  Chunks in shared memory: the count that keeps the
+// most warps resident per SM, by the occupancy calculator (shared memory and
+// registers).  Cached per shape.
+template <int P, int MT>
+static int lbi_filter_warps_for(int n, int w, int S, int seg_len) {
+    if constexpr (MT > 0) {
+        int nw = 8;
+        while (nw > 1 && lbi_filter_smem(n, w, S, seg_len, nw) > 227 * 1024) --nw;
+        return nw;
+    }
+    static std::mutex mu;
+    static std::map<std::array<int, 4>, int> cache;
+    const std::array<int, 4> key{n, w, S, seg_len};
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    cudaFuncSetAttribute(k_lbi_filter<P, MT>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         (int)cudaSharedmemCarveoutMaxShared);
+    int best = 0, best_warps = 0;
+    for (int nw = 1; nw <= 8; ++nw) {
+        const size_t smem = lbi_filter_smem(n, w, S, seg_len, nw);
+        if (smem > 227 * 1024) break;
+        int blocks = 0;
+        if (cudaFuncSetAttribute(k_lbi_filter<P, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+                cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_lbi_filter<P, MT>, nw * 32, smem) !=
+                cudaSuccess) {
+            cudaGetLastError();
+            blocks = 0;
+        }
+        if (blocks * nw > best_warps) {
+            best_warps = blocks * nw;
+            best = nw;
+        }
+    }
+    if (best == 0) {
+        // no answer from the calculator: the largest count within 72 KB
+        best = 8;
+        while (best > 1 && lbi_filter_smem(n, w, S, seg_len, best) > 72 * 1024) --best;
+    }
+    cache[key] = best;
+    return best;
+}
+
+template <int P>
+static int lbi_filter_warps_p(int n, int w, int S, int seg_len) {
+    switch (lbi_geom(n).m) {
+        case 1: return lbi_filter_warps_for<P, 1>(n, w, S, seg_len);
+        case 2: return lbi_filter_warps_for<P, 2>(n, w, S, seg_len);
+        case 4: return lbi_filter_warps_for<P, 4>(n, w, S, seg_len);
+        case 8: return lbi_filter_warps_for<P, 8>(n, w, S, seg_len);
+        default: return lbi_filter_warps_for<P, 0>(n, w, S, seg_len);
+    }
+}
+
+int lbi_filter_warps(int n, int w, int S, int seg_len, int p, int want) {
+    if (want > 0) {
+        int nw = want > 8 ? 8 : want;
+        while (nw > 1 && lbi_filter_smem(n, w, S, seg_len, nw) > 227 * 1024) --nw;
+        return nw;
+    }
+    return p == 1 ? lbi_filter_warps_p<1>(n, w, S, seg_len) : lbi_filter_warps_p<2>(n, w, S, seg_len);
 }
 
 template <int P, int MT>
 static void lbi_filter_go(const CascadeBufs &b, bool vec, cudaStream_t s) {
-    const int nw = lbi_filter_warps(b.n, b.w, b.S, b.seg_len);
-    const int64_t per_warp = (int64_t)lbi_scratch_floats(b.n, b.w) * sizeof(float);
-    const int64_t per_query = (int64_t)lbi_query_floats(b.n) * sizeof(float);
-    const size_t smem = (size_t)per_query + (size_t)b.S * 4 + 64 + (size_t)nw * (per_warp + 8 * (b.seg_len / nw + 32));
+    const int nw = b.filter_warps > 0 ? b.filter_warps : lbi_filter_warps(b.n, b.w, b.S, b.seg_len, P);
+    const size_t smem = lbi_filter_smem(b.n, b.w, b.S, b.seg_len, nw);
     const int nsegs = b.nseg / nw;
     const dim3 grid(b.Q, (nsegs + b.seg_per_cta - 1) / b.seg_per_cta);
     cudaFuncSetAttribute(k_lbi_filter<P, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
