@@ -260,7 +260,8 @@ enum {
 };
 
 /* Cascade parameters of one (n, w, k); see dtw_options for parts, seeds and dtw_path.
- * seg_len: candidates per filter segment (512, 1024 or 2048). ms: time of the
+ * seg_len: candidates per filter segment (512, 1024 or 2048; 0: 2048 for n <= 256,
+ * else 1024). ms: time of the
  * tuning sample in milliseconds, or -1 when the values are the defaults. */
 typedef struct {
     int32_t parts;

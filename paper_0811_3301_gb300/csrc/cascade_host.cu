@@ -135,7 +135,9 @@ CascadePlan make_plan(int64_t N, int64_t Qmax, int n, int w, int p, int k, const
     if (Qc > Qmax) Qc = Qmax;
     if (Qc < 1) Qc = 1;
     pl.Qc = Qc;
-    pl.seg_len = seg_len;
+    // filter segments: longer ones amortise more of a CTA's setup; for series
+    // up to 256 (chunks in registers) 2048 measured fastest, 1024 otherwise
+    pl.seg_len = seg_len > 0 ? seg_len : (n <= 256 ? 2048 : 1024);
     pl.dtw_path = o.dtw_path;
     pl.filter_warps = lbi_filter_warps(n, pl.we, std::max(pl.S, 1), pl.seg_len, p, filter_warps);
     const int64_t nsegs = N > 0 ? (N + pl.seg_len - 1) / pl.seg_len : 1;

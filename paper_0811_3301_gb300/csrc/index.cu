@@ -203,7 +203,7 @@ Tuning tuning_for(const dtw_index *ix, int n, int w, int k) {
     Tuning t{};
     t.parts = ix->opt.parts;
     t.seeds = ix->opt.seeds;
-    t.seg_len = 1024;
+    t.seg_len = 0;
     t.ms = -1.0f;
     t.dtw_path = ix->opt.dtw_path;
     t.filter_warps = 0;
@@ -576,7 +576,7 @@ dtw_status tune_group(dtw_index *ix, int b, int w, int k, const float *qdev, int
     Tuning best = tuning_for(ix, n, we, k);
     best.parts = ix->opt.parts == 0 ? (n >= 64 ? n / 8 : -1) : ix->opt.parts;
     best.seeds = ix->opt.seeds > 0 ? ix->opt.seeds : 16;
-    best.seg_len = 1024;
+    best.seg_len = 0;
     best.dtw_path = ix->opt.dtw_path;
     best.filter_warps = 0;
     float best_ms = INFINITY;
@@ -788,10 +788,11 @@ dtw_status dtw_index_set_tuning(dtw_index *ix, int32_t n, int32_t w, int32_t k, 
     set_error_message("");
     if (!ix || !t) return ix_fail(DTW_ERR_INVALID_ARG, "null pointer");
     if (t->parts < -1 || t->parts > n || t->seeds < 0 || t->seeds > 32 ||
-        (t->seg_len != 512 && t->seg_len != 1024 && t->seg_len != 2048) || t->dtw_path < 0 || t->dtw_path > 2 ||
+        (t->seg_len != 0 && t->seg_len != 512 && t->seg_len != 1024 && t->seg_len != 2048) || t->dtw_path < 0 ||
+        t->dtw_path > 2 ||
         t->filter_warps < 0 || t->filter_warps > 8)
         return ix_fail(DTW_ERR_INVALID_ARG, "tuning out of range (parts in [-1, n], seeds in [0, 32], seg_len "
-                                            "512/1024/2048, dtw_path 0-2, filter_warps 0-8)");
+                                            "0/512/1024/2048, dtw_path 0-2, filter_warps 0-8)");
     if (w < 0 || k < 1 || k > DTW_MAX_K) return ix_fail(DTW_ERR_INVALID_ARG, "w or k out of range");
     std::lock_guard<std::mutex> lk(ix->mu);
     if (find_bucket(ix, n) < 0) return ix_fail(DTW_ERR_NO_BUCKET, "no bucket of length %d", n);
