@@ -343,6 +343,9 @@ typedef struct {
     int64_t slot_bytes; /* device arena per slot; 0: 2 GiB */
     int32_t max_wait_us;
     int32_t flags;      /* DTW_BATCH_GRAPH, DTW_BATCH_SERIAL or DTW_BATCH_PER_QUERY for every batch */
+    int32_t batch_timeout_ms; /* watchdog: a batch still running this long after launch completes
+                                 its requests with DTW_ERR_TIMEOUT (their buffers are not written;
+                                 the slot stays reserved until the device finishes); 0: none */
 } dtw_server_config;
 
 typedef struct {
@@ -358,6 +361,7 @@ typedef struct {
     int64_t submitted, completed, failed, batches;
     int64_t max_inflight_batches, max_batch_seen;
     int64_t pending, inflight_batches;
+    int64_t timed_out; /* requests completed by the watchdog */
 } dtw_server_stats;
 
 /* Starts a server on ix (which must outlive it); cfg may be NULL (defaults).
@@ -368,8 +372,9 @@ dtw_status dtw_server_create(dtw_index *ix, const dtw_server_config *cfg, dtw_se
  * result is written to out_idx [k] and out_dist [k] (host memory that must
  * stay valid until the request's completion is polled).  arrival_ns (0: now)
  * is the request's arrival time on the dtw_monotonic_ns clock.  Fails with
- * DTW_ERR_NO_BUCKET when no bucket has length n, DTW_ERR_OOM when a batch of
- * this request alone does not fit slot_bytes. */
+ * DTW_ERR_INVALID_ARG when the query holds a NaN or an infinity (they break
+ * the ordering of the bounds), DTW_ERR_NO_BUCKET when no bucket has length n,
+ * DTW_ERR_OOM when a batch of this request alone does not fit slot_bytes. */
 dtw_status dtw_server_submit(dtw_server *srv, const float *query, int32_t n, int32_t w, int32_t k,
                              int64_t *out_idx, float *out_dist, int64_t arrival_ns, uint64_t *ticket);
 

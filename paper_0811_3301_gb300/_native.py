@@ -92,7 +92,7 @@ BATCH_GRAPH, BATCH_AUTOTUNE, BATCH_SERIAL, BATCH_PER_QUERY = 1, 2, 4, 8
 
 class ServerConfig(ctypes.Structure):
     _fields_ = [("slots", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("slot_bytes", ctypes.c_int64),
-                ("max_wait_us", ctypes.c_int32), ("flags", ctypes.c_int32)]
+                ("max_wait_us", ctypes.c_int32), ("flags", ctypes.c_int32), ("batch_timeout_ms", ctypes.c_int32)]
 
 
 class Completion(ctypes.Structure):
@@ -103,7 +103,7 @@ class Completion(ctypes.Structure):
 class ServerStats(ctypes.Structure):
     _fields_ = [(name, ctypes.c_int64) for name in ("submitted", "completed", "failed", "batches",
                                                      "max_inflight_batches", "max_batch_seen", "pending",
-                                                     "inflight_batches")]
+                                                     "inflight_batches", "timed_out")]
 
     def as_dict(self) -> dict:
         return {k: int(getattr(self, k)) for k, _ in self._fields_}

@@ -314,10 +314,12 @@ class DtwServer:
     """
 
     def __init__(self, index: DtwIndex, *, slots: int = 4, max_batch: int = 512, slot_bytes: int = 0,
-                 max_wait_us: int = 0, graph: bool = False, serial: bool = False, per_query: bool = False):
+                 max_wait_us: int = 0, graph: bool = False, serial: bool = False, per_query: bool = False,
+                 batch_timeout_ms: int = 0):
         flags = ((N.BATCH_GRAPH if graph else 0) | (N.BATCH_SERIAL if serial else 0) |
                  (N.BATCH_PER_QUERY if per_query else 0))
-        cfg = N.ServerConfig(int(slots), int(max_batch), int(slot_bytes), int(max_wait_us), flags)
+        cfg = N.ServerConfig(int(slots), int(max_batch), int(slot_bytes), int(max_wait_us), flags,
+                             int(batch_timeout_ms))
         h = ctypes.c_void_p()
         N.check(N.lib.dtw_server_create(index._h, ctypes.byref(cfg), ctypes.byref(h)))
         self._h = h

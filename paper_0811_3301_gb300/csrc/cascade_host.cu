@@ -7,6 +7,8 @@
 #include <mutex>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "cascade_host.cuh"
 
 namespace dtwk {
@@ -47,13 +49,18 @@ cudaError_t profile_collect(double *ms, int64_t *launches, bool reset) {
     return cudaSuccess;
 }
 
-// Records a pair of events around a stage when profiling is on and the
-// stream is not being captured.
+static const char *const kStageNames[DTW_NUM_STAGES] = {"envelope", "lb_keogh",    "seed_select", "seed_dtw",
+                                                         "seed_kth", "lb_improved", "dtw",         "finalize"};
+
+// Marks a stage with an NVTX range (host side, for timeline tools; no cost
+// without one attached) and, when profiling is on and the stream is not being
+// captured, records a pair of events around it.
 struct StageTimer {
     StageEvents ev{};
     bool on = false;
     cudaStream_t s;
     StageTimer(int stage, cudaStream_t st) : s(st) {
+        nvtxRangePushA(stage >= 0 && stage < DTW_NUM_STAGES ? kStageNames[stage] : "stage");
         if (!g_prof_on) return;
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
         if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
@@ -69,6 +76,7 @@ struct StageTimer {
         cudaEventRecord(ev.a, s);
     }
     ~StageTimer() {
+        nvtxRangePop();
         if (!on) return;
         cudaEventRecord(ev.b, s);
         std::lock_guard<std::mutex> lk(g_prof_mu);

@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <array>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -47,6 +48,8 @@ struct ServerSlot {
     std::vector<Request> reqs;
     Batch bt;
     int k_stride = 1;
+    int64_t launched_ns = 0;
+    bool timed_out = false;  // its requests were completed by the watchdog
     float *hq = nullptr;  // pinned staged queries
     size_t hq_cap = 0;
     int64_t *hoi = nullptr;  // pinned outputs [max_batch][DTW_MAX_K]
@@ -162,10 +165,27 @@ static void launch_slot(dtw_server *srv, ServerSlot &ss, std::unique_lock<std::m
         return;
     }
     ss.busy = true;
+    ss.timed_out = false;
+    ss.launched_ns = now_ns();
     srv->inflight += 1;
     srv->st.batches += 1;
     srv->st.max_inflight_batches = std::max<int64_t>(srv->st.max_inflight_batches, srv->inflight);
     srv->st.max_batch_seen = std::max<int64_t>(srv->st.max_batch_seen, Q);
+}
+
+// The watchdog: completes a slot's requests with DTW_ERR_TIMEOUT when its
+// batch has run past the deadline (srv->mu held).  The slot is released only
+// when the device work ends (finish_slot), since it still uses the buffers.
+static void expire_slot(dtw_server *srv, ServerSlot &ss) {
+    const int64_t t = now_ns();
+    for (auto &r : ss.reqs)
+        srv->done.push_back(dtw_completion{r.ticket, (int32_t)DTW_ERR_TIMEOUT, r.k, r.arrival, r.admit, t});
+    srv->st.completed += (int64_t)ss.reqs.size();
+    srv->st.failed += (int64_t)ss.reqs.size();
+    srv->st.timed_out += (int64_t)ss.reqs.size();
+    ss.reqs.clear();
+    ss.timed_out = true;
+    srv->done_cv.notify_all();
 }
 
 // Delivers the results of a completed slot (srv->mu held).
@@ -196,7 +216,14 @@ static void scheduler(dtw_server *srv) {
         for (auto &ss : srv->slots) {
             if (!ss.busy) continue;
             const cudaError_t e = cudaEventQuery(ss.ev);
-            if (e == cudaErrorNotReady) continue;
+            if (e == cudaErrorNotReady) {
+                if (!ss.timed_out && srv->cfg.batch_timeout_ms > 0 &&
+                    now_ns() - ss.launched_ns > (int64_t)srv->cfg.batch_timeout_ms * 1000000) {
+                    expire_slot(srv, ss);
+                    progress = true;
+                }
+                continue;
+            }
             if (e != cudaSuccess) cudaGetLastError();
             finish_slot(srv, ss, e);
             progress = true;
@@ -234,12 +261,13 @@ dtw_status dtw_server_create(dtw_index *ix, const dtw_server_config *cfg, dtw_se
     set_error_message("");
     if (!ix || !out) return ix_fail(DTW_ERR_INVALID_ARG, "null pointer");
     *out = nullptr;
-    dtw_server_config c{4, 512, 0, 0, 0};
+    dtw_server_config c{4, 512, 0, 0, 0, 0};
     if (cfg) c = *cfg;
     if (c.slots < 1 || c.slots > 16) return ix_fail(DTW_ERR_INVALID_ARG, "slots=%d outside [1, 16]", c.slots);
     if (c.max_batch < 1 || c.max_batch > 65536)
         return ix_fail(DTW_ERR_INVALID_ARG, "max_batch=%d outside [1, 65536]", c.max_batch);
-    if (c.slot_bytes < 0 || c.max_wait_us < 0) return ix_fail(DTW_ERR_INVALID_ARG, "negative slot_bytes or max_wait_us");
+    if (c.slot_bytes < 0 || c.max_wait_us < 0 || c.batch_timeout_ms < 0)
+        return ix_fail(DTW_ERR_INVALID_ARG, "negative slot_bytes, max_wait_us or batch_timeout_ms");
     if (c.flags & ~(DTW_BATCH_GRAPH | DTW_BATCH_SERIAL | DTW_BATCH_PER_QUERY))
         return ix_fail(DTW_ERR_INVALID_ARG, "flags=0x%x: only GRAPH, SERIAL and PER_QUERY apply", c.flags);
     if (c.slot_bytes == 0) c.slot_bytes = (int64_t)2 << 30;
@@ -309,6 +337,9 @@ dtw_status dtw_server_submit(dtw_server *srv, const float *query, int32_t n, int
     if (n < 1 || n > DTW_MAX_N) return ix_fail(DTW_ERR_INVALID_ARG, "n=%d out of range", n);
     if (w < 0) return ix_fail(DTW_ERR_INVALID_ARG, "w=%d must be >= 0", w);
     if (k < 1 || k > DTW_MAX_K) return ix_fail(DTW_ERR_INVALID_ARG, "k=%d outside [1, %d]", k, DTW_MAX_K);
+    for (int32_t i = 0; i < n; ++i)
+        if (!std::isfinite(query[i]))
+            return ix_fail(DTW_ERR_INVALID_ARG, "query value %d is not finite (NaN or infinity)", i);
     dtw_index *ix = srv->ix;
     int b;
     size_t need;

@@ -152,3 +152,36 @@ def test_query_without_bucket_is_rejected(api, index):
         with pytest.raises(api.DtwError) as e:
             srv.submit(np.zeros(100, np.float32), 10, 1)
         assert e.value.status == 5  # DTW_ERR_NO_BUCKET
+
+
+def test_poisoned_request_is_rejected_at_admission(api, index, requests):
+    q = requests[0][0].copy()
+    q[5] = np.nan
+    with api.DtwServer(index, slots=1, max_batch=4) as srv:
+        with pytest.raises(api.DtwError) as e:
+            srv.submit(q, requests[0][1], requests[0][2])
+        assert e.value.status == 1  # DTW_ERR_INVALID_ARG
+        q[5] = np.inf
+        with pytest.raises(api.DtwError):
+            srv.submit(q, requests[0][1], requests[0][2])
+        # the server keeps serving
+        t = srv.submit(requests[1][0], requests[1][1], requests[1][2])
+        assert collect(srv, [t])[0]["status"] == 0
+
+
+def test_watchdog_completes_overdue_batches_with_timeout(api, index, requests, alone):
+    # one query per launch makes a batch of many requests take milliseconds;
+    # with a 1 ms deadline the watchdog completes them with DTW_ERR_TIMEOUT
+    # (their buffers untouched) while the device finishes, and the slot is
+    # reused once it has
+    with api.DtwServer(index, slots=1, max_batch=64, per_query=True, batch_timeout_ms=1) as srv:
+        tickets = [srv.submit(q, w, k) for q, w, k in requests[:80]]
+        res = collect(srv, tickets)
+        info = srv.info()
+    timed = [r for r in res if r["status"] == 4]  # DTW_ERR_TIMEOUT
+    assert len(timed) >= 1 and info["timed_out"] == len(timed), info
+    assert info["completed"] == len(tickets)
+    for a, b in zip(alone, res):
+        if b["status"] == 0:
+            np.testing.assert_array_equal(a["idx"], b["idx"])
+            np.testing.assert_array_equal(a["dist"], b["dist"])
