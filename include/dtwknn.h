@@ -81,7 +81,8 @@ typedef struct {
                       of every pair), otherwise 1 <= d <= n */
     int32_t dtw_path; /* DTW kernel of the cascade's DTW stages: 0 chooses (one warp per
                          pair for long series or wide bands, else one thread per pair),
-                         1 one thread per pair where the band fits, 2 one warp per pair */
+                         1 one thread per pair where the band fits, 2 one warp per pair,
+                         3 one warp per two pairs (16-lane groups) where the band allows */
 } dtw_options;
 
 /*

@@ -315,7 +315,7 @@ dtw_status knn_search_ex(const float *db, int64_t N, const float *queries, int64
         return fail(DTW_ERR_INVALID_ARG, "mode=%d unknown", o.mode);
     if (!(o.slack >= 0.0f) || std::isinf(o.slack)) return fail(DTW_ERR_INVALID_ARG, "slack must be finite and >= 0");
     if (o.seeds < 0) return fail(DTW_ERR_INVALID_ARG, "seeds=%d must be >= 0", o.seeds);
-    if (o.dtw_path < 0 || o.dtw_path > 2) return fail(DTW_ERR_INVALID_ARG, "dtw_path=%d outside [0, 2]", o.dtw_path);
+    if (o.dtw_path < 0 || o.dtw_path > 3) return fail(DTW_ERR_INVALID_ARG, "dtw_path=%d outside [0, 3]", o.dtw_path);
     if (stats) memset(stats, 0, sizeof(*stats));
     if (Q == 0) return DTW_OK;
     if (!queries || !out_idx || !out_dist || (N > 0 && !db)) return fail(DTW_ERR_INVALID_ARG, "null pointer");

@@ -104,6 +104,7 @@ static cudaError_t launch_dtw_any(const DtwJob &j, const DtwGeom &g, cudaStream_
 // Bands wider than one thread's registers always take the warp path.
 static int use_lanes(const CascadePlan &pl, int64_t npairs, bool main_stage) {
     if (dtw_lanes_cl(pl.n, pl.we) == 0) return 0;
+    if (pl.dtw_path == 3) return main_stage ? 2 : 1;
     if (pl.dtw_path == 2) return 1;
     if (pl.dtw_path == 1) return 0;
     if (main_stage) return 0;

@@ -208,7 +208,7 @@ struct DtwJob {
     int root_out;             // store DTW_p (root taken) instead of DTW_p^p
     unsigned long long *cursor;    // chunk cursor (zeroed by the caller)
     unsigned long long *counters;  // nullable
-    int lanes;                // 1: warp path (32 lanes share a pair's band, two pairs per warp)
+    int lanes;                // 1: warp path (lane groups share a pair's band); 2: with 16-lane groups
 };
 
 

@@ -18,7 +18,7 @@ int blocks_for(K kernel, int64_t warps_needed) {
 
 cudaError_t launch_dtw_p1(const DtwJob &j, const DtwGeom &g, cudaStream_t s) {
     if (j.npairs <= 0) return cudaSuccess;
-    const bool many = j.npairs_dev == nullptr && j.npairs >= 65536;
+    const bool many = j.lanes == 2 || (j.npairs_dev == nullptr && j.npairs >= 65536);
     const LanesShape ls = dtw_lanes_shape(j.n, j.w, many);
     // one query per pair: a thread per pair would read its own band-wide query
     // window every row, the warp path one value per row and lane

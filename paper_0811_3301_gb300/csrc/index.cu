@@ -510,7 +510,10 @@ dtw_status tune_group(dtw_index *ix, int b, int w, int k, const float *qdev, int
         if (sd >= k && sd <= 32 && std::find(seeds_c.begin(), seeds_c.end(), sd) == seeds_c.end()) seeds_c.push_back(sd);
     const std::vector<int> seg_c{512, 1024, 2048};
     std::vector<int> path_c{1};
-    if (dtw_lanes_cl(n, we) > 0) path_c.push_back(2);
+    if (dtw_lanes_cl(n, we) > 0) {
+        path_c.push_back(2);
+        if (2 * we + 1 <= 512) path_c.push_back(3);
+    }
     const std::vector<int> fw_c{0, 4, 5, 6, 7, 8};
 
     // scratch sized for the largest candidate plan
@@ -684,7 +687,7 @@ dtw_status dtw_index_create(int32_t p, const dtw_options *opt, dtw_index **out) 
     if (!(o.slack >= 0.0f) || std::isinf(o.slack)) return ix_fail(DTW_ERR_INVALID_ARG, "slack must be finite and >= 0");
     if (o.seeds < 0) return ix_fail(DTW_ERR_INVALID_ARG, "seeds=%d must be >= 0", o.seeds);
     if (o.parts < -1) return ix_fail(DTW_ERR_INVALID_ARG, "parts=%d must be >= -1", o.parts);
-    if (o.dtw_path < 0 || o.dtw_path > 2) return ix_fail(DTW_ERR_INVALID_ARG, "dtw_path=%d outside [0, 2]", o.dtw_path);
+    if (o.dtw_path < 0 || o.dtw_path > 3) return ix_fail(DTW_ERR_INVALID_ARG, "dtw_path=%d outside [0, 3]", o.dtw_path);
     auto *ix = new dtw_index();
     ix->p = p;
     ix->opt = o;
@@ -789,10 +792,10 @@ dtw_status dtw_index_set_tuning(dtw_index *ix, int32_t n, int32_t w, int32_t k, 
     if (!ix || !t) return ix_fail(DTW_ERR_INVALID_ARG, "null pointer");
     if (t->parts < -1 || t->parts > n || t->seeds < 0 || t->seeds > 32 ||
         (t->seg_len != 0 && t->seg_len != 512 && t->seg_len != 1024 && t->seg_len != 2048) || t->dtw_path < 0 ||
-        t->dtw_path > 2 ||
+        t->dtw_path > 3 ||
         t->filter_warps < 0 || t->filter_warps > 8)
         return ix_fail(DTW_ERR_INVALID_ARG, "tuning out of range (parts in [-1, n], seeds in [0, 32], seg_len "
-                                            "0/512/1024/2048, dtw_path 0-2, filter_warps 0-8)");
+                                            "0/512/1024/2048, dtw_path 0-3, filter_warps 0-8)");
     if (w < 0 || k < 1 || k > DTW_MAX_K) return ix_fail(DTW_ERR_INVALID_ARG, "w or k out of range");
     std::lock_guard<std::mutex> lk(ix->mu);
     if (find_bucket(ix, n) < 0) return ix_fail(DTW_ERR_NO_BUCKET, "no bucket of length %d", n);

@@ -272,6 +272,10 @@ def test_knn_warp_dtw_path(api, p, n, w, k):
     wi, wd, _ = _knn_case(api, db, qs, w, p, k, dtw_path=2)
     ti, td = api.knn_search(cuda(db), cuda(qs), w, p, k, dtw_path=1)
     assert torch.equal(wi, ti) and torch.equal(wd, td)
+    if 2 * min(w, n - 1) + 1 <= 512:
+        # the main stage on two 16-lane groups per warp
+        gi, gd = api.knn_search(cuda(db), cuda(qs), w, p, k, dtw_path=3)
+        assert torch.equal(gi, ti) and torch.equal(gd, td)
 
 
 def test_knn_edge_cases(api):
