@@ -105,6 +105,14 @@ def cpu_info():
                 break
     except OSError:
         pass
+    if not model:
+        try:  # Arm hosts name the core in lscpu only
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.lower().startswith(("model name", "vendor id")):
+                    model = (model + " " + line.split(":", 1)[1].strip()).strip()
+        except (OSError, subprocess.SubprocessError):
+            pass
     return os.cpu_count() or 1, model
 
 
@@ -122,9 +130,15 @@ def oracle_rate(db, queries, w, p, k, budget_s):
     t0 = time.perf_counter()
     oracle.knn_cascade(db, queries[:m], w, p, k, mode=1, threads=cores)
     dt = time.perf_counter() - t0
+    # the same scan on one thread, over a few queries
+    m1 = max(1, min(len(queries), int(budget_s / 8 / per_q / cores) or 1, 8))
+    t0 = time.perf_counter()
+    oracle.knn_cascade(db, queries[:m1], w, p, k, mode=1, threads=1)
+    dt1 = time.perf_counter() - t0
     return {"value": m / dt, "unit": "queries/s", "cores": cores, "cpu": model, "kind": "oracle",
             "sample": "%d of the step's queries against the full database, Algorithm 3 scan in fp64 C, "
-                      "one query per thread" % m, "seconds": dt}
+                      "one query per thread" % m, "seconds": dt,
+            "single_thread_value": m1 / dt1, "single_thread_sample": "%d queries on one thread" % m1}
 
 
 class ClockSampler:
@@ -188,6 +202,33 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "power_w_max": max(pw) if pw else None, "reasons": sorted(reasons), "samples": len(win),
                 "window": note}
+
+
+def stage_rates(prof, a, steps, peaks, stats):
+    """Achieved rate of each timed stage against the derived fp32 ALU peak:
+    the piecewise-sum / LB_Keogh tile (4 ops per pair and index), the filter
+    (the work the roofline counts) and the DTW stages (3 ops per cell)."""
+    import torch
+
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    clock = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    alu_peak = sms * 128 * clock / 1e12
+    out = {}
+
+    def ms(stage):
+        return prof[stage]["ms"] / max(1, steps)
+
+    d = a.n // 8 if a.n >= 64 else a.n
+    if prof["lb_keogh"]["launches"]:
+        t = a.Q * a.N * d * 4.0 / 1e12 / (ms("lb_keogh") / 1e3)
+        out["lb_keogh_tile"] = {"ms": ms("lb_keogh"), "Top_s": t, "frac_alu": t / alu_peak}
+    if prof["dtw"]["launches"] and stats.get("dtw_cells"):
+        cells = stats["dtw_cells"] / (ms("dtw") / 1e3)
+        out["dtw"] = {"ms": ms("dtw"), "cells_per_s": cells, "frac_alu": cells * 3 / 1e12 / alu_peak}
+    if prof["seed_dtw"]["launches"] and stats.get("seed_cells"):
+        cells = stats["seed_cells"] / (ms("seed_dtw") / 1e3)
+        out["seed_dtw"] = {"ms": ms("seed_dtw"), "cells_per_s": cells, "frac_alu": cells * 3 / 1e12 / alu_peak}
+    return out
 
 
 def roofline(prof, a, steps, peaks, stats):
@@ -385,6 +426,7 @@ def run_ours(a):
         "config": workload_config(a, world), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": launches, "clocks": clocks, "p2": p2, "pruning": pruning,
         "stages_ms_per_step": {k: v["ms"] / a.steps for k, v in prof.items()},
+        "stage_rates": stage_rates(prof, a, a.steps, peaks, st_main),
         "stats_per_step": st_main,
     }
     return out
