@@ -45,7 +45,7 @@ METRIC = "exact 1-NN DTW queries/s (LB_Improved cascade)"
 # DRAM bytes per launch of the filter kernel at the default workload, from one
 # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum); valid for that
 # workload and the kernel as captured (profiles/k_lbi_filter_traffic_*.md)
-FILTER_TRAFFIC = {"workload": (100_000, 256, 25, 1000), "bytes": 524.79e6,
+FILTER_TRAFFIC = {"workload": (100_000, 256, 25, 1000), "bytes": 540.64e6,
                   "source": "profiles/k_lbi_filter_traffic_rw100k_n256_w25_q1000.md"}
 L2_BYTES = 129 * 2**20
 
@@ -275,7 +275,8 @@ def roofline(prof, a, steps, peaks, stats):
         return {"kernel": "k_lbi_filter", "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Top/s",
                 "frac": (achieved / alu_peak) if achieved else None, "traffic": traffic,
                 "traffic_note": ("DRAM bytes per launch, %s; algorithmic bytes 502.4 MB (bound matrix 400 MB + "
-                                 "database 102.4 MB)" % FILTER_TRAFFIC["source"]) if traffic else None,
+                                 "database 102.4 MB) plus the survivor list" % FILTER_TRAFFIC["source"])
+                if traffic else None,
                 "hbm_gbs": (traffic / 1e9 / (ms / 1e3)) if traffic else None, "ms_per_launch": ms,
                 "lb_keogh_pairs": pd_surv, "lb_improved_pairs": lbk_surv, "stage_share": share,
                 "peak_note": "%d SMs x 128 fp32 lanes x %.0f MHz (max SM clock)" % (sms, clock / 1e6)}
