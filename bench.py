@@ -63,9 +63,12 @@ def parse():
     ap.add_argument("--k", type=int, default=1)
     ap.add_argument("--p", type=int, default=1)
     ap.add_argument("--seed", type=int, default=2)
+    ap.add_argument("--data", choices=["random_walk", "shapes"], default="random_walk",
+                    help="retrieval: database and query generator (shapes: z-normalised shape-like series)")
     ap.add_argument("--seeds", type=int, default=0, help="seed DTWs per query (0: library default)")
     ap.add_argument("--parts", type=int, default=0, help="piecewise-sum parts (0: default n/8, -1: off)")
-    ap.add_argument("--dtw-path", type=int, default=0, help="DTW kernel: 0 auto, 1 thread per pair, 2 warp per pair")
+    ap.add_argument("--dtw-path", type=int, default=0, help="DTW kernel: 0 auto, 1 thread per pair, 2 warp per pair, "
+                    "3 main stage on two 16-lane groups per warp")
     ap.add_argument("--no-p2", action="store_true", help="skip the DTW_2 side measurement")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU baseline sample")
     ap.add_argument("--workload", choices=["retrieval", "batched", "serve", "triangle"], default="retrieval",
@@ -85,12 +88,25 @@ def parse():
     return ap.parse_args()
 
 
+DATA = {  # workload label, short description, description for the config
+    "random_walk": ("random-walk", "seeded random walks", "seeded synthetic random walks (fp32)"),
+    "shapes": ("shape-like", "seeded shape-like series",
+               "seeded synthetic shape-like series (plateaus, ramps, sinusoid sums; noise, time shift, "
+               "z-normalised; fp32)"),
+}
+
+
+def make_series(a, count, stream):
+    gen = synth.shapes if a.data == "shapes" else synth.random_walks
+    return gen(count, a.n, seed=a.seed, stream=stream)
+
+
 def workload_config(a, world):
     return {
-        "workload": "random-walk 1-NN retrieval: N=%d series, n=%d, w=%d, %d queries/step/GPU, DTW_%d, k=%d"
-        % (a.N, a.n, a.w, a.Q, a.p, a.k),
+        "workload": "%s %d-NN retrieval: N=%d series, n=%d, w=%d, %d queries/step/GPU, DTW_%d"
+        % (DATA[a.data][0], a.k, a.N, a.n, a.w, a.Q, a.p),
         "N": a.N, "n": a.n, "w": a.w, "queries_per_step_per_gpu": a.Q, "p": a.p, "k": a.k,
-        "data": "seeded synthetic random walks (fp32)", "seed": a.seed,
+        "data": DATA[a.data][2], "seed": a.seed,
         "l2": "flushed between timed steps (256 MiB write)",
         "parallelism": "queries sharded over %d GPU(s), database replicated" % world,
     }
@@ -257,7 +273,10 @@ def roofline(prof, a, steps, peaks, stats):
         cells = stats.get("dtw_cells" if dom == "dtw" else "seed_cells", 0)
         work = cells * 3.0 / 1e12  # 3 ops per cell: subtraction, 3-input min, add/fma
         achieved = work / (ms / 1e3) if cells else None
-        return {"kernel": "k_dtw_reg", "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Top/s",
+        band = 2 * a.w + 1
+        lanes = a.dtw_path == 2 or (a.dtw_path == 0 and band > 208)
+        name = "k_dtw_lanes" if lanes else ("k_dtw_reg4" if band <= 64 else "k_dtw_reg")
+        return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Top/s",
                 "frac": (achieved / alu_peak) if achieved else None, "traffic": None, "ms_per_launch": ms,
                 "cells_per_launch": cells, "stage_share": share,
                 "peak_note": "%d SMs x 128 fp32 lanes x %.0f MHz (max SM clock)" % (sms, clock / 1e6)}
@@ -271,7 +290,8 @@ def roofline(prof, a, steps, peaks, stats):
         lbk_surv = pd_surv - stats.get("pruned_keogh", 0)
         ops = scanned * 1.0 + pd_surv * a.n * 4.0 + lbk_surv * a.n * 7.0
         achieved = ops / 1e12 / (ms / 1e3) if scanned > 0 else None
-        traffic = FILTER_TRAFFIC["bytes"] if (a.N, a.n, a.w, a.Q) == FILTER_TRAFFIC["workload"] else None
+        same = (a.N, a.n, a.w, a.Q) == FILTER_TRAFFIC["workload"] and a.data == "random_walk"
+        traffic = FILTER_TRAFFIC["bytes"] if same else None
         return {"kernel": "k_lbi_filter", "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Top/s",
                 "frac": (achieved / alu_peak) if achieved else None, "traffic": traffic,
                 "traffic_note": ("DRAM bytes per launch, %s; algorithmic bytes 502.4 MB (bound matrix 400 MB + "
@@ -305,8 +325,8 @@ def run_ours(a):
     from paper_0811_3301_gb300 import _native as N
     from paper_0811_3301_gb300 import api
 
-    db_h = synth.random_walks(a.N, a.n, seed=a.seed)
-    q_h = synth.random_walks(a.Q, a.n, seed=a.seed, stream=synth.STREAM_QUERY + 16 * rank)
+    db_h = make_series(a, a.N, synth.STREAM_DB)
+    q_h = make_series(a, a.Q, synth.STREAM_QUERY + 16 * rank)
     db = torch.from_numpy(db_h).to(dev)
     qs = torch.from_numpy(q_h).to(dev)
     flush = torch.empty(256 * 2**20 // 4, dtype=torch.float32, device=dev)
@@ -423,7 +443,7 @@ def run_ours(a):
     out = {
         "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded random walks)",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (%s)" % DATA[a.data][1],
         "config": workload_config(a, world), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": launches, "clocks": clocks, "p2": p2, "pruning": pruning,
         "stages_ms_per_step": {k: v["ms"] / a.steps for k, v in prof.items()},
@@ -715,8 +735,8 @@ def run_reference(a):
     import oracle
 
     oracle.build()
-    db_h = synth.random_walks(a.N, a.n, seed=a.seed)
-    q_h = synth.random_walks(a.Q, a.n, seed=a.seed, stream=synth.STREAM_QUERY)
+    db_h = make_series(a, a.N, synth.STREAM_DB)
+    q_h = make_series(a, a.Q, synth.STREAM_QUERY)
     cores, model = cpu_info()
     budget = max(2.0, 120.0 / max(1, a.warmup + a.steps))  # whole run within a few minutes
     per_step = []
@@ -730,7 +750,7 @@ def run_reference(a):
     return {
         "impl": "reference", "metric": METRIC, "value": v, "unit": "queries/s", "n_gpus": world,
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * a.Q / v, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded random walks)",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (%s)" % DATA[a.data][1],
         "config": workload_config(a, world),
         "cpu_baseline": {"value": v, "unit": "queries/s", "cores": cores, "cpu": model, "kind": "oracle",
                          "sample": base["sample"] + "; each step a bounded sample of the 1,000-query batch"},

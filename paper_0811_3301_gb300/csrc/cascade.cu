@@ -140,11 +140,14 @@ __global__ void __launch_bounds__(256) k_finalize(CascadeBufs b) {
         }
         if (b.nseg > 0) {
             const int cnt = b.qcount[q];
+            const int lead = b.order_first > 0 ? (cnt < b.order_first ? cnt : b.order_first) : cnt;
             const int64_t base = b.qstart[q];
+            const int64_t base_b = b.order_first > 0 ? b.qstart_b[q] - lead : 0;
             for (int e = t; e < cnt; e += blockDim.x) {
-                float d = b.pair_res[base + e];
+                const int64_t at = e < lead ? base + e : base_b + e;
+                float d = b.pair_res[at];
                 if (d < kInf && d <= bq) {
-                    unsigned long long v = pack_key(d, b.pairs[base + e].c);
+                    unsigned long long v = pack_key(d, b.pairs[at].c);
                     if ((first || v > last) && v < m) m = v;
                 }
             }
@@ -191,21 +194,32 @@ cudaError_t launch_finalize(const CascadeBufs &b, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------------------
-// Group the filter's survivors by query (a counting sort): an exclusive scan
-// of the per-query counts gives each query a contiguous range, and one CTA
-// per query copies its sub-segments into it in order.  The DTW stage then
-// sees runs of pairs that share a query (warp-uniform band-window loads).
+// Group the filter's survivors by query (a counting sort): exclusive scans of
+// the per-query counts give each query its output ranges, and one CTA per
+// query moves its sub-segments there.  The DTW stage then sees runs of pairs
+// that share a query (warp-uniform band-window loads).
+//
+// With order_first = F > 0 the CTA also orders its query's pairs by bound:
+// bin = floor(256 * bound / threshold), a histogram and its scan give each
+// pair a rank, and rank r goes to the leading region (r < F) or to the
+// query's range after it.  The leading region holds every query's F
+// lowest-bound pairs, so the DTW stage computes the likeliest neighbours of
+// all queries before anything else.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_qscan(const int32_t *__restrict__ cnt, int32_t *__restrict__ start, int Q,
-                                                unsigned long long *total) {
+constexpr int kOrderBins = 256;
+
+// Exclusive scan over Q of f(cnt[i]) into out[i] + base, one CTA; returns the total.
+template <typename F>
+__device__ int32_t block_scan_counts(const int32_t *__restrict__ cnt, int32_t *__restrict__ out, int Q, int32_t base,
+                                     F f) {
     __shared__ int32_t wsum[32];
     __shared__ int32_t carry;
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
-    if (t == 0) carry = 0;
+    if (t == 0) carry = base;
     __syncthreads();
-    for (int base = 0; base < Q; base += blockDim.x) {
-        const int i = base + t;
-        const int v = i < Q ? cnt[i] : 0;
+    for (int b0 = 0; b0 < Q; b0 += blockDim.x) {
+        const int i = b0 + t;
+        const int v = i < Q ? f(cnt[i]) : 0;
         int x = v;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -225,12 +239,33 @@ __global__ void __launch_bounds__(1024) k_qscan(const int32_t *__restrict__ cnt,
         }
         __syncthreads();
         const int before = (wid > 0 ? wsum[wid - 1] : 0) + carry;
-        if (i < Q) start[i] = before + x - v;
+        if (i < Q) out[i] = before + x - v;
         __syncthreads();
         if (t == blockDim.x - 1) carry = before + x;
         __syncthreads();
     }
-    if (t == 0 && total) *total = (unsigned long long)carry;
+    const int32_t total = carry;
+    __syncthreads();
+    return total;
+}
+
+__global__ void __launch_bounds__(1024) k_qscan(const int32_t *__restrict__ cnt, int32_t *__restrict__ start,
+                                                int32_t *__restrict__ start_b, int Q, int first,
+                                                unsigned long long *total) {
+    if (first <= 0) {
+        const int32_t all = block_scan_counts(cnt, start, Q, 0, [](int32_t c) { return c; });
+        if (threadIdx.x == 0 && total) *total = (unsigned long long)all;
+        return;
+    }
+    const int32_t lead = block_scan_counts(cnt, start, Q, 0, [first](int32_t c) { return c < first ? c : first; });
+    const int32_t all =
+        block_scan_counts(cnt, start_b, Q, lead, [first](int32_t c) { return c > first ? c - first : 0; });
+    if (threadIdx.x == 0 && total) *total = (unsigned long long)all;
+}
+
+__device__ __forceinline__ int order_bin(float bound, float scale) {
+    const float r = bound * scale;
+    return r < (float)(kOrderBins - 1) ? (int)r : kOrderBins - 1;  // bound >= 0
 }
 
 __global__ void __launch_bounds__(256) k_gather(CascadeBufs b) {
@@ -238,9 +273,53 @@ __global__ void __launch_bounds__(256) k_gather(CascadeBufs b) {
     const int t = threadIdx.x;
     __shared__ int32_t offs[256];
     __shared__ int32_t carry;
+    const int64_t out0 = b.qstart[q];
+    const int F = b.order_first;
+    if (F > 0) {
+        __shared__ int32_t hist[kOrderBins];
+        const int64_t outb = b.qstart_b[q];
+        const int cq = b.qcount[q];
+        const int lead = cq < F ? cq : F;
+        const float thr = __uint_as_float(b.bsf[q]);
+        // bins relative to the threshold the filter used; without a finite
+        // positive threshold every pair shares bin 0
+        const float scale = (thr > 0.0f && thr < kInf) ? (float)kOrderBins / thr : 0.0f;
+        for (int i = t; i < kOrderBins; i += blockDim.x) hist[i] = 0;
+        __syncthreads();
+        for (int sg = t; sg < b.nseg; sg += blockDim.x) {
+            const int c = b.seg_count[(int64_t)q * b.nseg + sg];
+            const int64_t src = b.seg_start[(int64_t)q * b.nseg + sg];
+            for (int e = 0; e < c; ++e) atomicAdd(&hist[order_bin(b.lbi_u[src + e], scale)], 1);
+        }
+        __syncthreads();
+        // exclusive scan of the histogram (kOrderBins == blockDim.x)
+        const int h = hist[t];
+        offs[t] = h;
+        __syncthreads();
+        for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+            const int v = t >= o ? offs[t - o] : 0;
+            __syncthreads();
+            offs[t] += v;
+            __syncthreads();
+        }
+        hist[t] = offs[t] - h;
+        __syncthreads();
+        for (int sg = t; sg < b.nseg; sg += blockDim.x) {
+            const int c = b.seg_count[(int64_t)q * b.nseg + sg];
+            const int64_t src = b.seg_start[(int64_t)q * b.nseg + sg];
+            for (int e = 0; e < c; ++e) {
+                const float lb = b.lbi_u[src + e];
+                const int r = atomicAdd(&hist[order_bin(lb, scale)], 1);
+                const int64_t dst = r < lead ? out0 + r : outb + (r - lead);
+                b.pairs[dst] = b.pairs_u[src + e];
+                b.pair_lbi[dst] = lb;
+                b.pair_res[dst] = kInf;
+            }
+        }
+        return;
+    }
     if (t == 0) carry = 0;
     __syncthreads();
-    const int64_t out0 = b.qstart[q];
     for (int s0 = 0; s0 < b.nseg; s0 += blockDim.x) {
         const int sg = s0 + t;
         const int c = sg < b.nseg ? b.seg_count[(int64_t)q * b.nseg + sg] : 0;
@@ -271,7 +350,8 @@ __global__ void __launch_bounds__(256) k_gather(CascadeBufs b) {
 
 cudaError_t launch_group_by_query(const CascadeBufs &b, cudaStream_t s) {
     if (b.Q <= 0 || b.nseg <= 0) return cudaSuccess;
-    k_qscan<<<1, 1024, 0, s>>>(b.qcount, b.qstart, b.Q, b.pair_total);
+    static_assert(kOrderBins == 256, "k_gather scans the histogram with one thread per bin");
+    k_qscan<<<1, 1024, 0, s>>>(b.qcount, b.qstart, b.qstart_b, b.Q, b.order_first, b.pair_total);
     k_gather<<<b.Q, 256, 0, s>>>(b);
     return cudaGetLastError();
 }

@@ -148,6 +148,12 @@ CascadePlan make_plan(int64_t N, int64_t Qmax, int n, int w, int p, int k, const
     // up to 256 (chunks in registers) 2048 measured fastest, 1024 otherwise
     pl.seg_len = seg_len > 0 ? seg_len : (n <= 256 ? 2048 : 1024);
     pl.dtw_path = o.dtw_path;
+    // The DTW stage takes every query's lowest-bound pairs first (a multiple
+    // of 32, at least 2k), so that each query's threshold falls to near its
+    // final value early and its remaining pairs are skipped or abandoned
+    // sooner.  The order changes which non-neighbours are computed, never
+    // the result.
+    pl.order_first = pl.mode == DTW_MODE_NOPRUNE ? 0 : 32 * ((k + 15) / 16);
     pl.filter_warps = lbi_filter_warps(n, pl.we, std::max(pl.S, 1), pl.seg_len, p, filter_warps);
     const int64_t nsegs = N > 0 ? (N + pl.seg_len - 1) / pl.seg_len : 1;
     pl.nseg = (int)nsegs * pl.filter_warps;
@@ -179,6 +185,7 @@ CascadeWs carve_ws(const CascadePlan &pl, Carve &cv) {
     l.lbi_u = cv.take<float>((size_t)Qc * Nc);
     l.qcount = cv.take<int32_t>((size_t)Qc);
     l.qstart = cv.take<int32_t>((size_t)Qc);
+    l.qstart_b = cv.take<int32_t>((size_t)Qc);
     l.pairs = cv.take<Pair>((size_t)Qc * Nc);
     l.pair_lbi = cv.take<float>((size_t)Qc * Nc);
     l.pair_res = cv.take<float>((size_t)Qc * Nc);
@@ -243,6 +250,8 @@ cudaError_t cascade_run(const CascadePlan &pl, const CascadeWs &l, const float *
     b.lbi_u = l.lbi_u;
     b.qcount = l.qcount;
     b.qstart = l.qstart;
+    b.qstart_b = l.qstart_b;
+    b.order_first = pl.order_first;
     b.pair_total = pair_total;
     b.lbi_inline = pl.mode == DTW_MODE_IMPROVED ? 1 : 0;
     b.summary = pl.summary ? 1 : 0;

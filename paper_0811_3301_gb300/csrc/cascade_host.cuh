@@ -39,6 +39,7 @@ struct CascadePlan {
     int nseg;        // sub-segments per query
     int seg_per_cta; // filter segments per CTA
     int dtw_path;    // 0 auto, 1 thread per pair, 2 warp per pair (main DTW stage)
+    int order_first; // pairs per query the DTW stage takes first, by ascending bound (0: filter order)
 };
 
 // Device buffers of one run, carved from a workspace.
@@ -47,7 +48,7 @@ struct CascadeWs {
     unsigned long long *tile_min, *misc;
     Pair *seed_pairs, *pairs_u, *pairs;
     uint32_t *gmin, *bsf;
-    int32_t *qcount, *qstart, *seg_start, *seg_count;
+    int32_t *qcount, *qstart, *qstart_b, *seg_start, *seg_count;
 };
 
 // o.parts: 0 = default (n/8 for n >= 64, else off), -1 = off, else d.

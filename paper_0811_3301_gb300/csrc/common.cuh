@@ -150,12 +150,18 @@ struct CascadeBufs {
     // survivors of the bound stages, as written by the filter (unordered) ...
     Pair *pairs_u;
     float *lbi_u;
-    // ... and grouped by query: query q owns [qstart[q], qstart[q] + qcount[q])
+    // ... and grouped by query.  With order_first = F > 0 each query's pairs
+    // are ordered by ascending bound (to 1/256 of its threshold) and split:
+    // its first min(F, qcount[q]) pairs at qstart[q] in a leading region that
+    // holds every query's first pairs, the rest at qstart_b[q] after it.  With
+    // F = 0 query q owns [qstart[q], qstart[q] + qcount[q]) in filter order.
     Pair *pairs;
     float *pair_lbi;
     float *pair_res;
     int32_t *qcount;      // [Q], zeroed before the filter
     int32_t *qstart;      // [Q]
+    int32_t *qstart_b;    // [Q], used when order_first > 0
+    int order_first;
     unsigned long long *pair_total;  // pairs after grouping
     int lbi_inline;       // the filter computes LB_Improved (warp per pair)
     int summary;          // the matrix holds the piecewise-sum bound; LB_Keogh is computed in the filter
