@@ -111,8 +111,12 @@ __device__ __forceinline__ void lanes_block(float (&DX)[CL], float (&DY)[CL], fl
     }
 }
 
+// Register budget: the steps are chains of dependent cells, so the kernel
+// lives on the number of warps in flight.  Up to 13 slots per lane fit 128
+// registers (16 warps per SM) and up to 20 fit 168 (12 warps) without
+// spilling; wider lanes keep what they need.
 template <int CL, int G, int P>
-__global__ void __launch_bounds__(kDtwThreads) k_dtw_lanes(DtwJob j) {
+__global__ void __launch_bounds__(kDtwThreads, (CL <= 13 ? 4 : (CL <= 20 ? 3 : 1))) k_dtw_lanes(DtwJob j) {
     static_assert(G == 16 || G == 32, "lane groups of 16 or 32");
     const int lane = threadIdx.x & 31;
     const int gl = lane & (G - 1);      // lane within the group
