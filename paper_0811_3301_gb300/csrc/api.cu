@@ -329,7 +329,7 @@ dtw_status knn_search_ex(const float *db, int64_t N, const float *queries, int64
     const int64_t Qc = pl.Qc;
 
     struct Extra {
-        float *db, *q, *PX, *out_dist;
+        float *db, *q, *PX, *XU, *XL, *out_dist;
         int64_t *out_idx;
         unsigned long long *counters, *xmax;
     };
@@ -337,6 +337,8 @@ dtw_status knn_search_ex(const float *db, int64_t N, const float *queries, int64
         x.db = db_dev ? nullptr : cv.take<float>((size_t)N * n);
         x.q = q_dev ? nullptr : cv.take<float>((size_t)Qc * n);
         x.PX = pl.summary ? cv.take<float>((size_t)N * pl.parts) : nullptr;
+        x.XU = plan_needs_db_envelope(pl) ? cv.take<float>((size_t)N * n) : nullptr;
+        x.XL = plan_needs_db_envelope(pl) ? cv.take<float>((size_t)N * n) : nullptr;
         x.counters = cv.take<unsigned long long>(2 * CNT_NUM);
         x.xmax = cv.take<unsigned long long>(1);
         x.out_idx = oi_dev ? nullptr : cv.take<int64_t>((size_t)Q * k);
@@ -366,6 +368,10 @@ dtw_status knn_search_ex(const float *db, int64_t N, const float *queries, int64
         CUDA_TRY(cudaMemsetAsync(xmax_bits, 0, sizeof(unsigned long long), s));
         CUDA_TRY(launch_summarize(dbd, N, n, pl.parts, x.PX, xmax_bits, s));
     }
+    if (plan_needs_db_envelope(pl)) {
+        // the database rows' envelopes, once per call (LB_Improved's second sum)
+        CUDA_TRY(launch_envelope(dbd, N, n, pl.we, x.XU, x.XL, QueryCopies{}, 0, s));
+    }
     for (int64_t q0 = 0; q0 < Q; q0 += Qc) {
         const int qn = (int)((Q - q0) < Qc ? (Q - q0) : Qc);
         const float *qd;
@@ -376,7 +382,8 @@ dtw_status knn_search_ex(const float *db, int64_t N, const float *queries, int64
                                      cudaMemcpyHostToDevice, s));
             qd = x.q;
         }
-        CUDA_TRY(cascade_run(pl, ws, dbd, x.PX, xmax_bits, qd, qn, oidx + q0 * k, odist + q0 * k, x.counters, s));
+        CUDA_TRY(cascade_run(pl, ws, dbd, x.PX, xmax_bits, x.XU, x.XL, qd, qn, oidx + q0 * k, odist + q0 * k,
+                             x.counters, s));
     }
     if (!oi_dev)
         CUDA_TRY(cudaMemcpyAsync(out_idx, x.out_idx, (size_t)Q * k * sizeof(int64_t), cudaMemcpyDeviceToHost, s));

@@ -172,6 +172,8 @@ CascadeWs carve_ws(const CascadePlan &pl, Carve &cv) {
     const int n = pl.n;
     l.U = cv.take<float>((size_t)Qc * n);
     l.L = cv.take<float>((size_t)Qc * n);
+    l.UL = plan_needs_db_envelope(pl) ? cv.take<float>((size_t)Qc * n) : nullptr;
+    l.LU = plan_needs_db_envelope(pl) ? cv.take<float>((size_t)Qc * n) : nullptr;
     l.copies = cv.take<float>((size_t)Qc * 4 * pl.g.ylen);
     l.lb = cv.take<float>((size_t)Qc * Nc);
     l.PU = pl.summary ? cv.take<float>((size_t)Qc * pl.parts) : nullptr;
@@ -205,8 +207,9 @@ size_t cascade_ws_bytes(const CascadePlan &pl) {
 // one run over qn <= Qc queries
 // ---------------------------------------------------------------------------
 cudaError_t cascade_run(const CascadePlan &pl, const CascadeWs &l, const float *db, const float *PX,
-                        const unsigned *xmax_bits, const float *q, int qn, int64_t *out_idx, float *out_dist,
-                        unsigned long long *counters, cudaStream_t s) {
+                        const unsigned *xmax_bits, const float *XU, const float *XL, const float *q, int qn,
+                        int64_t *out_idx, float *out_dist, unsigned long long *counters, cudaStream_t s) {
+    if (plan_needs_db_envelope(pl) && (XU == nullptr || XL == nullptr)) return cudaErrorInvalidValue;
     const int n = pl.n, we = pl.we, p = pl.p, k = pl.k;
     const int64_t N = pl.N;
     const int64_t Nc = N > 0 ? N : 1;
@@ -222,13 +225,17 @@ cudaError_t cascade_run(const CascadePlan &pl, const CascadeWs &l, const float *
     qc.ylen = pl.g.ylen;
     {
         StageTimer tm(DTW_STAGE_ENVELOPE, s);
-        RUN_TRY(launch_envelope(q, qn, n, we, l.U, l.L, qc, pl.g.padl, s));
+        RUN_TRY(launch_envelope(q, qn, n, we, l.U, l.L, qc, pl.g.padl, s, l.UL, l.LU));
     }
     CascadeBufs b{};
     b.db = db;
     b.queries = q;
     b.U = l.U;
     b.L = l.L;
+    b.UL = l.UL;
+    b.LU = l.LU;
+    b.XU = XU;
+    b.XL = XL;
     b.qc = qc;
     b.N = (int)N;
     b.Q = qn;

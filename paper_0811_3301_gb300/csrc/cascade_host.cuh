@@ -44,7 +44,7 @@ struct CascadePlan {
 
 // Device buffers of one run, carved from a workspace.
 struct CascadeWs {
-    float *U, *L, *copies, *lb, *PU, *PL, *seed_res, *lbi_u, *pair_lbi, *pair_res;
+    float *U, *L, *UL, *LU, *copies, *lb, *PU, *PL, *seed_res, *lbi_u, *pair_lbi, *pair_res;
     unsigned long long *tile_min, *misc;
     Pair *seed_pairs, *pairs_u, *pairs;
     uint32_t *gmin, *bsf;
@@ -61,12 +61,16 @@ size_t cascade_ws_bytes(const CascadePlan &pl);
 
 // One run over qn <= pl.Qc queries q [qn][n] (device).  PX [N][parts] and
 // xmax_bits are the database part sums and max |x| (launch_summarize), used
-// when pl.summary.  counters: 2 * CNT_NUM device counters (run counters, then
+// when pl.summary; XU, XL [N][n] the database rows' envelopes for band pl.we
+// (launch_envelope), used when pl.mode is DTW_MODE_IMPROVED.  counters: 2 * CNT_NUM device counters (run counters, then
 // seed-stage counters), accumulated, zeroed by the caller.  Outputs
 // out_idx/out_dist [qn][k] (device).  Asynchronous on s; allocates nothing.
 cudaError_t cascade_run(const CascadePlan &pl, const CascadeWs &ws, const float *db, const float *PX,
-                        const unsigned *xmax_bits, const float *q, int qn, int64_t *out_idx, float *out_dist,
-                        unsigned long long *counters, cudaStream_t s);
+                        const unsigned *xmax_bits, const float *XU, const float *XL, const float *q, int qn,
+                        int64_t *out_idx, float *out_dist, unsigned long long *counters, cudaStream_t s);
+
+// Whether a run under pl reads the database envelopes XU, XL.
+inline bool plan_needs_db_envelope(const CascadePlan &pl) { return pl.N > 0 && pl.mode == DTW_MODE_IMPROVED; }
 
 // Adds the statistics of Q queries run under pl, from the host copy of the
 // 2 * CNT_NUM counters, to st.

@@ -87,8 +87,11 @@ struct QueryCopies {
 // ---------------------------------------------------------------------------
 // Launchers (all asynchronous on `s`; they return cudaGetLastError()).
 // ---------------------------------------------------------------------------
+// U, L of count series (and, with UL/LU, the second-order envelopes
+// UL = U(L), LU = L(U)); qc.data: optional shifted copies.
 cudaError_t launch_envelope(const float *y, int64_t count, int n, int w, float *U, float *L,
-                            QueryCopies qc, int copies_padl, cudaStream_t s);
+                            QueryCopies qc, int copies_padl, cudaStream_t s, float *UL = nullptr,
+                            float *LU = nullptr);
 
 cudaError_t launch_lbk_single(const float *cand, int64_t N, const float *U, const float *L, int n,
                               int p, float *out, cudaStream_t s);
@@ -133,6 +136,8 @@ struct CascadeBufs {
     const float *db;        // [N][n]
     const float *queries;   // [Q][n]
     const float *U, *L;     // [Q][n]
+    const float *UL, *LU;   // [Q][n] U(L) and L(U), for LB_Improved's second sum
+    const float *XU, *XL;   // [N][n] the candidates' own envelopes (same band)
     QueryCopies qc;
     int N, Q, n, w, p, k, mode;
     float slack;

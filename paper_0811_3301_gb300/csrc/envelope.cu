@@ -10,7 +10,9 @@
 // bit-identical to the definition.
 //
 // The same kernel optionally writes the four shifted, +INF-padded copies of
-// each series that the DTW kernels read their band windows from.
+// each series that the DTW kernels read their band windows from, and the
+// second-order envelopes U(L(y)) and L(U(y)) that LB_Improved's second sum
+// takes for the query (Sec. 8; see the filter in lb.cu).
 #include "common.cuh"
 
 namespace dtwk {
@@ -19,29 +21,11 @@ constexpr int kEnvThreads = 256;
 
 __device__ __forceinline__ int floor_log2(int v) { return 31 - __clz(v); }
 
-__global__ void __launch_bounds__(kEnvThreads)
-k_envelope(const float *__restrict__ y, int n, int w, float *__restrict__ U, float *__restrict__ L,
-           float *__restrict__ copies, int padl, int ylen) {
-    extern __shared__ float sm[];
-    float *ax = sm;          // level j max
-    float *an = sm + n;      // level j min
-    float *bx = sm + 2 * n;  // level j-1 max (after the loop)
-    float *bn = sm + 3 * n;  // level j-1 min
-    const int64_t row = blockIdx.x;
-    const float *yr = y + row * (int64_t)n;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        float v = yr[i];
-        ax[i] = v;
-        an[i] = v;
-    }
-    if (copies != nullptr) {
-        float *cr = copies + row * 4 * (int64_t)ylen;
-        for (int t = threadIdx.x; t < 4 * ylen; t += blockDim.x) {
-            int r = t / ylen, tt = t - r * ylen;
-            int j = tt + r - padl;
-            cr[t] = (j >= 0 && j < n) ? yr[j] : kInf;
-        }
-    }
+// Max table over amax[0..n) and min table over amin[0..n) (both in shared
+// memory, ax/an on entry), then U_i = max over the clipped window of i from
+// the first and L_i = min from the second.  Ends with a barrier.
+__device__ void envelope_windows(float *ax, float *an, float *bx, float *bn, int n, int w, float *__restrict__ Ur,
+                                 float *__restrict__ Lr) {
     __syncthreads();
     const int len_max = min(2 * w + 1, n);
     const int kmax = floor_log2(len_max);
@@ -58,8 +42,6 @@ k_envelope(const float *__restrict__ y, int n, int w, float *__restrict__ U, flo
         t = an; an = bn; bn = t;
     }
     // now ax/an = T_kmax and bx/bn = T_(kmax-1) (unused when kmax == 0)
-    float *Ur = U + row * (int64_t)n;
-    float *Lr = L + row * (int64_t)n;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         int a = max(0, i - w), b = min(n - 1, i + w);
         int k = floor_log2(b - a + 1);
@@ -69,11 +51,46 @@ k_envelope(const float *__restrict__ y, int n, int w, float *__restrict__ U, flo
         Ur[i] = fmaxf(tx[a], tx[b2]);
         Lr[i] = fminf(tn[a], tn[b2]);
     }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kEnvThreads)
+k_envelope(const float *__restrict__ y, int n, int w, float *__restrict__ U, float *__restrict__ L,
+           float *__restrict__ UL, float *__restrict__ LU, float *__restrict__ copies, int padl, int ylen) {
+    extern __shared__ float sm[];
+    float *ax = sm, *an = sm + n, *bx = sm + 2 * n, *bn = sm + 3 * n;
+    const int64_t row = blockIdx.x;
+    const float *yr = y + row * (int64_t)n;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        float v = yr[i];
+        ax[i] = v;
+        an[i] = v;
+    }
+    if (copies != nullptr) {
+        float *cr = copies + row * 4 * (int64_t)ylen;
+        for (int t = threadIdx.x; t < 4 * ylen; t += blockDim.x) {
+            int r = t / ylen, tt = t - r * ylen;
+            int j = tt + r - padl;
+            cr[t] = (j >= 0 && j < n) ? yr[j] : kInf;
+        }
+    }
+    float *Ur = U + row * (int64_t)n;
+    float *Lr = L + row * (int64_t)n;
+    envelope_windows(ax, an, bx, bn, n, w, Ur, Lr);
+    if (UL == nullptr) return;
+    // second order: the max table over L(y) and the min table over U(y)
+    // (written above by this block, visible after the barrier)
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        ax[i] = Lr[i];
+        an[i] = Ur[i];
+    }
+    envelope_windows(ax, an, bx, bn, n, w, UL + row * (int64_t)n, LU + row * (int64_t)n);
 }
 
 cudaError_t launch_envelope(const float *y, int64_t count, int n, int w, float *U, float *L,
-                            QueryCopies qc, int copies_padl, cudaStream_t s) {
+                            QueryCopies qc, int copies_padl, cudaStream_t s, float *UL, float *LU) {
     if (count <= 0) return cudaSuccess;
+    if ((UL == nullptr) != (LU == nullptr)) return cudaErrorInvalidValue;
     w = min(w, n - 1);
     size_t smem = 4 * (size_t)n * sizeof(float);
     static bool attr_set = false;
@@ -82,7 +99,7 @@ cudaError_t launch_envelope(const float *y, int64_t count, int n, int w, float *
                              4 * DTW_MAX_N * (int)sizeof(float));
         attr_set = true;
     }
-    k_envelope<<<(unsigned)count, kEnvThreads, smem, s>>>(y, n, w, U, L, qc.data, copies_padl,
+    k_envelope<<<(unsigned)count, kEnvThreads, smem, s>>>(y, n, w, U, L, UL, LU, qc.data, copies_padl,
                                                           qc.ylen);
     return cudaGetLastError();
 }

@@ -197,6 +197,36 @@ dtw_status ensure_sums(dtw_index *ix, int b, int parts, const PartSums **out) {
     return DTW_OK;
 }
 
+// Envelopes of bucket b's rows for band w (computed on first use,
+// synchronously; w already clamped to n - 1).
+dtw_status ensure_env(dtw_index *ix, int b, int w, const DbEnvelope **out) {
+    Bucket &bk = ix->buckets[b];
+    for (const auto &ev : bk.envs)
+        if (ev.w == w) {
+            *out = &ev;
+            return DTW_OK;
+        }
+    DbEnvelope ev{};
+    ev.w = w;
+    const size_t row_bytes = ((size_t)bk.N * bk.n * sizeof(float) + 255) & ~size_t(255);
+    cudaError_t e = cudaMalloc(&ev.XU, 2 * row_bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return ix_fail(DTW_ERR_OOM, "envelopes of %lld x %d: %s", (long long)bk.N, bk.n, cudaGetErrorString(e));
+    }
+    ev.XL = reinterpret_cast<float *>(reinterpret_cast<char *>(ev.XU) + row_bytes);
+    cudaStream_t s = ix->slot.origin;
+    e = launch_envelope(bk.db, bk.N, bk.n, w, ev.XU, ev.XL, QueryCopies{}, 0, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        cudaFree(ev.XU);
+        return ix_fail(DTW_ERR_CUDA, "bucket envelopes: %s", cudaGetErrorString(e));
+    }
+    bk.envs.push_back(ev);
+    *out = &bk.envs.back();
+    return DTW_OK;
+}
+
 Tuning tuning_for(const dtw_index *ix, int n, int w, int k) {
     auto it = ix->tuned.find(TuneKey{n, w, k});
     if (it != ix->tuned.end()) return it->second;
@@ -322,11 +352,21 @@ dtw_status prepare_batch(dtw_index *ix, int64_t Q, const int32_t *q_len, const i
     return DTW_OK;
 }
 
-// Part sums of every group that uses the pre-filter (outside any capture).
+// Part sums of every group that uses the pre-filter, and the row envelopes
+// of every group that computes LB_Improved (outside any capture).
 dtw_status bind_sums(dtw_index *ix, Batch &bt) {
     for (auto &gr : bt.groups) {
         gr.PX = nullptr;
         gr.xmax = nullptr;
+        gr.XU = nullptr;
+        gr.XL = nullptr;
+        if (plan_needs_db_envelope(gr.pl)) {
+            const DbEnvelope *ev = nullptr;
+            dtw_status st = ensure_env(ix, gr.bucket, gr.pl.we, &ev);
+            if (st != DTW_OK) return st;
+            gr.XU = ev->XU;
+            gr.XL = ev->XL;
+        }
         if (gr.pl.summary) {
             const PartSums *ps = nullptr;
             dtw_status st = ensure_sums(ix, gr.bucket, gr.pl.parts, &ps);
@@ -379,8 +419,8 @@ static cudaError_t enqueue_batch(dtw_index *ix, Slot &sl, const Batch &bt, const
         const int64_t step = per_query ? 1 : gr.pl.Qc;
         for (int64_t q0 = 0; q0 < gr.qn; q0 += step) {
             const int qn = (int)std::min<int64_t>(step, gr.qn - q0);
-            e = cascade_run(gr.pl, L.ws[g], bk.db, gr.PX, gr.xmax, L.grouped + gr.qoff + q0 * bk.n, qn,
-                            L.gidx + gr.ooff + q0 * gr.k, L.gdist + gr.ooff + q0 * gr.k, cnt, gs);
+            e = cascade_run(gr.pl, L.ws[g], bk.db, gr.PX, gr.xmax, gr.XU, gr.XL, L.grouped + gr.qoff + q0 * bk.n,
+                            qn, L.gidx + gr.ooff + q0 * gr.k, L.gdist + gr.ooff + q0 * gr.k, cnt, gs);
             if (e != cudaSuccess) return e;
         }
     }
@@ -556,6 +596,14 @@ dtw_status tune_group(dtw_index *ix, int b, int w, int k, const float *qdev, int
             PX = ps->PX;
             xm = reinterpret_cast<const unsigned *>(ps->xmax);
         }
+        const float *XU = nullptr, *XL = nullptr;
+        if (plan_needs_db_envelope(pl)) {
+            const DbEnvelope *ev = nullptr;
+            dtw_status s2 = ensure_env(ix, b, pl.we, &ev);
+            if (s2 != DTW_OK) return s2;
+            XU = ev->XU;
+            XL = ev->XL;
+        }
         Carve c2;
         c2.base = buf + head;
         const CascadeWs ws = carve_ws(pl, c2);
@@ -564,7 +612,8 @@ dtw_status tune_group(dtw_index *ix, int b, int w, int k, const float *qdev, int
             IX_TRY(cudaEventRecord(e0, s));
             for (int64_t q0 = 0; q0 < qn; q0 += pl.Qc) {
                 const int m = (int)std::min<int64_t>(pl.Qc, qn - q0);
-                IX_TRY(cascade_run(pl, ws, bk.db, PX, xm, qdev + q0 * n, m, oidx + q0 * k, odist + q0 * k, cnt, s));
+                IX_TRY(cascade_run(pl, ws, bk.db, PX, xm, XU, XL, qdev + q0 * n, m, oidx + q0 * k, odist + q0 * k,
+                                   cnt, s));
             }
             IX_TRY(cudaEventRecord(e1, s));
             IX_TRY(cudaEventSynchronize(e1));
@@ -736,6 +785,12 @@ dtw_status dtw_index_add_bucket(dtw_index *ix, const float *db, int64_t N, int32
         dtw_status st = ensure_sums(ix, (int)ix->buckets.size() - 1, parts, &ps);
         if (st != DTW_OK) return st;
     }
+    // row envelopes for the usual band w = floor(n / 10)
+    if (ix->opt.mode == DTW_MODE_IMPROVED) {
+        const DbEnvelope *ev = nullptr;
+        dtw_status st = ensure_env(ix, (int)ix->buckets.size() - 1, std::min(n / 10, n - 1), &ev);
+        if (st != DTW_OK) return st;
+    }
     return DTW_OK;
 }
 
@@ -865,6 +920,7 @@ dtw_status dtw_index_destroy(dtw_index *ix) {
         slot_release(ix->slot);
         for (auto &bk : ix->buckets) {
             for (auto &ps : bk.sums) cudaFree(ps.PX);
+            for (auto &ev : bk.envs) cudaFree(ev.XU);
             cudaFree(bk.db);
         }
         ix->buckets.clear();

@@ -49,11 +49,19 @@ struct PartSums {
     unsigned long long *xmax;  // max |x| over the bucket (float bits in the low word)
 };
 
+// Envelopes of a bucket's rows for one band (LB_Improved's second sum).
+struct DbEnvelope {
+    int w;
+    float *XU;  // [N][n], owns the allocation (XL follows it)
+    float *XL;  // [N][n]
+};
+
 struct Bucket {
     int n;
     int64_t N;
     float *db;  // [N][n], owned
     std::vector<PartSums> sums;
+    std::vector<DbEnvelope> envs;
 };
 
 struct TuneKey {
@@ -83,6 +91,7 @@ struct GroupRun {
     int stream;    // pool stream index
     const float *PX;
     const unsigned *xmax;
+    const float *XU, *XL;
 };
 
 struct Batch {
@@ -122,6 +131,7 @@ namespace dtwk {
 
 int find_bucket(const dtw_index *ix, int n);
 dtw_status ensure_sums(dtw_index *ix, int b, int parts, const PartSums **out);
+dtw_status ensure_env(dtw_index *ix, int b, int w, const DbEnvelope **out);
 Tuning tuning_for(const dtw_index *ix, int n, int w, int k);
 CascadePlan plan_for(const dtw_index *ix, int b, int w, int k, int64_t qmax, const Tuning &t);
 dtw_status prepare_batch(dtw_index *ix, int64_t Q, const int32_t *q_len, const int32_t *q_w, const int32_t *q_k,

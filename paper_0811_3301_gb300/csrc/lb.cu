@@ -774,55 +774,157 @@ cudaError_t launch_lbi_single(const float *cand, int64_t N, const float *q, cons
 
 // ---------------------------------------------------------------------------
 // Cascade filter over one (query, candidate segment) per CTA:
-//   LB_Keogh test  lb[q][c] <= thr                      (Algorithm 3, first test)
-//   LB_Improved    lbi = LB_Improved^p <= thr            (second test)
+//   pre-filter / LB_Keogh test  lb[q][c] <= thr        (Algorithm 3, first test)
+//   LB_Improved                 LB_Improved^p <= thr   (second test)
 // with thr = b (1 + slack), b the query's current k-th best DTW^p.  Seeds
 // (already evaluated) are skipped.  Survivors are collected in shared memory
 // and written as one contiguous block of the pair list, whose start and
-// length are recorded per (query, segment).
+// length are recorded per (query, segment, warp).
+//
+// LB_Improved's second sum, sum_i d(y_i, [L(H)_i, U(H)_i])^p over the
+// envelope of the projection H = H(x, y) (Eq. 1), is evaluated as
+//
+//   sum_i d(y_i, [min(XL_i, LU_i), max(XU_i, UL_i)])^p
+//
+// with XU, XL the candidate's own envelope (computed once per database row)
+// and UL = U(L), LU = L(U) the envelopes of the query's envelope.  The two
+// are equal term by term.  H_j = min(max(x_j, L_j), U_j) <= max(x_j, L_j), so
+// U(H)_i <= max(XU_i, UL_i): where y_i <= U(H)_i both upper terms are 0.
+// Where y_i > U(H)_i, every j in the window of i has i in its own window, so
+// U_j >= y_i > U(H)_i >= H_j: no H_j in the window is clipped at U_j, and
+// U(H)_i = max_j max(x_j, L_j) = max(XU_i, UL_i).  The lower terms follow by
+// symmetry.  Min and max do not round, so each term is the one the
+// definition gives; only the order of the fp32 sums differs.  No projection,
+// no sliding window and no exchange between lanes remain: each lane adds
+// its own indices and one warp reduction closes each sum.
 // ---------------------------------------------------------------------------
+
+// Query side of the filter for MT > 0: this lane's chunk of U, L, y, UL, LU
+// (zero beyond the series, where every term is then 0).
+template <int MT>
+struct EnvQuery {
+    float u[MT > 0 ? MT : 1], l[MT > 0 ? MT : 1], y[MT > 0 ? MT : 1], ul[MT > 0 ? MT : 1], lu[MT > 0 ? MT : 1];
+};
+
+// UL, LU exist only when the run computes LB_Improved (b.lbi_inline).
+template <int MT>
+__device__ __forceinline__ void env_load_query(EnvQuery<MT> &Qv, const CascadeBufs &b, int q) {
+    if constexpr (MT > 0) {
+        const int lane = threadIdx.x & 31;
+        const int64_t o = (int64_t)q * b.n;
+        const bool second = b.lbi_inline != 0;
+#pragma unroll
+        for (int t = 0; t < MT; ++t) {
+            const int i = lane * MT + t;
+            const bool in = i < b.n;
+            Qv.u[t] = in ? b.U[o + i] : 0.0f;
+            Qv.l[t] = in ? b.L[o + i] : 0.0f;
+            Qv.y[t] = in ? b.queries[o + i] : 0.0f;
+            Qv.ul[t] = (in && second) ? b.UL[o + i] : 0.0f;
+            Qv.lu[t] = (in && second) ? b.LU[o + i] : 0.0f;
+        }
+    }
+}
+
+// The rows of one candidate this lane reads (MT > 0): its chunk of x (for
+// the first sum, when the matrix does not already hold LB_Keogh) and of the
+// candidate's envelope XU, XL (for the second).
+template <int MT>
+struct EnvRows {
+    LbiChunk<MT> x, xu, xl;
+};
+
+// XU, XL exist only when the run computes LB_Improved (b.lbi_inline).
+template <int MT>
+__device__ __forceinline__ void env_load_rows(EnvRows<MT> &r, const CascadeBufs &b, int c, bool vec, bool need_x) {
+    const int64_t o = (int64_t)c * b.n;
+    if (need_x) lbi_load_chunk<MT>(r.x, b.db + o, b.n, vec);
+    if (b.lbi_inline) {
+        lbi_load_chunk<MT>(r.xu, b.XU + o, b.n, vec);
+        lbi_load_chunk<MT>(r.xl, b.XL + o, b.n, vec);
+    }
+}
+
+// LB_Improved^p of the pair (q, c), or LB_Keogh^p alone when that exceeds thr
+// or !do_lbi.  known >= 0: LB_Keogh^p already computed (the first sum is not
+// formed again).  *lbk gets LB_Keogh^p.  MT > 0: r holds this lane's chunks;
+// MT == 0: lane l takes indices l, l + 32, ... (coalesced loads).
 template <int P, int MT>
-__global__ void __launch_bounds__(256, 3) k_lbi_filter(CascadeBufs b, bool vec) {
+__device__ __forceinline__ float warp_lbi_env(const CascadeBufs &b, int q, int c, const EnvQuery<MT> &Qv,
+                                              const EnvRows<MT> &r, float known, float thr, bool do_lbi,
+                                              float *lbk) {
+    const int lane = threadIdx.x & 31;
+    const int n = b.n;
+    float first = known;
+    if (known < 0.0f) {
+        float acc = 0.0f;
+        if constexpr (MT > 0) {
+#pragma unroll
+            for (int t = 0; t < MT; ++t) acc = acc_dist<P>(acc, r.x.v[t], Qv.l[t], Qv.u[t]);
+        } else {
+            const float *x = b.db + (int64_t)c * n;
+            const float *U = b.U + (int64_t)q * n, *L = b.L + (int64_t)q * n;
+#pragma unroll 4
+            for (int i = lane; i < n; i += 32) acc = acc_dist<P>(acc, __ldg(x + i), __ldg(L + i), __ldg(U + i));
+        }
+        first = warp_sum(acc);
+    }
+    *lbk = first;
+    if (!do_lbi || first > thr) return first;
+    float acc = 0.0f;
+    if constexpr (MT > 0) {
+#pragma unroll
+        for (int t = 0; t < MT; ++t)
+            acc = acc_dist<P>(acc, Qv.y[t], fminf(r.xl.v[t], Qv.lu[t]), fmaxf(r.xu.v[t], Qv.ul[t]));
+    } else {
+        const int64_t oc = (int64_t)c * n, oq = (int64_t)q * n;
+        const float *xu = b.XU + oc, *xl = b.XL + oc;
+        const float *y = b.queries + oq, *ul = b.UL + oq, *lu = b.LU + oq;
+#pragma unroll 4
+        for (int i = lane; i < n; i += 32)
+            acc = acc_dist<P>(acc, __ldg(y + i), fminf(__ldg(xl + i), __ldg(lu + i)),
+                              fmaxf(__ldg(xu + i), __ldg(ul + i)));
+    }
+    // one reduction of the full value keeps the sum's rounding independent
+    // of where the first sum came from
+    return warp_sum(acc + (lane == 0 ? first : 0.0f));
+}
+
+template <int P, int MT>
+__global__ void __launch_bounds__(256, 2) k_lbi_filter(CascadeBufs b, bool vec) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int nw = blockDim.x >> 5;
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // CTAs in flight share a candidate segment (consecutive CTAs are queries),
     // so the segment's rows stay in L2 for all the queries that test them
     const int q = blockIdx.x;
-    const int n = b.n, w = b.w;
     const int per_warp_cap = b.seg_len / nw + 32;  // candidates one warp scans, rounded up
-    float *sq = reinterpret_cast<float *>(smraw);
-    float *scratch_all = sq + lbi_query_floats(n);
-    float *scratch = scratch_all + (size_t)wid * lbi_scratch_floats(n, w);
-    int32_t *seeds = reinterpret_cast<int32_t *>(scratch_all + (size_t)nw * lbi_scratch_floats(n, w));
+    int32_t *seeds = reinterpret_cast<int32_t *>(smraw);
     int32_t *surv_c = seeds + b.S + (size_t)wid * 2 * per_warp_cap;
     float *surv_v = reinterpret_cast<float *>(surv_c + per_warp_cap);
     for (int t = threadIdx.x; t < b.S; t += blockDim.x) seeds[t] = b.seed_pairs[(int64_t)t * b.Q + q].c;
-    LbiQuery<MT> Qv;
-    if (b.lbi_inline || b.summary) {
-        lbi_load_query<MT>(Qv, b.queries + (int64_t)q * n, b.U + (int64_t)q * n, b.L + (int64_t)q * n, n, sq);
-        lbi_init_scratch<MT>(scratch, n, b.w);
-    }
+    EnvQuery<MT> Qv;
+    if (b.lbi_inline || b.summary) env_load_query<MT>(Qv, b, q);
     __syncthreads();
 
     // From here on each warp works alone: for each of the CTA's segments it
     // scans its share of the segment, keeps its survivors in its own shared
     // buffer and writes them as one contiguous block of the pair list
-    // (sub-segment (q, sg, wid)).  The query staging above is shared by the
-    // CTA's seg_per_cta consecutive segments.
+    // (sub-segment (q, sg, wid)).
     const float bq = (b.mode == DTW_MODE_NOPRUNE) ? kInf : load_threshold(b.bsf + q);
     const float thr = bq * (1.0f + b.slack);
     // the matrix holds LB_Keogh^p, or the piecewise-sum bound in the units of
     // sum_j D_j^p (for p = 2 the bound is that sum over max_j |C_j|)
     const float thr_m = b.summary ? thr * b.summary_scale : thr;
     const int nsegs = b.nseg / nw;
+    const bool lbk_done = !b.summary;  // the survivors carry LB_Keogh^p
     for (int sj = 0; sj < b.seg_per_cta; ++sj) {
     const int sg = blockIdx.y * b.seg_per_cta + sj;
     if (sg >= nsegs) break;
     const int c0 = sg * b.seg_len;
     const int c1 = min(b.N, c0 + b.seg_len);
     const float *lbrow = b.lb + (int64_t)q * b.N;
-    // phase 1: LB_Keogh test over this warp's share of the segment; the
+    // phase 1: matrix test over this warp's share of the segment; the
     // survivors (not seeds) are compacted into the warp's buffer
     int cnt1 = 0;
     for (int base = c0 + wid * 32; base < c1; base += nw * 32) {
@@ -845,25 +947,24 @@ __global__ void __launch_bounds__(256, 3) k_lbi_filter(CascadeBufs b, bool vec) 
     }
     __syncwarp();
     const unsigned long long pk = (unsigned long long)cnt1;
-    const bool lbk_done = !b.summary;  // the survivors carry LB_Keogh^p
-    unsigned long long kp = 0;         // LB_Keogh survivors (summary mode)
-    // phase 2: LB_Improved of each survivor (warp per pair), the next
-    // candidate's chunk prefetched while the current one is processed;
-    // survivors are kept in place (write index <= read index).  With the
-    // piecewise-sum pre-filter the matrix held that bound, and LB_Keogh is
-    // formed here first; otherwise the matrix value is LB_Keogh^p itself.
+    unsigned long long kp = 0;  // LB_Keogh survivors (summary mode)
+    // phase 2: LB_Keogh (when the matrix held the pre-filter bound) and
+    // LB_Improved of each survivor, warp per pair, the next candidate's rows
+    // loaded while the current one is processed; survivors are kept in
+    // place (write index <= read index)
     int cnt = 0;
     if (b.lbi_inline || !lbk_done) {
-        LbiChunk<MT> cur, nxt;
-        if (cnt1 > 0) lbi_load_chunk<MT>(nxt, b.db + (int64_t)surv_c[0] * n, n, vec);
+        EnvRows<MT> cur, nxt;
+        if (MT > 0 && cnt1 > 0) env_load_rows<MT>(nxt, b, surv_c[0], vec, !lbk_done);
         for (int e = 0; e < cnt1; ++e) {
             const int cc = surv_c[e];
             const float known = lbk_done ? surv_v[e] : -1.0f;
-            cur = nxt;
-            if (e + 1 < cnt1) lbi_load_chunk<MT>(nxt, b.db + (int64_t)surv_c[e + 1] * n, n, vec);
-            float lbk = known;
-            const float v = warp_lb_improved<P, MT>(b.db + (int64_t)cc * n, Qv, n, w, scratch, vec,
-                                                    MT > 0 ? &cur : nullptr, b.lbi_inline != 0, thr, &lbk, known);
+            if constexpr (MT > 0) {
+                cur = nxt;
+                if (e + 1 < cnt1) env_load_rows<MT>(nxt, b, surv_c[e + 1], vec, !lbk_done);
+            }
+            float lbk;
+            const float v = warp_lbi_env<P, MT>(b, q, cc, Qv, cur, known, thr, b.lbi_inline != 0, &lbk);
             if (!lbk_done) kp += (lbk <= thr) ? 1 : 0;
             if (v <= thr) {
                 if (lane == 0) {
@@ -906,88 +1007,28 @@ __global__ void __launch_bounds__(256, 3) k_lbi_filter(CascadeBufs b, bool vec) 
     }  // segments of this CTA
 }
 
-static size_t lbi_filter_smem(int n, int w, int S, int seg_len, int nw) {
-    const int64_t per_warp = (int64_t)lbi_scratch_floats(n, w) * sizeof(float);
-    const int64_t per_query = (int64_t)lbi_query_floats(n) * sizeof(float);
-    return (size_t)(per_query + (int64_t)S * 4 + 64 + nw * (per_warp + 8 * (seg_len / nw + 32)));
+static size_t lbi_filter_smem(int S, int seg_len, int nw) {
+    return (size_t)((int64_t)S * 4 + 64 + (int64_t)nw * 8 * (seg_len / nw + 32));
 }
 
-// Warps per filter CTA.  Chunks in registers (n <= 256): as many as fit (up
-// to 8): measured fastest, as the CTA's query staging and its segments are
-// shared by more warps.  Chunks in shared memory: the count that keeps the
-// most warps resident per SM, by the occupancy calculator (shared memory and
-// registers).  Cached per shape.
-template <int P, int MT>
-static int lbi_filter_warps_for(int n, int w, int S, int seg_len) {
-    if constexpr (MT > 0) {
-        int nw = 8;
-        while (nw > 1 && lbi_filter_smem(n, w, S, seg_len, nw) > 227 * 1024) --nw;
-        return nw;
-    }
-    static std::mutex mu;
-    static std::map<std::array<int, 4>, int> cache;
-    const std::array<int, 4> key{n, w, S, seg_len};
-    std::lock_guard<std::mutex> lk(mu);
-    auto it = cache.find(key);
-    if (it != cache.end()) return it->second;
-    cudaFuncSetAttribute(k_lbi_filter<P, MT>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                         (int)cudaSharedmemCarveoutMaxShared);
-    int best = 0, best_warps = 0;
-    for (int nw = 1; nw <= 8; ++nw) {
-        const size_t smem = lbi_filter_smem(n, w, S, seg_len, nw);
-        if (smem > 227 * 1024) break;
-        int blocks = 0;
-        if (cudaFuncSetAttribute(k_lbi_filter<P, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-                cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_lbi_filter<P, MT>, nw * 32, smem) !=
-                cudaSuccess) {
-            cudaGetLastError();
-            blocks = 0;
-        }
-        if (blocks * nw > best_warps) {
-            best_warps = blocks * nw;
-            best = nw;
-        }
-    }
-    if (best == 0) {
-        // no answer from the calculator: the largest count within 72 KB
-        best = 8;
-        while (best > 1 && lbi_filter_smem(n, w, S, seg_len, best) > 72 * 1024) --best;
-    }
-    cache[key] = best;
-    return best;
-}
-
-template <int P>
-static int lbi_filter_warps_p(int n, int w, int S, int seg_len) {
-    switch (lbi_geom(n).m) {
-        case 1: return lbi_filter_warps_for<P, 1>(n, w, S, seg_len);
-        case 2: return lbi_filter_warps_for<P, 2>(n, w, S, seg_len);
-        case 4: return lbi_filter_warps_for<P, 4>(n, w, S, seg_len);
-        case 8: return lbi_filter_warps_for<P, 8>(n, w, S, seg_len);
-        default: return lbi_filter_warps_for<P, 0>(n, w, S, seg_len);
-    }
-}
-
+// Warps per filter CTA: `want` (1..8) if its shared memory fits, else 8 (the
+// CTA's segments and query are then shared by the most warps).
 int lbi_filter_warps(int n, int w, int S, int seg_len, int p, int want) {
-    if (want > 0) {
-        int nw = want > 8 ? 8 : want;
-        while (nw > 1 && lbi_filter_smem(n, w, S, seg_len, nw) > 227 * 1024) --nw;
-        return nw;
-    }
-    return p == 1 ? lbi_filter_warps_p<1>(n, w, S, seg_len) : lbi_filter_warps_p<2>(n, w, S, seg_len);
+    (void)n;
+    (void)w;
+    (void)p;
+    int nw = (want > 0 && want < 8) ? want : 8;
+    while (nw > 1 && lbi_filter_smem(S, seg_len, nw) > 227 * 1024) --nw;
+    return nw;
 }
 
 template <int P, int MT>
 static void lbi_filter_go(const CascadeBufs &b, bool vec, cudaStream_t s) {
     const int nw = b.filter_warps > 0 ? b.filter_warps : lbi_filter_warps(b.n, b.w, b.S, b.seg_len, P);
-    const size_t smem = lbi_filter_smem(b.n, b.w, b.S, b.seg_len, nw);
+    const size_t smem = lbi_filter_smem(b.S, b.seg_len, nw);
     const int nsegs = b.nseg / nw;
     const dim3 grid(b.Q, (nsegs + b.seg_per_cta - 1) / b.seg_per_cta);
     cudaFuncSetAttribute(k_lbi_filter<P, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    // the CTAs per SM are limited by shared memory: prefer it over L1
-    cudaFuncSetAttribute(k_lbi_filter<P, MT>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                         (int)cudaSharedmemCarveoutMaxShared);
     k_lbi_filter<P, MT><<<grid, nw * 32, smem, s>>>(b, vec);
 }
 
@@ -1004,6 +1045,10 @@ static void lbi_filter_dispatch(const CascadeBufs &b, bool vec, cudaStream_t s) 
 
 cudaError_t launch_lbi_filter(const CascadeBufs &b, cudaStream_t s) {
     if (b.N <= 0 || b.Q <= 0) return cudaSuccess;
+    if (b.lbi_inline && (b.XU == nullptr || b.XL == nullptr || b.UL == nullptr || b.LU == nullptr))
+        return cudaErrorInvalidValue;
+    // rows start on 16-byte boundaries when n % 4 == 0 and the bases do (the
+    // envelope rows always do)
     const bool vec = (b.n % 4 == 0) && ((reinterpret_cast<uintptr_t>(b.db) & 15) == 0);
     if (b.p == 1) lbi_filter_dispatch<1>(b, vec, s);
     else lbi_filter_dispatch<2>(b, vec, s);
