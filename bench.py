@@ -45,7 +45,7 @@ METRIC = "exact 1-NN DTW queries/s (LB_Improved cascade)"
 # DRAM bytes per launch of the filter kernel at the default workload, from one
 # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum); valid for that
 # workload and the kernel as captured (profiles/k_lbi_filter_traffic_*.md)
-FILTER_TRAFFIC = {"workload": (100_000, 256, 25, 1000), "bytes": 540.64e6,
+FILTER_TRAFFIC = {"workload": (100_000, 256, 25, 1000), "bytes": None,
                   "source": "profiles/k_lbi_filter_traffic_rw100k_n256_w25_q1000.md"}
 L2_BYTES = 129 * 2**20
 
@@ -282,21 +282,24 @@ def roofline(prof, a, steps, peaks, stats):
                 "peak_note": "%d SMs x 128 fp32 lanes x %.0f MHz (max SM clock)" % (sms, clock / 1e6)}
     if dom == "lb_improved":
         # the filter stage: a compare per scanned bound, LB_Keogh (4 fp32 ops
-        # per index) of each piecewise-sum survivor, and LB_Improved's second
-        # pass (7 more per index: envelope 3 -- the paper's 3n comparisons --
-        # and second term 4) of each LB_Keogh survivor
+        # per index: 2 subtractions, a 3-input max, an add/fma) of each
+        # piecewise-sum survivor, and LB_Improved's second sum (6 per index: the
+        # max and min with the query's second-order envelope, 2 subtractions, a
+        # 3-input max, an add/fma) of each LB_Keogh survivor
         scanned = stats.get("candidates", 0) - stats.get("seeds", 0)
         pd_surv = scanned - stats.get("pruned_summary", 0)
         lbk_surv = pd_surv - stats.get("pruned_keogh", 0)
-        ops = scanned * 1.0 + pd_surv * a.n * 4.0 + lbk_surv * a.n * 7.0
+        ops = scanned * 1.0 + pd_surv * a.n * 4.0 + lbk_surv * a.n * 6.0
         achieved = ops / 1e12 / (ms / 1e3) if scanned > 0 else None
         same = (a.N, a.n, a.w, a.Q) == FILTER_TRAFFIC["workload"] and a.data == "random_walk"
         traffic = FILTER_TRAFFIC["bytes"] if same else None
+        # algorithmic DRAM bytes: the bound matrix and the database rows and
+        # their envelopes once each
+        alg_bytes = a.Q * a.N * 4.0 + a.N * a.n * 4.0 * 3
         return {"kernel": "k_lbi_filter", "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Top/s",
                 "frac": (achieved / alu_peak) if achieved else None, "traffic": traffic,
-                "traffic_note": ("DRAM bytes per launch, %s; algorithmic bytes 502.4 MB (bound matrix 400 MB + "
-                                 "database 102.4 MB) plus the survivor list" % FILTER_TRAFFIC["source"])
-                if traffic else None,
+                "traffic_note": ("DRAM bytes per launch, %s" % FILTER_TRAFFIC["source"]) if traffic else None,
+                "algorithmic_bytes": alg_bytes,
                 "hbm_gbs": (traffic / 1e9 / (ms / 1e3)) if traffic else None, "ms_per_launch": ms,
                 "lb_keogh_pairs": pd_surv, "lb_improved_pairs": lbk_surv, "stage_share": share,
                 "peak_note": "%d SMs x 128 fp32 lanes x %.0f MHz (max SM clock)" % (sms, clock / 1e6)}

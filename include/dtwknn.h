@@ -191,7 +191,8 @@ enum {
     DTW_STAGE_LB_IMPROVED = 5,
     DTW_STAGE_DTW = 6,
     DTW_STAGE_FINALIZE = 7,
-    DTW_NUM_STAGES = 8
+    DTW_STAGE_DB_PREP = 8, /* per-call database terms: part sums, row envelopes */
+    DTW_NUM_STAGES = 9
 };
 typedef struct {
     double ms[DTW_NUM_STAGES];

@@ -53,8 +53,9 @@ class Stats(ctypes.Structure):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
 
 
-NUM_STAGES = 8
-STAGE_NAMES = ["envelope", "lb_keogh", "seed_select", "seed_dtw", "seed_kth", "lb_improved", "dtw", "finalize"]
+NUM_STAGES = 9
+STAGE_NAMES = ["envelope", "lb_keogh", "seed_select", "seed_dtw", "seed_kth", "lb_improved", "dtw", "finalize",
+               "db_prep"]
 
 
 class Profile(ctypes.Structure):

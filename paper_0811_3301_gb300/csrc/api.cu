@@ -363,15 +363,8 @@ dtw_status knn_search_ex(const float *db, int64_t N, const float *queries, int64
     float *odist = od_dev ? out_dist : x.out_dist;
     CUDA_TRY(cudaMemsetAsync(x.counters, 0, 2 * CNT_NUM * sizeof(unsigned long long), s));
     unsigned *xmax_bits = reinterpret_cast<unsigned *>(x.xmax);
-    if (pl.summary) {
-        // part sums of the database rows, once per call
-        CUDA_TRY(cudaMemsetAsync(xmax_bits, 0, sizeof(unsigned long long), s));
-        CUDA_TRY(launch_summarize(dbd, N, n, pl.parts, x.PX, xmax_bits, s));
-    }
-    if (plan_needs_db_envelope(pl)) {
-        // the database rows' envelopes, once per call (LB_Improved's second sum)
-        CUDA_TRY(launch_envelope(dbd, N, n, pl.we, x.XU, x.XL, QueryCopies{}, 0, s));
-    }
+    // part sums and row envelopes of the database, once per call
+    CUDA_TRY(prepare_database(pl, dbd, x.PX, xmax_bits, x.XU, x.XL, s));
     for (int64_t q0 = 0; q0 < Q; q0 += Qc) {
         const int qn = (int)((Q - q0) < Qc ? (Q - q0) : Qc);
         const float *qd;

@@ -70,6 +70,10 @@ __global__ void __launch_bounds__(256) k_seed_select(CascadeBufs b) {
             int c = (best == ~0ull) ? -1 : (int)(unsigned)(best & 0xffffffffull);
             b.seed_pairs[(int64_t)s * b.Q + q] = Pair{q, c};
             b.seed_res[(int64_t)s * b.Q + q] = kInf;
+            // the seed's matrix entry becomes NaN, which no bound test passes:
+            // the filter then skips seeds without looking them up (every
+            // thread finished reading the row before the first barrier above)
+            if (c >= 0) b.lb[(int64_t)q * b.N + c] = __int_as_float(0x7fc00000);
         }
         __syncthreads();
         if (key[0] == winner && winner != ~0ull) {

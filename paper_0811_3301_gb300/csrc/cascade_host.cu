@@ -49,8 +49,9 @@ cudaError_t profile_collect(double *ms, int64_t *launches, bool reset) {
     return cudaSuccess;
 }
 
-static const char *const kStageNames[DTW_NUM_STAGES] = {"envelope", "lb_keogh",    "seed_select", "seed_dtw",
-                                                         "seed_kth", "lb_improved", "dtw",         "finalize"};
+static const char *const kStageNames[DTW_NUM_STAGES] = {"envelope",    "lb_keogh", "seed_select",
+                                                         "seed_dtw",    "seed_kth", "lb_improved",
+                                                         "dtw",         "finalize", "db_prep"};
 
 // Marks a stage with an NVTX range (host side, for timeline tools; no cost
 // without one attached) and, when profiling is on and the stream is not being
@@ -350,6 +351,17 @@ cudaError_t cascade_run(const CascadePlan &pl, const CascadeWs &l, const float *
         StageTimer tm(DTW_STAGE_FINALIZE, s);
         RUN_TRY(launch_finalize(b, s));
     }
+    return cudaSuccess;
+}
+
+cudaError_t prepare_database(const CascadePlan &pl, const float *db, float *PX, unsigned *xmax_bits, float *XU,
+                             float *XL, cudaStream_t s) {
+    StageTimer tm(DTW_STAGE_DB_PREP, s);
+    if (pl.summary) {
+        RUN_TRY(cudaMemsetAsync(xmax_bits, 0, sizeof(unsigned long long), s));
+        RUN_TRY(launch_summarize(db, pl.N, pl.n, pl.parts, PX, xmax_bits, s));
+    }
+    if (plan_needs_db_envelope(pl)) RUN_TRY(launch_envelope(db, pl.N, pl.n, pl.we, XU, XL, QueryCopies{}, 0, s));
     return cudaSuccess;
 }
 

@@ -72,6 +72,13 @@ cudaError_t cascade_run(const CascadePlan &pl, const CascadeWs &ws, const float 
 // Whether a run under pl reads the database envelopes XU, XL.
 inline bool plan_needs_db_envelope(const CascadePlan &pl) { return pl.N > 0 && pl.mode == DTW_MODE_IMPROVED; }
 
+// The database terms a run reads, computed from db [N][n]: the part sums PX
+// [N][parts] and max |x| (xmax_bits, 8 bytes) when pl.summary, and the row
+// envelopes XU, XL [N][n] when plan_needs_db_envelope(pl).  Timed as stage
+// DTW_STAGE_DB_PREP.
+cudaError_t prepare_database(const CascadePlan &pl, const float *db, float *PX, unsigned *xmax_bits, float *XU,
+                             float *XL, cudaStream_t s);
+
 // Adds the statistics of Q queries run under pl, from the host copy of the
 // 2 * CNT_NUM counters, to st.
 void cascade_stats(const CascadePlan &pl, int64_t Q, const unsigned long long *h, dtw_stats *st);

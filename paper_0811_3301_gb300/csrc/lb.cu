@@ -799,8 +799,17 @@ cudaError_t launch_lbi_single(const float *cand, int64_t N, const float *q, cons
 // its own indices and one warp reduction closes each sum.
 // ---------------------------------------------------------------------------
 
-// Query side of the filter for MT > 0: this lane's chunk of U, L, y, UL, LU
-// (zero beyond the series, where every term is then 0).
+// Indices of a lane for MT > 0 (no sum here relates different indices, so
+// any assignment works; this one makes every copy of a warp contiguous):
+// with vector rows, 16-byte pieces lane, lane + 32, ... (index 4 (lane + 32 j)
+// + k is element 4 j + k); otherwise indices lane, lane + 32, ...
+template <int MT>
+__device__ __forceinline__ int env_index(int lane, int t, bool vec) {
+    return (vec && MT >= 4) ? 4 * (lane + 32 * (t >> 2)) + (t & 3) : lane + 32 * t;
+}
+
+// Query side of the filter for MT > 0: this lane's elements of U, L, y, UL,
+// LU (zero beyond the series, where every term is then 0).
 template <int MT>
 struct EnvQuery {
     float u[MT > 0 ? MT : 1], l[MT > 0 ? MT : 1], y[MT > 0 ? MT : 1], ul[MT > 0 ? MT : 1], lu[MT > 0 ? MT : 1];
@@ -808,14 +817,14 @@ struct EnvQuery {
 
 // UL, LU exist only when the run computes LB_Improved (b.lbi_inline).
 template <int MT>
-__device__ __forceinline__ void env_load_query(EnvQuery<MT> &Qv, const CascadeBufs &b, int q) {
+__device__ __forceinline__ void env_load_query(EnvQuery<MT> &Qv, const CascadeBufs &b, int q, bool vec) {
     if constexpr (MT > 0) {
         const int lane = threadIdx.x & 31;
         const int64_t o = (int64_t)q * b.n;
         const bool second = b.lbi_inline != 0;
 #pragma unroll
         for (int t = 0; t < MT; ++t) {
-            const int i = lane * MT + t;
+            const int i = env_index<MT>(lane, t, vec);
             const bool in = i < b.n;
             Qv.u[t] = in ? b.U[o + i] : 0.0f;
             Qv.l[t] = in ? b.L[o + i] : 0.0f;
@@ -834,14 +843,76 @@ struct EnvRows {
     LbiChunk<MT> x, xu, xl;
 };
 
-// XU, XL exist only when the run computes LB_Improved (b.lbi_inline).
+// Rows reach the warp through a ring of kEnvStages stages in shared memory,
+// filled by cp.async kEnvStages - 1 pairs ahead of their use.  Each lane
+// copies and reads back only its own elements of each row (x, XU, XL), so
+// the ring needs no barrier: a lane's wait for its copy group is enough.  A
+// stage holds each row in order ([row][32 MT] floats): a warp's copies and
+// reads cover contiguous 512-byte (or 128-byte) spans.
+constexpr int kEnvStages = 3;
 template <int MT>
-__device__ __forceinline__ void env_load_rows(EnvRows<MT> &r, const CascadeBufs &b, int c, bool vec, bool need_x) {
-    const int64_t o = (int64_t)c * b.n;
-    if (need_x) lbi_load_chunk<MT>(r.x, b.db + o, b.n, vec);
-    if (b.lbi_inline) {
-        lbi_load_chunk<MT>(r.xu, b.XU + o, b.n, vec);
-        lbi_load_chunk<MT>(r.xl, b.XL + o, b.n, vec);
+constexpr int env_ring_floats() {
+    return MT > 0 ? kEnvStages * 3 * 32 * MT : 0;
+}
+
+// Starts the copies of candidate c's rows into stage st.  XU, XL exist only
+// when the run computes LB_Improved (b.lbi_inline); x only when the matrix
+// does not already hold LB_Keogh (need_x).  Elements past the series are
+// zero-filled (their terms are then 0), their source clamped to the row start.
+template <int MT>
+__device__ __forceinline__ void env_issue(float *ring, int st, const CascadeBufs &b, int c, bool vec, bool need_x) {
+    const int lane = threadIdx.x & 31;
+    const int64_t row = (int64_t)c * b.n;
+    float *stage = ring + st * 3 * 32 * MT;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        if (r == 0 && !need_x) continue;
+        if (r > 0 && !b.lbi_inline) continue;
+        const float *src = (r == 0 ? b.db : (r == 1 ? b.XU : b.XL)) + row;
+        float *dst = stage + r * 32 * MT;
+        if (vec && MT >= 4) {
+#pragma unroll
+            for (int j = 0; j < MT / 4; ++j) {
+                const int i = 4 * (lane + 32 * j);  // n % 4 == 0: a piece is wholly in or out
+                const bool in = i < b.n;
+                cp_async16(dst + i, in ? src + i : src, in);
+            }
+        } else {
+#pragma unroll
+            for (int t = 0; t < MT; ++t) {
+                const int i = lane + 32 * t;
+                const bool in = i < b.n;
+                cp_async4(dst + i, in ? src + i : src, in);
+            }
+        }
+    }
+}
+
+// This lane's chunks of stage st, after its copies completed.
+template <int MT>
+__device__ __forceinline__ void env_read(EnvRows<MT> &rw, const float *ring, int st, bool vec, bool need_x,
+                                         bool need_env) {
+    const int lane = threadIdx.x & 31;
+    const float *stage = ring + st * 3 * 32 * MT;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        if (r == 0 && !need_x) continue;
+        if (r > 0 && !need_env) continue;
+        float *v = r == 0 ? rw.x.v : (r == 1 ? rw.xu.v : rw.xl.v);
+        const float *src = stage + r * 32 * MT;
+        if (vec && MT >= 4) {
+#pragma unroll
+            for (int j = 0; j < MT / 4; ++j) {
+                const float4 f = *reinterpret_cast<const float4 *>(src + 4 * (lane + 32 * j));
+                v[4 * j] = f.x;
+                v[4 * j + 1] = f.y;
+                v[4 * j + 2] = f.z;
+                v[4 * j + 3] = f.w;
+            }
+        } else {
+#pragma unroll
+            for (int t = 0; t < MT; ++t) v[t] = src[lane + 32 * t];
+        }
     }
 }
 
@@ -899,13 +970,12 @@ __global__ void __launch_bounds__(256, 2) k_lbi_filter(CascadeBufs b, bool vec) 
     // so the segment's rows stay in L2 for all the queries that test them
     const int q = blockIdx.x;
     const int per_warp_cap = b.seg_len / nw + 32;  // candidates one warp scans, rounded up
-    int32_t *seeds = reinterpret_cast<int32_t *>(smraw);
-    int32_t *surv_c = seeds + b.S + (size_t)wid * 2 * per_warp_cap;
+    float *ring = reinterpret_cast<float *>(smraw) + (size_t)wid * env_ring_floats<MT>();
+    int32_t *surv_c = reinterpret_cast<int32_t *>(smraw) + (size_t)nw * env_ring_floats<MT>() +
+                      (size_t)wid * 2 * per_warp_cap;
     float *surv_v = reinterpret_cast<float *>(surv_c + per_warp_cap);
-    for (int t = threadIdx.x; t < b.S; t += blockDim.x) seeds[t] = b.seed_pairs[(int64_t)t * b.Q + q].c;
     EnvQuery<MT> Qv;
-    if (b.lbi_inline || b.summary) env_load_query<MT>(Qv, b, q);
-    __syncthreads();
+    if (b.lbi_inline || b.summary) env_load_query<MT>(Qv, b, q, vec);
 
     // From here on each warp works alone: for each of the CTA's segments it
     // scans its share of the segment, keeps its survivors in its own shared
@@ -925,22 +995,27 @@ __global__ void __launch_bounds__(256, 2) k_lbi_filter(CascadeBufs b, bool vec) 
     const int c1 = min(b.N, c0 + b.seg_len);
     const float *lbrow = b.lb + (int64_t)q * b.N;
     // phase 1: matrix test over this warp's share of the segment; the
-    // survivors (not seeds) are compacted into the warp's buffer
+    // survivors are compacted into the warp's buffer (seeds hold NaN in the
+    // matrix and never pass).  Eight loads per lane are issued before any is
+    // tested, so that the scan waits on memory once per eight rows of 32.
     int cnt1 = 0;
-    for (int base = c0 + wid * 32; base < c1; base += nw * 32) {
-        const int c = base + lane;
-        const bool valid = c < c1;
-        const float lbv = valid ? lbrow[c] : kInf;
-        bool pass = valid && (lbv <= thr_m);
-        if (__any_sync(0xffffffffu, pass)) {
-            if (pass) {
-                for (int t = 0; t < b.S; ++t) pass = pass && (seeds[t] != c);
-            }
+    const int stride = nw * 32;
+    for (int base0 = c0 + wid * 32; base0 < c1; base0 += 8 * stride) {
+        float v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int c = base0 + u * stride + lane;
+            v[u] = c < c1 ? lbrow[c] : kInf;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int c = base0 + u * stride + lane;
+            const bool pass = c < c1 && v[u] <= thr_m;
             const unsigned m = __ballot_sync(0xffffffffu, pass);
             if (pass) {
                 const int slot = cnt1 + __popc(m & ((1u << lane) - 1));
                 surv_c[slot] = c;
-                surv_v[slot] = lbv;
+                surv_v[slot] = v[u];
             }
             cnt1 += __popc(m);
         }
@@ -949,19 +1024,30 @@ __global__ void __launch_bounds__(256, 2) k_lbi_filter(CascadeBufs b, bool vec) 
     const unsigned long long pk = (unsigned long long)cnt1;
     unsigned long long kp = 0;  // LB_Keogh survivors (summary mode)
     // phase 2: LB_Keogh (when the matrix held the pre-filter bound) and
-    // LB_Improved of each survivor, warp per pair, the next candidate's rows
-    // loaded while the current one is processed; survivors are kept in
-    // place (write index <= read index)
+    // LB_Improved of each survivor, warp per pair, the rows of the next
+    // kEnvStages - 1 candidates in flight (MT > 0) while the current one is
+    // processed; survivors are kept in place (write index <= read index)
     int cnt = 0;
     if (b.lbi_inline || !lbk_done) {
-        EnvRows<MT> cur, nxt;
-        if (MT > 0 && cnt1 > 0) env_load_rows<MT>(nxt, b, surv_c[0], vec, !lbk_done);
+        const bool need_x = !lbk_done;
+        if constexpr (MT > 0) {
+#pragma unroll
+            for (int e = 0; e < kEnvStages - 1; ++e) {
+                if (e < cnt1) env_issue<MT>(ring, e, b, surv_c[e], vec, need_x);
+                cp_async_commit();
+            }
+        }
         for (int e = 0; e < cnt1; ++e) {
             const int cc = surv_c[e];
             const float known = lbk_done ? surv_v[e] : -1.0f;
+            EnvRows<MT> cur;
             if constexpr (MT > 0) {
-                cur = nxt;
-                if (e + 1 < cnt1) env_load_rows<MT>(nxt, b, surv_c[e + 1], vec, !lbk_done);
+                // the stage refilled here was read (and used) by pair e - 1
+                const int ahead = e + kEnvStages - 1;
+                if (ahead < cnt1) env_issue<MT>(ring, ahead % kEnvStages, b, surv_c[ahead], vec, need_x);
+                cp_async_commit();
+                cp_async_wait<kEnvStages - 1>();
+                env_read<MT>(cur, ring, e % kEnvStages, vec, need_x, b.lbi_inline != 0);
             }
             float lbk;
             const float v = warp_lbi_env<P, MT>(b, q, cc, Qv, cur, known, thr, b.lbi_inline != 0, &lbk);
@@ -975,6 +1061,7 @@ __global__ void __launch_bounds__(256, 2) k_lbi_filter(CascadeBufs b, bool vec) 
             }
             __syncwarp();
         }
+        if constexpr (MT > 0) cp_async_wait<0>();  // only empty groups remain
     } else {
         cnt = cnt1;
     }
@@ -1007,25 +1094,33 @@ __global__ void __launch_bounds__(256, 2) k_lbi_filter(CascadeBufs b, bool vec) 
     }  // segments of this CTA
 }
 
-static size_t lbi_filter_smem(int S, int seg_len, int nw) {
-    return (size_t)((int64_t)S * 4 + 64 + (int64_t)nw * 8 * (seg_len / nw + 32));
+// chunk length the filter keeps in registers (0: strided loads)
+static int lbi_filter_mt(int n) {
+    const int m = lbi_geom(n).m;
+    return m <= kLbiRegM ? m : 0;
+}
+
+static size_t lbi_filter_smem(int n, int S, int seg_len, int nw) {
+    (void)S;
+    const int mt = lbi_filter_mt(n);
+    const int64_t ring = mt > 0 ? (int64_t)kEnvStages * 3 * 32 * mt * 4 : 0;
+    return (size_t)(nw * ring + 64 + (int64_t)nw * 8 * (seg_len / nw + 32));
 }
 
 // Warps per filter CTA: `want` (1..8) if its shared memory fits, else 8 (the
 // CTA's segments and query are then shared by the most warps).
 int lbi_filter_warps(int n, int w, int S, int seg_len, int p, int want) {
-    (void)n;
     (void)w;
     (void)p;
     int nw = (want > 0 && want < 8) ? want : 8;
-    while (nw > 1 && lbi_filter_smem(S, seg_len, nw) > 227 * 1024) --nw;
+    while (nw > 1 && lbi_filter_smem(n, S, seg_len, nw) > 227 * 1024) --nw;
     return nw;
 }
 
 template <int P, int MT>
 static void lbi_filter_go(const CascadeBufs &b, bool vec, cudaStream_t s) {
     const int nw = b.filter_warps > 0 ? b.filter_warps : lbi_filter_warps(b.n, b.w, b.S, b.seg_len, P);
-    const size_t smem = lbi_filter_smem(b.S, b.seg_len, nw);
+    const size_t smem = lbi_filter_smem(b.n, b.S, b.seg_len, nw);
     const int nsegs = b.nseg / nw;
     const dim3 grid(b.Q, (nsegs + b.seg_per_cta - 1) / b.seg_per_cta);
     cudaFuncSetAttribute(k_lbi_filter<P, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
