@@ -257,7 +257,8 @@ BatchLayout layout_batch(Carve &cv, int64_t Q, int64_t total, int64_t gout, int 
     BatchLayout L{};
     L.staged = cv.take<float>((size_t)std::max<int64_t>(total, 1));
     L.map = cv.take<QMap>((size_t)std::max<int64_t>(Q, 1));
-    L.grouped = cv.take<float>((size_t)std::max<int64_t>(total, 1));
+    // each group's queries start on a 16-byte boundary (vector loads)
+    L.grouped = cv.take<float>((size_t)std::max<int64_t>(total + 4 * (int64_t)groups.size(), 1));
     L.gidx = cv.take<int64_t>((size_t)std::max<int64_t>(gout, 1));
     L.gdist = cv.take<float>((size_t)std::max<int64_t>(gout, 1));
     L.oidx = cv.take<int64_t>((size_t)std::max<int64_t>(Q * k_stride, 1));
@@ -342,6 +343,7 @@ dtw_status prepare_batch(dtw_index *ix, int64_t Q, const int32_t *q_len, const i
         gr.qn = (int)gr.members.size();
         gr.t = tuning_for(ix, bk.n, gr.w, gr.k);
         gr.pl = plan_for(ix, gr.bucket, gr.w, gr.k, per_query ? 1 : gr.qn, gr.t);
+        qdst = (qdst + 3) & ~int64_t(3);
         gr.qoff = qdst;
         gr.ooff = gout;
         qdst += (int64_t)gr.qn * bk.n;

@@ -93,6 +93,9 @@ __device__ __forceinline__ void cp_async4(void *smem, const void *gmem, bool pre
     int sz = pred ? 4 : 0;
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gmem), "r"(sz));
 }
+__device__ __forceinline__ void cp_async16_at(unsigned sa, const void *gmem) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
@@ -859,11 +862,27 @@ constexpr int env_ring_floats() {
 // when the run computes LB_Improved (b.lbi_inline); x only when the matrix
 // does not already hold LB_Keogh (need_x).  Elements past the series are
 // zero-filled (their terms are then 0), their source clamped to the row start.
-template <int MT>
+//
+// FAST: rows of exactly 32 MT elements with 16-byte pieces, x and the
+// envelope rows all needed (the common case, specialised at compile time:
+// no predicates and no clamped sources).
+template <int MT, bool FAST>
 __device__ __forceinline__ void env_issue(float *ring, int st, const CascadeBufs &b, int c, bool vec, bool need_x) {
     const int lane = threadIdx.x & 31;
     const int64_t row = (int64_t)c * b.n;
     float *stage = ring + st * 3 * 32 * MT;
+    if constexpr (FAST) {
+        static_assert(MT >= 4, "16-byte pieces");
+        const unsigned sa = (unsigned)__cvta_generic_to_shared(stage) + 16u * lane;
+        const float *s0 = b.db + row + 4 * lane, *s1 = b.XU + row + 4 * lane, *s2 = b.XL + row + 4 * lane;
+#pragma unroll
+        for (int j = 0; j < MT / 4; ++j) {
+            cp_async16_at(sa + 512u * j, s0 + 128 * j);
+            cp_async16_at(sa + 128u * MT + 512u * j, s1 + 128 * j);
+            cp_async16_at(sa + 256u * MT + 512u * j, s2 + 128 * j);
+        }
+        return;
+    }
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
         if (r == 0 && !need_x) continue;
@@ -916,14 +935,31 @@ __device__ __forceinline__ void env_read(EnvRows<MT> &rw, const float *ring, int
     }
 }
 
+__device__ __forceinline__ float4 ldg4(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
+
+template <int P>
+__device__ __forceinline__ float acc_dist4(float acc, float4 v, float4 lo, float4 hi) {
+    acc = acc_dist<P>(acc, v.x, lo.x, hi.x);
+    acc = acc_dist<P>(acc, v.y, lo.y, hi.y);
+    acc = acc_dist<P>(acc, v.z, lo.z, hi.z);
+    return acc_dist<P>(acc, v.w, lo.w, hi.w);
+}
+__device__ __forceinline__ float4 min4(float4 a, float4 b) {
+    return make_float4(fminf(a.x, b.x), fminf(a.y, b.y), fminf(a.z, b.z), fminf(a.w, b.w));
+}
+__device__ __forceinline__ float4 max4(float4 a, float4 b) {
+    return make_float4(fmaxf(a.x, b.x), fmaxf(a.y, b.y), fmaxf(a.z, b.z), fmaxf(a.w, b.w));
+}
+
 // LB_Improved^p of the pair (q, c), or LB_Keogh^p alone when that exceeds thr
 // or !do_lbi.  known >= 0: LB_Keogh^p already computed (the first sum is not
 // formed again).  *lbk gets LB_Keogh^p.  MT > 0: r holds this lane's chunks;
-// MT == 0: lane l takes indices l, l + 32, ... (coalesced loads).
+// MT == 0: lane l takes the 16-byte pieces l, l + 32, ... (vec: n % 4 == 0
+// and aligned rows) or the indices l, l + 32, ... (coalesced loads).
 template <int P, int MT>
 __device__ __forceinline__ float warp_lbi_env(const CascadeBufs &b, int q, int c, const EnvQuery<MT> &Qv,
                                               const EnvRows<MT> &r, float known, float thr, bool do_lbi,
-                                              float *lbk) {
+                                              float *lbk, bool vec) {
     const int lane = threadIdx.x & 31;
     const int n = b.n;
     float first = known;
@@ -935,8 +971,13 @@ __device__ __forceinline__ float warp_lbi_env(const CascadeBufs &b, int q, int c
         } else {
             const float *x = b.db + (int64_t)c * n;
             const float *U = b.U + (int64_t)q * n, *L = b.L + (int64_t)q * n;
+            if (vec) {
+#pragma unroll 2
+                for (int i = 4 * lane; i < n; i += 128) acc = acc_dist4<P>(acc, ldg4(x + i), ldg4(L + i), ldg4(U + i));
+            } else {
 #pragma unroll 4
-            for (int i = lane; i < n; i += 32) acc = acc_dist<P>(acc, __ldg(x + i), __ldg(L + i), __ldg(U + i));
+                for (int i = lane; i < n; i += 32) acc = acc_dist<P>(acc, __ldg(x + i), __ldg(L + i), __ldg(U + i));
+            }
         }
         first = warp_sum(acc);
     }
@@ -951,18 +992,27 @@ __device__ __forceinline__ float warp_lbi_env(const CascadeBufs &b, int q, int c
         const int64_t oc = (int64_t)c * n, oq = (int64_t)q * n;
         const float *xu = b.XU + oc, *xl = b.XL + oc;
         const float *y = b.queries + oq, *ul = b.UL + oq, *lu = b.LU + oq;
+        if (vec) {
+#pragma unroll 2
+            for (int i = 4 * lane; i < n; i += 128)
+                acc = acc_dist4<P>(acc, ldg4(y + i), min4(ldg4(xl + i), ldg4(lu + i)), max4(ldg4(xu + i), ldg4(ul + i)));
+        } else {
 #pragma unroll 4
-        for (int i = lane; i < n; i += 32)
-            acc = acc_dist<P>(acc, __ldg(y + i), fminf(__ldg(xl + i), __ldg(lu + i)),
-                              fmaxf(__ldg(xu + i), __ldg(ul + i)));
+            for (int i = lane; i < n; i += 32)
+                acc = acc_dist<P>(acc, __ldg(y + i), fminf(__ldg(xl + i), __ldg(lu + i)),
+                                  fmaxf(__ldg(xu + i), __ldg(ul + i)));
+        }
     }
     // one reduction of the full value keeps the sum's rounding independent
     // of where the first sum came from
     return warp_sum(acc + (lane == 0 ? first : 0.0f));
 }
 
-template <int P, int MT>
-__global__ void __launch_bounds__(256, 2) k_lbi_filter(CascadeBufs b, bool vec) {
+template <int P, int MT, bool FAST>
+__global__ void __launch_bounds__(256, 2) k_lbi_filter(CascadeBufs b, bool vec_arg) {
+    // FAST (see env_issue): 16-byte rows of exactly 32 MT elements, the
+    // pre-filter matrix and LB_Improved on
+    const bool vec = FAST ? true : vec_arg;
     extern __shared__ __align__(16) unsigned char smraw[];
     const int nw = blockDim.x >> 5;
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -987,25 +1037,28 @@ __global__ void __launch_bounds__(256, 2) k_lbi_filter(CascadeBufs b, bool vec) 
     // sum_j D_j^p (for p = 2 the bound is that sum over max_j |C_j|)
     const float thr_m = b.summary ? thr * b.summary_scale : thr;
     const int nsegs = b.nseg / nw;
-    const bool lbk_done = !b.summary;  // the survivors carry LB_Keogh^p
+    const bool lbk_done = FAST ? false : !b.summary;  // the survivors carry LB_Keogh^p
+    const bool lbi_on = FAST ? true : b.lbi_inline != 0;
+    const float *lbrow = b.lb + (int64_t)q * b.N;
+    const int stride = nw * 32;
     for (int sj = 0; sj < b.seg_per_cta; ++sj) {
     const int sg = blockIdx.y * b.seg_per_cta + sj;
     if (sg >= nsegs) break;
     const int c0 = sg * b.seg_len;
     const int c1 = min(b.N, c0 + b.seg_len);
-    const float *lbrow = b.lb + (int64_t)q * b.N;
     // phase 1: matrix test over this warp's share of the segment; the
     // survivors are compacted into the warp's buffer (seeds hold NaN in the
     // matrix and never pass).  Eight loads per lane are issued before any is
     // tested, so that the scan waits on memory once per eight rows of 32.
+    // The matrix is read once: its loads are marked evict-first, so that
+    // the segment's rows, which every query's CTA reads, stay in L2.
     int cnt1 = 0;
-    const int stride = nw * 32;
     for (int base0 = c0 + wid * 32; base0 < c1; base0 += 8 * stride) {
         float v[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
             const int c = base0 + u * stride + lane;
-            v[u] = c < c1 ? lbrow[c] : kInf;
+            v[u] = c < c1 ? __ldcs(lbrow + c) : kInf;
         }
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
@@ -1028,12 +1081,12 @@ __global__ void __launch_bounds__(256, 2) k_lbi_filter(CascadeBufs b, bool vec) 
     // kEnvStages - 1 candidates in flight (MT > 0) while the current one is
     // processed; survivors are kept in place (write index <= read index)
     int cnt = 0;
-    if (b.lbi_inline || !lbk_done) {
+    if (lbi_on || !lbk_done) {
         const bool need_x = !lbk_done;
         if constexpr (MT > 0) {
 #pragma unroll
             for (int e = 0; e < kEnvStages - 1; ++e) {
-                if (e < cnt1) env_issue<MT>(ring, e, b, surv_c[e], vec, need_x);
+                if (e < cnt1) env_issue<MT, FAST>(ring, e, b, surv_c[e], vec, need_x);
                 cp_async_commit();
             }
         }
@@ -1044,13 +1097,13 @@ __global__ void __launch_bounds__(256, 2) k_lbi_filter(CascadeBufs b, bool vec) 
             if constexpr (MT > 0) {
                 // the stage refilled here was read (and used) by pair e - 1
                 const int ahead = e + kEnvStages - 1;
-                if (ahead < cnt1) env_issue<MT>(ring, ahead % kEnvStages, b, surv_c[ahead], vec, need_x);
+                if (ahead < cnt1) env_issue<MT, FAST>(ring, ahead % kEnvStages, b, surv_c[ahead], vec, need_x);
                 cp_async_commit();
                 cp_async_wait<kEnvStages - 1>();
-                env_read<MT>(cur, ring, e % kEnvStages, vec, need_x, b.lbi_inline != 0);
+                env_read<MT>(cur, ring, e % kEnvStages, vec, need_x, lbi_on);
             }
             float lbk;
-            const float v = warp_lbi_env<P, MT>(b, q, cc, Qv, cur, known, thr, b.lbi_inline != 0, &lbk);
+            const float v = warp_lbi_env<P, MT>(b, q, cc, Qv, cur, known, thr, lbi_on, &lbk, vec);
             if (!lbk_done) kp += (lbk <= thr) ? 1 : 0;
             if (v <= thr) {
                 if (lane == 0) {
@@ -1123,8 +1176,10 @@ static void lbi_filter_go(const CascadeBufs &b, bool vec, cudaStream_t s) {
     const size_t smem = lbi_filter_smem(b.n, b.S, b.seg_len, nw);
     const int nsegs = b.nseg / nw;
     const dim3 grid(b.Q, (nsegs + b.seg_per_cta - 1) / b.seg_per_cta);
-    cudaFuncSetAttribute(k_lbi_filter<P, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_lbi_filter<P, MT><<<grid, nw * 32, smem, s>>>(b, vec);
+    const bool fast = MT >= 4 && vec && b.n == 32 * MT && b.summary && b.lbi_inline;
+    auto kern = fast ? k_lbi_filter<P, MT, (MT >= 4)> : k_lbi_filter<P, MT, false>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kern<<<grid, nw * 32, smem, s>>>(b, vec);
 }
 
 template <int P>
@@ -1143,8 +1198,9 @@ cudaError_t launch_lbi_filter(const CascadeBufs &b, cudaStream_t s) {
     if (b.lbi_inline && (b.XU == nullptr || b.XL == nullptr || b.UL == nullptr || b.LU == nullptr))
         return cudaErrorInvalidValue;
     // rows start on 16-byte boundaries when n % 4 == 0 and the bases do (the
-    // envelope rows always do)
-    const bool vec = (b.n % 4 == 0) && ((reinterpret_cast<uintptr_t>(b.db) & 15) == 0);
+    // envelope rows and the query envelopes always do)
+    const bool vec = (b.n % 4 == 0) && ((reinterpret_cast<uintptr_t>(b.db) & 15) == 0) &&
+                     ((reinterpret_cast<uintptr_t>(b.queries) & 15) == 0);
     if (b.p == 1) lbi_filter_dispatch<1>(b, vec, s);
     else lbi_filter_dispatch<2>(b, vec, s);
     return cudaGetLastError();
