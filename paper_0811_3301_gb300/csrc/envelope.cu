@@ -87,11 +87,69 @@ k_envelope(const float *__restrict__ y, int n, int w, float *__restrict__ U, flo
     envelope_windows(ax, an, bx, bn, n, w, UL + row * (int64_t)n, LU + row * (int64_t)n);
 }
 
+// Many short series (the database rows, once per call): one warp per series,
+// the same doubling table in the warp's own shared memory, so that a level
+// costs a warp barrier instead of a block barrier.
+constexpr int kEnvWarpMaxN = 1024;
+constexpr int kEnvWarps = 8;
+
+__global__ void __launch_bounds__(kEnvWarps * 32)
+k_envelope_rows(const float *__restrict__ y, int64_t count, int n, int w, float *__restrict__ U,
+                float *__restrict__ L) {
+    extern __shared__ float sm[];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t row = (int64_t)blockIdx.x * kEnvWarps + wid;
+    if (row >= count) return;
+    float *ax = sm + (size_t)wid * 4 * n, *an = ax + n, *bx = ax + 2 * n, *bn = ax + 3 * n;
+    const float *yr = y + row * (int64_t)n;
+    for (int i = lane; i < n; i += 32) {
+        const float v = yr[i];
+        ax[i] = v;
+        an[i] = v;
+    }
+    __syncwarp();
+    const int kmax = floor_log2(min(2 * w + 1, n));
+    for (int j = 1; j <= kmax; ++j) {
+        const int h = 1 << (j - 1);
+        for (int i = lane; i < n; i += 32) {
+            const int i2 = min(i + h, n - 1);
+            bx[i] = fmaxf(ax[i], ax[i2]);
+            bn[i] = fminf(an[i], an[i2]);
+        }
+        __syncwarp();
+        float *t;
+        t = ax; ax = bx; bx = t;
+        t = an; an = bn; bn = t;
+    }
+    float *Ur = U + row * (int64_t)n, *Lr = L + row * (int64_t)n;
+    for (int i = lane; i < n; i += 32) {
+        const int a = max(0, i - w), b = min(n - 1, i + w);
+        const int k = floor_log2(b - a + 1);
+        const float *tx = (k == kmax) ? ax : bx;
+        const float *tn = (k == kmax) ? an : bn;
+        const int b2 = b - (1 << k) + 1;
+        Ur[i] = fmaxf(tx[a], tx[b2]);
+        Lr[i] = fminf(tn[a], tn[b2]);
+    }
+}
+
 cudaError_t launch_envelope(const float *y, int64_t count, int n, int w, float *U, float *L,
                             QueryCopies qc, int copies_padl, cudaStream_t s, float *UL, float *LU) {
     if (count <= 0) return cudaSuccess;
     if ((UL == nullptr) != (LU == nullptr)) return cudaErrorInvalidValue;
     w = min(w, n - 1);
+    if (qc.data == nullptr && UL == nullptr && n <= kEnvWarpMaxN && count >= 4096) {
+        const size_t smem = (size_t)kEnvWarps * 4 * n * sizeof(float);
+        static bool rows_attr = false;
+        if (!rows_attr) {
+            cudaFuncSetAttribute(k_envelope_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kEnvWarps * 4 * kEnvWarpMaxN * (int)sizeof(float));
+            rows_attr = true;
+        }
+        const int64_t blocks = (count + kEnvWarps - 1) / kEnvWarps;
+        k_envelope_rows<<<(unsigned)blocks, kEnvWarps * 32, smem, s>>>(y, count, n, w, U, L);
+        return cudaGetLastError();
+    }
     size_t smem = 4 * (size_t)n * sizeof(float);
     static bool attr_set = false;
     if (!attr_set) {
