@@ -315,9 +315,10 @@ __global__ void __launch_bounds__(256) k_gather(CascadeBufs b) {
                 const float lb = b.lbi_u[src + e];
                 const int r = atomicAdd(&hist[order_bin(lb, scale)], 1);
                 const int64_t dst = r < lead ? out0 + r : outb + (r - lead);
-                b.pairs[dst] = b.pairs_u[src + e];
+                const Pair pr = b.pairs_u[src + e];
+                b.pairs[dst] = pr;
                 b.pair_lbi[dst] = lb;
-                b.pair_res[dst] = kInf;
+                b.pair_res[dst] = b.lb[(int64_t)q * b.N + pr.c];  // LB_Keogh^p (see CascadeBufs)
             }
         }
         return;
@@ -343,9 +344,10 @@ __global__ void __launch_bounds__(256) k_gather(CascadeBufs b) {
         if (sg < b.nseg && c > 0) {
             const int64_t src = b.seg_start[(int64_t)q * b.nseg + sg];
             for (int e = 0; e < c; ++e) {
-                b.pairs[out0 + excl + e] = b.pairs_u[src + e];
+                const Pair pr = b.pairs_u[src + e];
+                b.pairs[out0 + excl + e] = pr;
                 b.pair_lbi[out0 + excl + e] = b.lbi_u[src + e];
-                b.pair_res[out0 + excl + e] = kInf;
+                b.pair_res[out0 + excl + e] = b.lb[(int64_t)q * b.N + pr.c];  // LB_Keogh^p
             }
         }
         __syncthreads();

@@ -342,6 +342,9 @@ cudaError_t cascade_run(const CascadePlan &pl, const CascadeWs &l, const float *
         jp.cursor = cur_pairs;
         jp.counters = counters;
         jp.lanes = use_lanes(pl, jp.npairs, true);
+        // the grouped pairs' result slots hold their LB_Keogh^p (k_gather)
+        jp.tU = jp.abandon ? l.U : nullptr;
+        jp.tL = jp.abandon ? l.L : nullptr;
         {
             StageTimer tm(DTW_STAGE_DTW, s);
             RUN_TRY(launch_dtw_any(jp, pl.g, s));

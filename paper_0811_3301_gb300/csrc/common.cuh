@@ -155,7 +155,9 @@ struct CascadeBufs {
     // survivors of the bound stages, as written by the filter (unordered) ...
     Pair *pairs_u;
     float *lbi_u;
-    // ... and grouped by query.  With order_first = F > 0 each query's pairs
+    // ... and grouped by query, each pair's result slot holding its
+    // LB_Keogh^p (from the matrix, where the filter leaves it for its
+    // survivors) until the DTW stage writes the result.  With order_first = F > 0 each query's pairs
     // are ordered by ascending bound (to 1/256 of its threshold) and split:
     // its first min(F, qcount[q]) pairs at qstart[q] in a leading region that
     // holds every query's first pairs, the rest at qstart_b[q] after it.  With
@@ -220,6 +222,10 @@ struct DtwJob {
     unsigned long long *cursor;    // chunk cursor (zeroed by the caller)
     unsigned long long *counters;  // nullable
     int lanes;                // 1: warp path (lane groups share a pair's band); 2: with 16-lane groups
+    // Cumulative LB_Keogh in the abandon test (thread-per-pair kernel): res
+    // holds each listed pair's LB_Keogh^p on entry, tU/tL [Q][n] the query
+    // envelopes.  nullptr: the row minimum alone.
+    const float *tU, *tL;
 };
 
 

@@ -264,6 +264,15 @@ k_dtw_reg4(DtwJob j, int e, int wl, bool xvec) {
             for (int k = 0; k < C; ++k) D[k] = sel_eq(k, wl, 0.0f, kInf);  // row -1: D(-1,-1) = 0
             bool abandoned = false;
             int rows = n;
+            // Cumulative bound: after rows 0..i every warping path still
+            // visits each later row k, at a cost of at least
+            // d(x_k, [L_k, U_k])^p, so DTW^p >= (minimum of row i) + the
+            // LB_Keogh^p terms of rows > i = LB_Keogh^p - those of rows <= i.
+            const bool tail = j.tU != nullptr && j.abandon;
+            const float lbk_total = tail ? j.res[pi] : 0.0f;
+            const float *tu = tail ? j.tU + (int64_t)q * n : nullptr;
+            const float *tl = tail ? j.tL + (int64_t)q * n : nullptr;
+            float lbk_pre = 0.0f;
             for (int i = 0; i < n; i += 4) {
                 float yw[C + 4];
                 const float4 *yb = reinterpret_cast<const float4 *>(y0 + i);
@@ -301,11 +310,33 @@ k_dtw_reg4(DtwJob j, int e, int wl, bool xvec) {
                     if (i + 2 < n) dtw_row_win<C, P, 2>(D, x4.z, yw, e);
                     if (i + 3 < n) dtw_row_win<C, P, 3>(D, x4.w, yw, e);
                 }
+                if (tail && i + 4 < n) {
+                    float4 u4, l4;
+                    if (xvec) {
+                        u4 = __ldg(reinterpret_cast<const float4 *>(tu + i));
+                        l4 = __ldg(reinterpret_cast<const float4 *>(tl + i));
+                    } else {
+                        u4 = make_float4(__ldg(tu + i), __ldg(tu + i + 1), __ldg(tu + i + 2), __ldg(tu + i + 3));
+                        l4 = make_float4(__ldg(tl + i), __ldg(tl + i + 1), __ldg(tl + i + 2), __ldg(tl + i + 3));
+                    }
+                    lbk_pre = acc_dist<P>(lbk_pre, x4.x, l4.x, u4.x);
+                    lbk_pre = acc_dist<P>(lbk_pre, x4.y, l4.y, u4.y);
+                    lbk_pre = acc_dist<P>(lbk_pre, x4.z, l4.z, u4.z);
+                    lbk_pre = acc_dist<P>(lbk_pre, x4.w, l4.w, u4.w);
+                }
                 if (j.abandon && (i & 4) && i + 4 < n) {
                     float mn = D[0];
 #pragma unroll
                     for (int k = 1; k < C; ++k) mn = fminf(mn, D[k]);
                     if (j.bsf) thr = load_threshold(j.bsf + q);
+                    if (tail) {
+                        // fp32: the two LB_Keogh sums (different orders) each
+                        // carry at most n u relative error, and the path's
+                        // remaining additions at most (2n - 1) u; c covers both
+                        const float c = (float)(2 * n + 2) * 5.9604645e-8f;
+                        const float rest = fmaxf(0.0f, lbk_total - lbk_pre - c * lbk_total);
+                        mn = fmaxf(mn, (mn + rest) * (1.0f - c));
+                    }
                     if (mn > thr) {
                         abandoned = true;
                         rows = i + 4;

@@ -1109,6 +1109,9 @@ __global__ void __launch_bounds__(256, 2) k_lbi_filter(CascadeBufs b, bool vec_a
                 if (lane == 0) {
                     surv_c[cnt] = cc;
                     surv_v[cnt] = v;
+                    // the survivor's matrix entry becomes its LB_Keogh^p (the
+                    // DTW stage's cumulative bound starts from it)
+                    if (!lbk_done) b.lb[(int64_t)q * b.N + cc] = lbk;
                 }
                 ++cnt;
             }
