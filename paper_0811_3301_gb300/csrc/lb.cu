@@ -962,6 +962,28 @@ __device__ __forceinline__ float warp_lbi_env(const CascadeBufs &b, int q, int c
                                               float *lbk, bool vec) {
     const int lane = threadIdx.x & 31;
     const int n = b.n;
+    if constexpr (MT > 0) {
+        if (known < 0.0f && do_lbi) {
+            // Registers hold both rows' chunks: form both sums, then reduce
+            // them together, so that their shuffle chains overlap (one
+            // reduction's latency per pair instead of two in a row).  The
+            // second sum of a pair that fails LB_Keogh is formed for nothing
+            // (a few percent of the pairs).
+            float a1 = 0.0f, a2 = 0.0f;
+#pragma unroll
+            for (int t = 0; t < MT; ++t) {
+                a1 = acc_dist<P>(a1, r.x.v[t], Qv.l[t], Qv.u[t]);
+                a2 = acc_dist<P>(a2, Qv.y[t], fminf(r.xl.v[t], Qv.lu[t]), fmaxf(r.xu.v[t], Qv.ul[t]));
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+                a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+            }
+            *lbk = a1;
+            return a1 > thr ? a1 : a1 + a2;
+        }
+    }
     float first = known;
     if (known < 0.0f) {
         float acc = 0.0f;
