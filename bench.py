@@ -71,7 +71,8 @@ def parse():
                     "3 main stage on two 16-lane groups per warp")
     ap.add_argument("--no-p2", action="store_true", help="skip the DTW_2 side measurement")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU baseline sample")
-    ap.add_argument("--workload", choices=["retrieval", "batched", "serve", "triangle"], default="retrieval",
+    ap.add_argument("--workload", choices=["retrieval", "batched", "serve", "triangle", "classify"],
+                    default="retrieval",
                     help="retrieval: one length, one knn_search per step (default); batched: mixed-length "
                          "batches against length buckets through the index")
     ap.add_argument("--bucket-N", type=int, default=20_000, help="batched: series per length bucket")
@@ -85,6 +86,7 @@ def parse():
                     help="serve: database size factor (1.0: 1,000,000 x 256 + 200,000 x 1024)")
     ap.add_argument("--serve-secondary", action="store_true",
                     help="serve: also run with small buckets for lengths 128, 512 and 2048")
+    ap.add_argument("--classify-dbs", type=int, default=50, help="classify: databases per instance count")
     return ap.parse_args()
 
 
@@ -730,6 +732,86 @@ def run_triangle(a):
     }
 
 
+def classify_labels(a, m, db_i, tests):
+    """Database labels (m per class) and test labels (uniform) of database db_i."""
+    g = np.random.default_rng([a.seed, 7000 + m, db_i])
+    return np.repeat(np.arange(synth.SHAPE_CLASSES), m), g.integers(0, synth.SHAPE_CLASSES, size=tests)
+
+
+def run_classify(a):
+    """App. C: 1-NN classification accuracy under DTW_p, p in {1, 2, 4,
+    infinity}, w = n/10, on the shape-like classes (plateau, rising ramp,
+    falling ramp, sum of sinusoids; n = 128, the length of the paper's first
+    data set) standing in for the paper's synthetic data sets: for m instances
+    per class, `classify_dbs` databases of 4 m series, each with 500 new test
+    series of random class; a test succeeds when its nearest neighbour (lowest
+    index on ties) has its class.  All (test, database series) pairs of all
+    databases go through dtw_band in one launch per (m, p); the oracle's 1-NN
+    labels are checked on a sample."""
+    import torch
+
+    from paper_0811_3301_gb300 import build
+
+    build.build()
+    import oracle
+
+    from paper_0811_3301_gb300 import api
+
+    n, tests, ms_list = 128, 500, (1, 2, 3, 5, 9)
+    w = n // 10
+    D = a.classify_dbs
+    ps = (1, 2, 4, math.inf)
+    acc = {}
+    rate_pairs, rate_ms = 0, 0.0
+    agree, checked = 0, 0
+    for m in ms_list:
+        k = synth.SHAPE_CLASSES * m
+        dbs, tsts, dlab, tlab = [], [], [], []
+        for i in range(D):
+            ld, lt = classify_labels(a, m, i, tests)
+            dbs.append(synth.shape_classes(ld, n, seed=a.seed + 100 * m + i))
+            tsts.append(synth.shape_classes(lt, n, seed=a.seed + 100 * m + i, stream=synth.STREAM_QUERY))
+            dlab.append(ld)
+            tlab.append(lt)
+        db = torch.from_numpy(np.stack(dbs)).cuda()     # [D][k][n]
+        ts = torch.from_numpy(np.stack(tsts)).cuda()    # [D][tests][n]
+        X = db[:, None, :, :].expand(D, tests, k, n).reshape(-1, n).contiguous()
+        Y = ts[:, :, None, :].expand(D, tests, k, n).reshape(-1, n).contiguous()
+        dl = np.stack(dlab)
+        tl = np.stack(tlab)
+        for p in ps:
+            api.dtw_band(X, Y, w, p)  # warm-up
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            d = api.dtw_band(X, Y, w, p)
+            e1.record()
+            torch.cuda.synchronize()
+            rate_ms += e0.elapsed_time(e1)
+            rate_pairs += X.shape[0]
+            nn = torch.argmin(d.view(D, tests, k), dim=2).cpu().numpy()  # first index on ties
+            pred = np.take_along_axis(dl, nn, axis=1)
+            acc.setdefault(str(m), {})["inf" if p == math.inf else str(p)] = float((pred == tl).mean())
+            # the oracle's nearest neighbour on a sample of tests of database 0
+            op = 0 if p == math.inf else p
+            for t in range(0, tests, 50):
+                oi, _ = oracle.knn_bruteforce(dbs[0], tsts[0][t][None, :], w, op, 1)
+                agree += int(oi[0, 0] == nn[0, t])
+                checked += 1
+    return {
+        "metric": "1-NN classification accuracy under DTW_p (App. C), with the DTW pair rate",
+        "value": rate_pairs / (rate_ms / 1e3), "unit": "DTW pairs/s", "n_gpus": 1, "steps": 1, "warmup": 1,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded shape-like series, 4 classes)",
+        "config": {"workload": "App. C: n = %d, w = %d, %d databases per m, %d tests each, m in %s instances "
+                               "per class, p in {1, 2, 4, inf}" % (n, w, D, tests, list(ms_list)),
+                   "paper": "DTW_1 classifies best, DTW_2 a close second, DTW_4 lower; DTW_inf is competitive "
+                            "only with one or two instances per class"},
+        "accuracy": acc,
+        "oracle_agreement": {"checked": checked, "equal": agree},
+    }
+
+
 def run_reference(a):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -771,6 +853,8 @@ def main():
         out = run_serve(a)
     elif a.workload == "triangle":
         out = run_triangle(a)
+    elif a.workload == "classify":
+        out = run_classify(a)
     else:
         out = run_ours(a)
     if out is not None:

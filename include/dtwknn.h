@@ -10,7 +10,9 @@
  *    1-based, Sec. 2).
  *  - n >= 1 and n <= DTW_MAX_N.  w >= 0 is the locality constraint of
  *    Sec. 4: x_i and y_j may be aligned only if |i - j| <= w; any w >= n - 1
- *    means no constraint.  p is 1 or 2 (the l_p norm of Sec. 2).
+ *    means no constraint.  p is 1 or 2 (the l_p norm of Sec. 2); the DTW
+ *    entry points dtw_band and dtw_band_noalloc also take p = 4 and
+ *    p = infinity (DTW_P_INF), the other measures of App. C.
  *  - Distances and bounds are returned with the p-th root taken, as the
  *    paper defines them (DTW_p = q_{1,1}^(1/p), Sec. 4).  Internally the
  *    kernels compare in power space.
@@ -38,6 +40,7 @@ extern "C" {
 
 #define DTW_MAX_N 4096 /* longest supported series */
 #define DTW_MAX_K 128  /* largest supported neighbour count */
+#define DTW_P_INF 0    /* p = infinity: DTW_inf, the largest cost along the best path (Sec. 4) */
 
 typedef enum {
     DTW_OK = 0,
@@ -128,10 +131,13 @@ dtw_status lb_improved(const float *cand, int64_t N, const float *q, const float
 /*
  * Band-constrained DTW_p (Sec. 4 recursion) of the pairs (x[c], y) for
  * c < N: x is [N][n]; y is one series [n] when y_stride == 0, or [N][n] when
- * y_stride == n (pair c uses y + c * n).  If threshold is finite, a pair whose
- * DTW_p provably exceeds it (the minimum of a row of the dynamic program is
- * above threshold^p, an exact test since costs are non-negative) is abandoned
- * and gets +INF; +INF disables abandoning.  out is [N] (root taken).
+ * y_stride == n (pair c uses y + c * n).  p is 1, 2, 4 or DTW_P_INF; for
+ * DTW_P_INF a cell holds max(|x_i - y_j|, min(predecessors)) (Sec. 4) and the
+ * result is DTW_inf.  If threshold is finite, a pair whose DTW_p provably
+ * exceeds it (the minimum of a row of the dynamic program is above
+ * threshold^p, or threshold for DTW_inf: an exact test since costs are
+ * non-negative) is abandoned and gets +INF; +INF disables abandoning.  out is
+ * [N] (root taken).
  */
 dtw_status dtw_band(const float *x, const float *y, int64_t N, int32_t y_stride,
                     int32_t n, int32_t w, int32_t p, float threshold, float *out,

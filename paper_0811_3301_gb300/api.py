@@ -102,11 +102,19 @@ def lb_improved(cand: torch.Tensor, q: torch.Tensor, U: torch.Tensor, L: torch.T
     return out
 
 
-def dtw_band(x: torch.Tensor, y: torch.Tensor, w: int, p: int, threshold: float = math.inf,
+def _p_code(p) -> int:
+    """The C ABI's code for p: 1, 2, 4, or DTW_P_INF (0) for p = infinity."""
+    if p in (math.inf, "inf"):
+        return 0
+    return int(p)
+
+
+def dtw_band(x: torch.Tensor, y: torch.Tensor, w: int, p, threshold: float = math.inf,
              out: torch.Tensor | None = None):
     """DTW_p with band w of the rows of x [N, n] against y ([n] shared, or [N, n] per pair), Sec. 4.
 
-    With a finite threshold, pairs whose DTW_p exceeds it return +inf.
+    p is 1, 2, 4 or math.inf (DTW_inf).  With a finite threshold, pairs whose
+    DTW_p exceeds it return +inf.
     """
     x = _cuda_f32(x, "x")
     y = _cuda_f32(y, "y")
@@ -120,7 +128,7 @@ def dtw_band(x: torch.Tensor, y: torch.Tensor, w: int, p: int, threshold: float 
             raise ValueError("per-pair y must have the shape of x")
         stride = n
     out = torch.empty(x.shape[0], device=x.device, dtype=torch.float32) if out is None else out
-    N.check(N.lib.dtw_band(_ptr(x), _ptr(y), x.shape[0], stride, n, int(w), int(p), float(threshold),
+    N.check(N.lib.dtw_band(_ptr(x), _ptr(y), x.shape[0], stride, n, int(w), _p_code(p), float(threshold),
                            _ptr(out), _stream()))
     return out
 

@@ -102,6 +102,20 @@ static dtw_status check_common(int32_t n, int32_t w, int32_t p) {
     return DTW_OK;
 }
 
+// dtw_band takes p in {1, 2, 4} or DTW_P_INF (0); the bounds and the cascade take p in {1, 2}.
+static dtw_status check_dtw_p(int32_t n, int32_t w, int32_t p) {
+    if (p == 4 || p == DTW_P_INF) return check_common(n, w, 1);
+    return check_common(n, w, p);
+}
+
+// A threshold on DTW_p in the units the kernels compare (DTW_p^p; DTW_inf itself).
+static float threshold_power(float t, int32_t p) {
+    if (std::isinf(t)) return INFINITY;
+    if (p == 2) return t * t;
+    if (p == 4) return (t * t) * (t * t);
+    return t;
+}
+
 static dtw_status check_band(int32_t n, int32_t w) {
     int we = w < n - 1 ? w : n - 1;
     if (2 * we + 1 > 2048)
@@ -110,7 +124,7 @@ static dtw_status check_band(int32_t n, int32_t w) {
 }
 
 static cudaError_t launch_dtw(const DtwJob &j, const DtwGeom &g, cudaStream_t s) {
-    return j.p == 1 ? launch_dtw_p1(j, g, s) : launch_dtw_p2(j, g, s);
+    return launch_dtw_by_p(j, g, s);
 }
 
 }  // namespace dtwk
@@ -190,7 +204,7 @@ dtw_status lb_improved(const float *cand, int64_t N, const float *q, const float
 dtw_status dtw_band(const float *x, const float *y, int64_t N, int32_t y_stride, int32_t n, int32_t w,
                     int32_t p, float threshold, float *out, void *stream) {
     g_err[0] = 0;
-    dtw_status st = check_common(n, w, p);
+    dtw_status st = check_dtw_p(n, w, p);
     if (st != DTW_OK) return st;
     if ((st = check_band(n, w)) != DTW_OK) return st;
     if (N < 0 || N > INT32_MAX) return fail(DTW_ERR_INVALID_ARG, "N=%lld out of range", (long long)N);
@@ -228,7 +242,7 @@ dtw_status dtw_band(const float *x, const float *y, int64_t N, int32_t y_stride,
     j.pairs = nullptr;
     j.npairs = N;
     j.per_pair_y = y_stride ? 1 : 0;
-    j.fixed_thr = std::isinf(threshold) ? INFINITY : (p == 1 ? threshold : threshold * threshold);
+    j.fixed_thr = threshold_power(threshold, p);
     j.abandon = std::isinf(threshold) ? 0 : 1;
     j.res = out;
     j.root_out = 1;

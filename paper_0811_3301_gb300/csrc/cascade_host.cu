@@ -92,7 +92,7 @@ struct StageTimer {
     } while (0)
 
 static cudaError_t launch_dtw_any(const DtwJob &j, const DtwGeom &g, cudaStream_t s) {
-    return j.p == 1 ? launch_dtw_p1(j, g, s) : launch_dtw_p2(j, g, s);
+    return launch_dtw_by_p(j, g, s);
 }
 
 // One warp per pair (dtw_lanes.cuh) or one thread per pair for a DTW stage of

@@ -48,8 +48,27 @@ __device__ __forceinline__ float acc_dist(float acc, float v, float lo, float hi
     return P == 1 ? acc + d : fmaf(d, d, acc);
 }
 
-// Root of a power-space value (the paper's DTW_p and LB_p carry the root).
-__device__ __forceinline__ float root_p(float v, int p) { return p == 1 ? v : sqrtf(v); }
+// Root of a power-space value (the paper's DTW_p and LB_p carry the root);
+// p = 0 stands for p = infinity, whose values carry no power.
+__device__ __forceinline__ float root_p(float v, int p) {
+    return (p == 1 || p == 0) ? v : (p == 2 ? sqrtf(v) : sqrtf(sqrtf(v)));
+}
+
+// One band cell of DTW_p (Sec. 4): the cost of (x_i, y_j) combined with the
+// best predecessor m.  P = 1, 2, 4: m + |d|^P (a sum along the path; the
+// result is DTW_P^P); P = 0 (p = infinity): max(|d|, m) (the largest cost
+// along the path).  Both never decrease m, which early abandoning relies on.
+template <int P>
+__device__ __forceinline__ float dtw_cost(float d, float m) {
+    static_assert(P == 0 || P == 1 || P == 2 || P == 4, "p in {1, 2, 4, infinity}");
+    if constexpr (P == 1) return fabsf(d) + m;
+    if constexpr (P == 2) return fmaf(d, d, m);
+    if constexpr (P == 4) {
+        const float s = d * d;
+        return fmaf(s, s, m);
+    }
+    return fmaxf(fabsf(d), m);
+}
 
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll

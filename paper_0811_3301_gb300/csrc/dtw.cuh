@@ -85,8 +85,23 @@ inline int dtw_lanes_cl(int n, int w) { return dtw_lanes_shape(n, w).cl; }
 
 cudaError_t launch_dtw_lanes_p1(const DtwJob &j, const DtwGeom &g, LanesShape ls, cudaStream_t s);
 cudaError_t launch_dtw_lanes_p2(const DtwJob &j, const DtwGeom &g, LanesShape ls, cudaStream_t s);
+cudaError_t launch_dtw_lanes_p4(const DtwJob &j, const DtwGeom &g, LanesShape ls, cudaStream_t s);
+cudaError_t launch_dtw_lanes_pinf(const DtwJob &j, const DtwGeom &g, LanesShape ls, cudaStream_t s);
 
 cudaError_t launch_dtw_p1(const DtwJob &j, const DtwGeom &g, cudaStream_t s);
 cudaError_t launch_dtw_p2(const DtwJob &j, const DtwGeom &g, cudaStream_t s);
+cudaError_t launch_dtw_p4(const DtwJob &j, const DtwGeom &g, cudaStream_t s);
+cudaError_t launch_dtw_pinf(const DtwJob &j, const DtwGeom &g, cudaStream_t s);
+
+// DTW of a job by its exponent j.p (1, 2, 4, or 0 for p = infinity).
+inline cudaError_t launch_dtw_by_p(const DtwJob &j, const DtwGeom &g, cudaStream_t s) {
+    switch (j.p) {
+        case 1: return launch_dtw_p1(j, g, s);
+        case 2: return launch_dtw_p2(j, g, s);
+        case 4: return launch_dtw_p4(j, g, s);
+        case 0: return launch_dtw_pinf(j, g, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
 
 }  // namespace dtwk

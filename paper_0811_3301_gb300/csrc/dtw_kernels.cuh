@@ -52,7 +52,7 @@ __device__ __forceinline__ void dtw_cell(float (&D)[C], float xi, float yv) {
     if constexpr (K > 0) below = D[K - 1]; else below = kInf;
     const float m = min3f(D[K], above, below);
     const float d = xi - yv;
-    D[K] = (P == 1) ? fabsf(d) + m : fmaf(d, d, m);
+    D[K] = dtw_cost<P>(d, m);
 }
 #define DTW_CELL(K, YV) dtw_cell<K, C, P>(D, xi, YV);
 
@@ -268,7 +268,7 @@ k_dtw_reg4(DtwJob j, int e, int wl, bool xvec) {
             // visits each later row k, at a cost of at least
             // d(x_k, [L_k, U_k])^p, so DTW^p >= (minimum of row i) + the
             // LB_Keogh^p terms of rows > i = LB_Keogh^p - those of rows <= i.
-            const bool tail = j.tU != nullptr && j.abandon;
+            const bool tail = (P == 1 || P == 2) && j.tU != nullptr && j.abandon;
             const float lbk_total = tail ? j.res[pi] : 0.0f;
             const float *tu = tail ? j.tU + (int64_t)q * n : nullptr;
             const float *tl = tail ? j.tL + (int64_t)q * n : nullptr;
@@ -457,7 +457,7 @@ k_dtw_wide(DtwJob j) {
                     const float below = (u > 0) ? D[(u > 0) ? u - 1 : 0] : left;
                     const float m = min3f(D[u], above, below);
                     const float df = xi - yw[u];
-                    D[u] = (P == 1) ? fabsf(df) + m : fmaf(df, df, m);
+                    D[u] = dtw_cost<P>(df, m);
                     mn = fminf(mn, D[u]);
                 }
                 if (lane == lane_dead) {

@@ -86,7 +86,7 @@ __device__ __forceinline__ void lanes_step(float (&D)[CL], float (&yw)[CL], floa
             const float below = (u > 0) ? D[(u > 0) ? u - 1 : 0] : left;
             const float m = min3f(D[u], above, below);
             const float df = xi - yw[(u + R) % CL];
-            D[u] = (P == 1) ? fabsf(df) + m : fmaf(df, df, m);
+            D[u] = dtw_cost<P>(df, m);
         }
         if (reset_dead) lanes_kill<CL>(D, c_dead);  // slot 2w+1 (outside the band) reads +INF next row
     }

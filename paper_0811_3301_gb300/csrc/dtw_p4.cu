@@ -1,0 +1,8 @@
+// Band-DTW kernels (register and wide thread paths) for p = 4.
+#include "dtw_launch.cuh"
+
+namespace dtwk {
+
+cudaError_t launch_dtw_p4(const DtwJob &j, const DtwGeom &g, cudaStream_t s) { return launch_dtw_pt<4>(j, g, s); }
+
+}  // namespace dtwk

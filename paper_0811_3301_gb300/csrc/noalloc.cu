@@ -83,7 +83,8 @@ extern "C" dtw_status dtw_band_noalloc(const float *x, const float *y, int64_t N
     set_error_message("");
     if (n < 1 || n > DTW_MAX_N) return noalloc_fail(DTW_ERR_INVALID_ARG, "n=%d outside [1, %d]", n, DTW_MAX_N);
     if (w < 0) return noalloc_fail(DTW_ERR_INVALID_ARG, "w=%d must be >= 0", w);
-    if (p != 1 && p != 2) return noalloc_fail(DTW_ERR_INVALID_ARG, "p=%d must be 1 or 2", p);
+    if (p != 1 && p != 2 && p != 4 && p != DTW_P_INF)
+        return noalloc_fail(DTW_ERR_INVALID_ARG, "p=%d must be 1, 2, 4 or DTW_P_INF (0)", p);
     const int we = w < n - 1 ? w : n - 1;
     if (2 * we + 1 > 2048)
         return noalloc_fail(DTW_ERR_INVALID_ARG, "DTW band 2*min(w,n-1)+1 = %d exceeds 2048", 2 * we + 1);
@@ -128,12 +129,14 @@ extern "C" dtw_status dtw_band_noalloc(const float *x, const float *y, int64_t N
     j.pairs = nullptr;
     j.npairs = N;
     j.per_pair_y = y_stride ? 1 : 0;
-    j.fixed_thr = std::isinf(threshold) ? INFINITY : (p == 1 ? threshold : threshold * threshold);
+    j.fixed_thr = std::isinf(threshold) ? INFINITY
+                  : (p == 2 ? threshold * threshold
+                            : (p == 4 ? (threshold * threshold) * (threshold * threshold) : threshold));
     j.abandon = std::isinf(threshold) ? 0 : 1;
     j.res = out;
     j.root_out = 1;
     j.cursor = cursor;
-    e = p == 1 ? launch_dtw_p1(j, g, s) : launch_dtw_p2(j, g, s);
+    e = launch_dtw_by_p(j, g, s);
     if (e != cudaSuccess) return noalloc_fail(DTW_ERR_CUDA, "DTW launch: %s", cudaGetErrorString(e));
     return DTW_OK;
 }

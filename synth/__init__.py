@@ -28,6 +28,8 @@ import numpy as np
 __all__ = [
     "random_walks",
     "shapes",
+    "shape_classes",
+    "SHAPE_CLASSES",
     "bucket_lengths",
     "log_uniform_lengths",
     "STREAM_DB",
@@ -62,10 +64,14 @@ def random_walks(count: int, n: int, seed: int, stream: int = STREAM_DB) -> np.n
     return out
 
 
-def _shape_rows(g: np.random.Generator, rows: int, n: int) -> np.ndarray:
+SHAPE_CLASSES = 4  # plateau, rising ramp, falling ramp, sum of sinusoids
+
+
+def _shape_rows(g: np.random.Generator, rows: int, n: int, cls=None) -> np.ndarray:
     t = np.arange(n, dtype=np.float64)
     out = np.empty((rows, n), dtype=np.float64)
-    cls = g.integers(0, 4, size=rows)
+    if cls is None:
+        cls = g.integers(0, SHAPE_CLASSES, size=rows)
     for r in range(rows):
         c = int(cls[r])
         if c < 3:
@@ -123,6 +129,20 @@ def shapes(count: int, n: int, seed: int, stream: int = STREAM_DB) -> np.ndarray
     for c, lo in enumerate(range(0, count, _CHUNK)):
         hi = min(count, lo + _CHUNK)
         out[lo:hi] = _shape_rows(_rng(seed, stream, c), hi - lo, n)
+    return out
+
+
+def shape_classes(labels, n: int, seed: int, stream: int = STREAM_DB) -> np.ndarray:
+    """Shape-like series of the given classes (0 plateau, 1 rising ramp, 2
+    falling ramp, 3 sum of sinusoids), fp32 [len(labels), n]: the labelled
+    stand-in for the classification experiment of App. C."""
+    labels = np.asarray(labels, dtype=np.int64)
+    if labels.ndim != 1 or np.any((labels < 0) | (labels >= SHAPE_CLASSES)) or n < 1:
+        raise ValueError("labels in [0, %d) and n >= 1 required" % SHAPE_CLASSES)
+    out = np.empty((labels.shape[0], n), dtype=np.float32)
+    for c, lo in enumerate(range(0, labels.shape[0], _CHUNK)):
+        hi = min(labels.shape[0], lo + _CHUNK)
+        out[lo:hi] = _shape_rows(_rng(seed, stream + 32, c), hi - lo, n, cls=labels[lo:hi])
     return out
 
 

@@ -147,7 +147,16 @@ DTW_CASES = [(1, 0), (2, 1), (8, 3), (33, 0), (64, 6), (128, 12), (181, 18), (25
              (512, 51), (1024, 102), (400, 103), (300, 104), (1024, 150), (1024, 204), (600, 599)]
 
 
-@pytest.mark.parametrize("p", [1, 2])
+# p = 4 and p = infinity (App. C's other measures) through dtw_band; the
+# oracle takes p = 0 for infinity
+P_ALL = [1, 2, 4, math.inf]
+
+
+def oracle_p(p):
+    return 0 if p == math.inf else p
+
+
+@pytest.mark.parametrize("p", P_ALL)
 @pytest.mark.parametrize("n,w", DTW_CASES)
 def test_dtw_band_shared_query(api, p, n, w):
     N = 70  # two full warps and a ragged tail
@@ -155,11 +164,11 @@ def test_dtw_band_shared_query(api, p, n, w):
     y = synth.random_walks(1, n, seed=200 + n, stream=synth.STREAM_QUERY)[0]
     d = api.dtw_band(cuda(X), cuda(y), w, p).cpu().numpy()
     for c in range(N):
-        ref = oracle.dtw(X[c], y, w, p)
+        ref = oracle.dtw(X[c], y, w, oracle_p(p))
         assert close(d[c], ref), (n, w, c, d[c], ref)
 
 
-@pytest.mark.parametrize("p", [1, 2])
+@pytest.mark.parametrize("p", P_ALL)
 @pytest.mark.parametrize("n,w", [(16, 2), (256, 25), (1024, 204)])
 def test_dtw_band_per_pair_query(api, p, n, w):
     N = 40
@@ -167,7 +176,33 @@ def test_dtw_band_per_pair_query(api, p, n, w):
     Y = synth.random_walks(N, n, seed=301 + n, stream=synth.STREAM_QUERY)
     d = api.dtw_band(cuda(X), cuda(Y), w, p).cpu().numpy()
     for c in range(N):
-        assert close(d[c], oracle.dtw(X[c], Y[c], w, p)), (c,)
+        assert close(d[c], oracle.dtw(X[c], Y[c], w, oracle_p(p))), (c,)
+
+
+@pytest.mark.parametrize("p", [4, math.inf])
+def test_dtw_band_p4_and_inf_special_cases(api, p):
+    # Sec. 4 / App. A facts that hold for every p: with w = 0 DTW_p is the l_p
+    # distance; against a constant series DTW_p is the l_p distance too; and
+    # DTW_inf(x, x + c) = |c| for a shift c
+    g = np.random.default_rng(5)
+    X = synth.random_walks(8, 64, seed=55)
+    y = synth.random_walks(1, 64, seed=56, stream=synth.STREAM_QUERY)[0]
+    d0 = api.dtw_band(cuda(X), cuda(y), 0, p).cpu().numpy()
+    diff = np.abs(X.astype(np.float64) - y.astype(np.float64))
+    lp = diff.max(axis=1) if p == math.inf else (diff ** 4).sum(axis=1) ** 0.25
+    np.testing.assert_allclose(d0, lp, rtol=1e-5)
+    cst = np.full(64, 1.5, np.float32)
+    dc = api.dtw_band(cuda(X), cuda(cst), 10, p).cpu().numpy()
+    dfc = np.abs(X.astype(np.float64) - 1.5)
+    lpc = dfc.max(axis=1) if p == math.inf else (dfc ** 4).sum(axis=1) ** 0.25
+    np.testing.assert_allclose(dc, lpc, rtol=1e-5)
+    if p == math.inf:
+        shift = np.float32(g.uniform(0.5, 2.0))
+        Y = X + shift  # fp32: the per-element shifts differ by rounding
+        ds = api.dtw_band(cuda(X), cuda(Y), 6, p).cpu().numpy()
+        np.testing.assert_allclose(ds, np.abs(Y.astype(np.float64) - X).max(axis=1), rtol=2e-5)
+        for c in range(len(X)):
+            assert close(ds[c], oracle.dtw(X[c], Y[c], 6, 0)), c
 
 
 @pytest.mark.parametrize("p", [1, 2])
@@ -187,13 +222,13 @@ def test_dtw_band_per_pair_many_pairs(api, p, n, w):
         assert close(d[c], ref), (n, w, c, d[c], ref)
 
 
-@pytest.mark.parametrize("p", [1, 2])
+@pytest.mark.parametrize("p", P_ALL)
 @pytest.mark.parametrize("n,w", [(128, 12), (1024, 204)])
 def test_dtw_band_threshold(api, p, n, w):
     N = 64
     X = synth.random_walks(N, n, seed=400 + n)
     y = synth.random_walks(1, n, seed=401 + n, stream=synth.STREAM_QUERY)[0]
-    ref = np.array([oracle.dtw(X[c], y, w, p) for c in range(N)])
+    ref = np.array([oracle.dtw(X[c], y, w, oracle_p(p)) for c in range(N)])
     thr = float(np.median(ref))
     d = api.dtw_band(cuda(X), cuda(y), w, p, threshold=thr).cpu().numpy()
     for c in range(N):
@@ -351,3 +386,23 @@ def test_knn_full_size_sampled(api, p):
     sample = np.array([0, 1, 2, 3, 500, 997, 998, 999])
     ri, rd, _ = oracle.knn_cascade(db, qs[sample], 25, p, 1, mode=1, threads=16)
     assert_knn(db, qs[sample], 25, p, 1, idx[sample], dist[sample], ri, rd)
+
+
+@pytest.mark.parametrize("p", P_ALL)
+def test_classification_nearest_neighbours_match_the_oracle(api, p):
+    # App. C: every test series against a small labelled database, all pairs
+    # in one dtw_band launch, nearest neighbour by first minimum
+    labels = np.repeat(np.arange(synth.SHAPE_CLASSES), 3)
+    db = synth.shape_classes(labels, 128, seed=71)
+    tl = np.random.default_rng(72).integers(0, synth.SHAPE_CLASSES, size=40)
+    ts = synth.shape_classes(tl, 128, seed=71, stream=synth.STREAM_QUERY)
+    k, T, w = len(labels), len(tl), 12
+    X = np.ascontiguousarray(np.tile(db, (T, 1)))
+    Y = np.ascontiguousarray(np.repeat(ts, k, axis=0))
+    d = api.dtw_band(cuda(X), cuda(Y), w, p).cpu().numpy().reshape(T, k)
+    nn = d.argmin(axis=1)
+    for t in range(T):
+        oi, od = oracle.knn_bruteforce(db, ts[t][None, :], w, oracle_p(p), 1)
+        if nn[t] != oi[0, 0]:  # a near-tie fp32 cannot order: same distance
+            assert close(oracle.dtw(db[nn[t]], ts[t], w, oracle_p(p)), od[0, 0]), (t, nn[t], oi[0, 0])
+        assert close(d[t, nn[t]], od[0, 0]), t
