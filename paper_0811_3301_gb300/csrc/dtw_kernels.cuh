@@ -197,12 +197,38 @@ __device__ __forceinline__ void dtw_cells_win(float (&D)[C], float xi, const flo
     }
 }
 
+// One band cell given its difference d = x_i - y_j.
+template <int K, int C, int P>
+__device__ __forceinline__ void dtw_cell_d(float (&D)[C], float d) {
+    float above, below;
+    if constexpr (K + 1 < C) above = D[K + 1]; else above = kInf;
+    if constexpr (K > 0) below = D[K - 1]; else below = kInf;
+    D[K] = dtw_cost<P>(d, min3f(D[K], above, below));
+}
+
+// Cells K..C-1 with the differences of two adjacent slots formed by one
+// packed fp32x2 fma (y * -1 + x: the same rounding as x - y); the
+// differences are off the row's dependency chain, which runs through the
+// minimum and the cost.
+template <int K, int C, int P, int U>
+__device__ __forceinline__ void dtw_cells_win2(float (&D)[C], float xi, const float (&yw)[C + 4]) {
+    if constexpr (K + 1 < C) {
+        const float2 d = __ffma2_rn(make_float2(yw[U + K], yw[U + K + 1]), make_float2(-1.0f, -1.0f),
+                                    make_float2(xi, xi));
+        dtw_cell_d<K, C, P>(D, d.x);
+        dtw_cell_d<K + 1, C, P>(D, d.y);
+        dtw_cells_win2<K + 2, C, P, U>(D, xi, yw);
+    } else if constexpr (K < C) {
+        dtw_cell<K, C, P>(D, xi, yw[U + K]);
+    }
+}
+
 // Cells K..C-1 of one row without a jump: used when the bottom padding E is
 // a compile-time constant (the common bands), so that the rows of a group
 // are one straight-line block the scheduler can interleave.
 template <int C, int P, int U, int E>
 __device__ __forceinline__ void dtw_row_win_fixed(float (&D)[C], float xi, const float (&yw)[C + 4]) {
-    dtw_cells_win<E, C, P, U>(D, xi, yw);
+    dtw_cells_win2<E, C, P, U>(D, xi, yw);
 }
 
 template <int C, int P, int U>
