@@ -56,10 +56,28 @@ __device__ __forceinline__ void dtw_cell(float (&D)[C], float xi, float yv) {
 }
 #define DTW_CELL(K, YV) dtw_cell<K, C, P>(D, xi, YV);
 
+// One band cell given its difference d = x_i - y_j.
+template <int K, int C, int P>
+__device__ __forceinline__ void dtw_cell_d(float (&D)[C], float d) {
+    float above, below;
+    if constexpr (K + 1 < C) above = D[K + 1]; else above = kInf;
+    if constexpr (K > 0) below = D[K - 1]; else below = kInf;
+    D[K] = dtw_cost<P>(d, min3f(D[K], above, below));
+}
+
+// Differences x - y of two adjacent slots by one packed fp32x2 fma (y * -1 +
+// x: the same rounding as x - y).  They are off the row's dependency chain,
+// which runs through the minimum and the cost.
+__device__ __forceinline__ float2 dtw_diff2(float xi, float ya, float yb) {
+    return __ffma2_rn(make_float2(ya, yb), make_float2(-1.0f, -1.0f), make_float2(xi, xi));
+}
+
 // Cells K..C-1, four per 128-bit load of the query window.
 template <int K, int C, int P>
 __device__ __forceinline__ void dtw_cells_from(float (&D)[C], float xi, const float4 *yb) {
     if constexpr (K < C) {
+        // (packed differences here measured slower: this kernel holds up to
+        // 255 registers already)
         const float4 t = __ldg(yb + (K >> 2));
         dtw_cell<K, C, P>(D, xi, t.x);
         dtw_cell<K + 1, C, P>(D, xi, t.y);
@@ -197,24 +215,11 @@ __device__ __forceinline__ void dtw_cells_win(float (&D)[C], float xi, const flo
     }
 }
 
-// One band cell given its difference d = x_i - y_j.
-template <int K, int C, int P>
-__device__ __forceinline__ void dtw_cell_d(float (&D)[C], float d) {
-    float above, below;
-    if constexpr (K + 1 < C) above = D[K + 1]; else above = kInf;
-    if constexpr (K > 0) below = D[K - 1]; else below = kInf;
-    D[K] = dtw_cost<P>(d, min3f(D[K], above, below));
-}
-
-// Cells K..C-1 with the differences of two adjacent slots formed by one
-// packed fp32x2 fma (y * -1 + x: the same rounding as x - y); the
-// differences are off the row's dependency chain, which runs through the
-// minimum and the cost.
+// Cells K..C-1, two adjacent slots' differences per packed fma.
 template <int K, int C, int P, int U>
 __device__ __forceinline__ void dtw_cells_win2(float (&D)[C], float xi, const float (&yw)[C + 4]) {
     if constexpr (K + 1 < C) {
-        const float2 d = __ffma2_rn(make_float2(yw[U + K], yw[U + K + 1]), make_float2(-1.0f, -1.0f),
-                                    make_float2(xi, xi));
+        const float2 d = dtw_diff2(xi, yw[U + K], yw[U + K + 1]);
         dtw_cell_d<K, C, P>(D, d.x);
         dtw_cell_d<K + 1, C, P>(D, d.y);
         dtw_cells_win2<K + 2, C, P, U>(D, xi, yw);
