@@ -983,6 +983,28 @@ __device__ __forceinline__ float warp_lbi_env(const CascadeBufs &b, int q, int c
             *lbk = a1;
             return a1 > thr ? a1 : a1 + a2;
         }
+    } else {
+        if (known < 0.0f && do_lbi && vec) {
+            // Long rows, streamed: both sums in one pass over 16-byte pieces,
+            // so that the loads of the two sums are in flight together, and
+            // one combined reduction.
+            const int64_t oc = (int64_t)c * n, oq = (int64_t)q * n;
+            const float *x = b.db + oc, *xu = b.XU + oc, *xl = b.XL + oc;
+            const float *U = b.U + oq, *L = b.L + oq, *y = b.queries + oq, *ul = b.UL + oq, *lu = b.LU + oq;
+            float a1 = 0.0f, a2 = 0.0f;
+#pragma unroll 2
+            for (int i = 4 * lane; i < n; i += 128) {
+                a1 = acc_dist4<P>(a1, ldg4(x + i), ldg4(L + i), ldg4(U + i));
+                a2 = acc_dist4<P>(a2, ldg4(y + i), min4(ldg4(xl + i), ldg4(lu + i)), max4(ldg4(xu + i), ldg4(ul + i)));
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+                a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+            }
+            *lbk = a1;
+            return a1 > thr ? a1 : a1 + a2;
+        }
     }
     float first = known;
     if (known < 0.0f) {
