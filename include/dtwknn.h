@@ -122,7 +122,10 @@ dtw_status lb_piecewise(const float *cand, int64_t N, const float *U, const floa
  * LB_Improved_p(x, y) with LB_Improved_p^p = LB_Keogh_p(x, y)^p +
  * LB_Keogh_p(y, H(x, y))^p (Sec. 8) for every candidate x = cand[c] against
  * the query q [n] with envelope U, L ([n] each, computed with the same w).
- * out[c] receives the bound (root taken), [N].
+ * out[c] receives the bound (root taken), [N].  The second sum is evaluated
+ * from the candidates' own envelopes and the envelopes of U and L, which
+ * give the same terms as the envelope of the projection H; uses the
+ * workspace (2 N n + 4 n floats).
  */
 dtw_status lb_improved(const float *cand, int64_t N, const float *q, const float *U,
                        const float *L, int32_t n, int32_t w, int32_t p, float *out,

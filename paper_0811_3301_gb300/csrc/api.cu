@@ -197,7 +197,30 @@ dtw_status lb_improved(const float *cand, int64_t N, const float *q, const float
     if (N < 0) return fail(DTW_ERR_INVALID_ARG, "N=%lld must be >= 0", (long long)N);
     if (N == 0) return DTW_OK;
     if (!cand || !q || !U || !L || !out) return fail(DTW_ERR_INVALID_ARG, "null pointer");
-    CUDA_TRY(launch_lbi_single(cand, N, q, U, L, n, w, p, out, (cudaStream_t)stream));
+    cudaStream_t s = (cudaStream_t)stream;
+    const int we = w < n - 1 ? w : n - 1;
+    // the candidates' envelopes and the query's second-order envelopes U(L),
+    // L(U) (the envelope of L gives U(L), that of U gives L(U))
+    auto layout = [&](Carve &cv, float *&XU, float *&XL, float *&UL, float *&LU, float *&t0, float *&t1) {
+        XU = cv.take<float>((size_t)N * n);
+        XL = cv.take<float>((size_t)N * n);
+        UL = cv.take<float>((size_t)n);
+        LU = cv.take<float>((size_t)n);
+        t0 = cv.take<float>((size_t)n);
+        t1 = cv.take<float>((size_t)n);
+    };
+    float *XU, *XL, *UL, *LU, *t0, *t1;
+    Carve sizing;
+    layout(sizing, XU, XL, UL, LU, t0, t1);
+    void *ws = nullptr;
+    if ((st = workspace_get(sizing.off, &ws)) != DTW_OK) return st;
+    Carve cv;
+    cv.base = (char *)ws;
+    layout(cv, XU, XL, UL, LU, t0, t1);
+    CUDA_TRY(launch_envelope(cand, N, n, we, XU, XL, QueryCopies{}, 0, s));
+    CUDA_TRY(launch_envelope(L, 1, n, we, UL, t0, QueryCopies{}, 0, s));
+    CUDA_TRY(launch_envelope(U, 1, n, we, t1, LU, QueryCopies{}, 0, s));
+    CUDA_TRY(launch_lbi_single(cand, N, q, U, L, XU, XL, UL, LU, n, p, out, s));
     return DTW_OK;
 }
 

@@ -147,8 +147,11 @@ struct Pair {
     int32_t c;
 };
 
-cudaError_t launch_lbi_single(const float *cand, int64_t N, const float *q, const float *U,
-                              const float *L, int n, int w, int p, float *out, cudaStream_t s);
+// LB_Improved^(1/p) of cand [N][n] against q [n] with envelope U, L, from the
+// candidates' envelopes XU, XL [N][n] and the query's U(L), L(U) [n] (same band).
+cudaError_t launch_lbi_single(const float *cand, int64_t N, const float *q, const float *U, const float *L,
+                              const float *XU, const float *XL, const float *UL, const float *LU, int n, int p,
+                              float *out, cudaStream_t s);
 
 struct CascadeBufs {
     // inputs

@@ -272,30 +272,17 @@ cudaError_t launch_lbk_tile(const float *db, int N, const float *U, const float 
 }
 
 // ---------------------------------------------------------------------------
-// LB_Improved of one pair by one warp (Sec. 8).
-//
-// Lane l owns the M consecutive indices l*M .. l*M+M-1 ("chunk" l), M the
-// power of two >= n/32.  For one query the lane keeps its chunk of U(y),
-// L(y) and y; per candidate it loads its chunk of x, clamps it into the
-// envelope (h = H(x, y), Eq. 1), adds the first-pass terms |x_i - h_i|^p and
-// forms the chunk's prefix and suffix max/min of h.  A table over the 32
-// chunk totals (max/min of 2^j consecutive chunks) covers whole chunks.  The
-// envelope of h at i, over [a, b] = [i-w, i+w] clipped, is suffix(a) of
-// chunk(a), the whole chunks strictly between, and prefix(b) of chunk(b) --
-// or a direct max/min over h when [a, b] lies strictly inside one chunk.  The
-// second-pass terms are d(y_i, [L'_i, U'_i])^p.
-//
-// Prefix/suffix pairs (max, min) and the table live in shared memory in
-// position-major order [t][lane], so that a lane's writes (fixed lane) and the
-// window lookups of a warp (fixed t, consecutive chunks) are conflict-free.
-// MT is M when M <= 16 (chunk held in registers) and 0 for a runtime M
-// (chunk streamed through shared memory).
+// LB_Improved (Sec. 8) of N candidates against one query: the second sum in
+// the envelope form derived at the cascade filter below (the candidates'
+// envelopes XU, XL and the query's U(L), L(U) computed by the caller); one
+// warp per candidate, lane l taking indices l, l + 32, ... (coalesced).
 // ---------------------------------------------------------------------------
-constexpr int kLbiRegM = 8;  // largest chunk kept in registers
+constexpr int kLbiRegM = 8;  // largest per-lane chunk the filter keeps in registers
 
 struct LbiGeom {
     int m, lg;
 };
+// M = the power of two >= n/32 (elements per lane), lg = log2(M)
 __host__ __device__ inline LbiGeom lbi_geom(int n) {
     LbiGeom g;
     const int need = (n + 31) / 32;
@@ -307,471 +294,40 @@ __host__ __device__ inline LbiGeom lbi_geom(int n) {
     }
     return g;
 }
-// Chunk columns of the prefix/suffix arrays.  For chunks held in registers
-// (M <= kLbiRegM) the arrays carry neutral (-inf, +inf) columns beyond both
-// ends of the series, so that a window reaching past an end needs no
-// clamping: column c of chunk c - pad_left.
-struct LbiCols {
-    int left, width;
-};
-__host__ __device__ inline LbiCols lbi_cols(int n, int w) {
-    const int m = lbi_geom(n).m;
-    LbiCols c;
-    if (m > kLbiRegM) {
-        c.left = 0;
-        c.width = 32;
-    } else {
-        c.left = (w + m - 1) / m + 1;
-        c.width = c.left + 32 + (w + 2 * m - 1) / m + 1;
-    }
-    return c;
-}
-// per-warp scratch in floats: prefix and suffix (max, min) pairs [M][width]
-// each, the chunk table (max, min) [6][32] and, where a window can lie inside
-// one chunk (runtime M, or 2w < M), the chunk of h [M][32]
-__host__ __device__ inline int lbi_scratch_floats(int n, int w) {
-    const int m = lbi_geom(n).m;
-    const bool keep_h = m > kLbiRegM || 2 * w < m;
-    return 2 * 2 * m * lbi_cols(n, w).width + 2 * 6 * 32 + (keep_h ? 32 * m : 0);
-}
-// per-query staging: y in [t][32] layout, and for runtime M also U and L
-__host__ __device__ inline int lbi_query_floats(int n) {
-    const int m = lbi_geom(n).m;
-    return m > kLbiRegM ? 3 * 32 * m : 32 * m;
-}
 
-// Per-lane view of the query: the chunk of U and L in registers for MT > 0,
-// otherwise in shared memory; y always in shared memory.
-template <int MT>
-struct LbiQuery {
-    float u[MT > 0 ? MT : 1], l[MT > 0 ? MT : 1], yr[MT > 0 ? MT : 1];
-    const float *sq;  // y [M][32]; for MT == 0 then U [M][32], L [M][32]
-    __device__ float U(int t, int lane, int m) const { return sq[(m + t) * 32 + lane]; }
-    __device__ float L(int t, int lane, int m) const { return sq[(2 * m + t) * 32 + lane]; }
-    __device__ float Y(int t, int lane, int m) const { return sq[t * 32 + lane]; }
-};
-
-// Load the query chunk of this lane (MT > 0: into registers; MT == 0: the
-// whole block stages [t][32] arrays into sq, caller synchronises).
-template <int MT>
-__device__ __forceinline__ void lbi_load_query(LbiQuery<MT> &Qv, const float *__restrict__ y, const float *__restrict__ U,
-                                               const float *__restrict__ L, int n, float *sq) {
-    const LbiGeom g = lbi_geom(n);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const int c = i >> g.lg, t = i & (g.m - 1);
-        sq[t * 32 + c] = y[i];
-        if constexpr (MT == 0) {
-            sq[(g.m + t) * 32 + c] = U[i];
-            sq[(2 * g.m + t) * 32 + c] = L[i];
-        }
-    }
-    Qv.sq = sq;
-    if constexpr (MT > 0) {
-        const int lane = threadIdx.x & 31;
-#pragma unroll
-        for (int t = 0; t < MT; ++t) {
-            const int i = lane * MT + t;
-            Qv.u[t] = i < n ? U[i] : 0.0f;
-            Qv.l[t] = i < n ? L[i] : 0.0f;
-            Qv.yr[t] = i < n ? y[i] : 0.0f;
-        }
-    }
-}
-
-// Write the neutral padding columns of a warp's prefix/suffix arrays (once
-// per warp; the per-pair passes only write the 32 real columns).
-template <int MT>
-__device__ inline void lbi_init_scratch(float *scratch, int n, int w) {
-    if constexpr (MT > 0) {
-        const int lane = threadIdx.x & 31;
-        const LbiCols cols = lbi_cols(n, w);
-        float2 *Pre = reinterpret_cast<float2 *>(scratch);
-        float2 *Suf = Pre + MT * cols.width;
-        const float2 neutral = make_float2(-kInf, kInf);
-        for (int e = lane; e < MT * cols.width; e += 32) {
-            const int c = e % cols.width;
-            if (c < cols.left || c >= cols.left + 32) {
-                Pre[e] = neutral;
-                Suf[e] = neutral;
-            }
-        }
-        __syncwarp();
-    }
-}
-
-// This lane's chunk of a candidate row (MT > 0), loaded ahead of its use.
+// This lane's elements of a candidate row (MT > 0).
 template <int MT>
 struct LbiChunk {
     float v[MT > 0 ? MT : 1];
 };
-template <int MT>
-__device__ __forceinline__ void lbi_load_chunk(LbiChunk<MT> &ch, const float *__restrict__ x, int n, bool vec) {
-    if constexpr (MT > 0) {
-        const int lane = threadIdx.x & 31;
-        const int i0 = lane * MT;
-        const int cnt_in = max(0, min(MT, n - i0));
-        if (vec && MT >= 4 && cnt_in == MT) {
-#pragma unroll
-            for (int t = 0; t < MT; t += 4) {
-                const float4 v = __ldg(reinterpret_cast<const float4 *>(x + i0 + t));
-                ch.v[t] = v.x;
-                ch.v[t + 1] = v.y;
-                ch.v[t + 2] = v.z;
-                ch.v[t + 3] = v.w;
-            }
-        } else {
-#pragma unroll
-            for (int t = 0; t < MT; ++t) ch.v[t] = t < cnt_in ? __ldg(x + i0 + t) : 0.0f;
-        }
-    }
-}
 
-// Second-pass terms of one lane's chunk when pa0 = (-w) mod M = PA0 is a
-// compile-time constant: position t's window starts in chunk lane + D0 + fa at
-// position pa and ends in chunk lane + E0 + fb at position pb, with fa, fb,
-// pa, pb known at compile time, so every lookup is a fixed offset.
-template <int P, int MT, int PA0>
-__device__ __forceinline__ float lbi_pass3(const float2 *sufb, const float2 *preb, int W, const float2 (&mid)[2][2],
-                                           const LbiQuery<MT> &Qv, int cnt_in) {
-    constexpr int PB0 = (MT - PA0) & (MT - 1);
-    float acc2 = 0.0f;
-#pragma unroll
-    for (int t = 0; t < MT; ++t) {
-        constexpr int dummy = 0;
-        (void)dummy;
-        const bool fa = PA0 + t >= MT, fb = PB0 + t >= MT;
-        const int pa = fa ? PA0 + t - MT : PA0 + t;
-        const int pb = fb ? PB0 + t - MT : PB0 + t;
-        const float2 sa = sufb[pa * W + (fa ? 1 : 0)];
-        const float2 pv = preb[pb * W + (fb ? 1 : 0)];
-        const float2 md = mid[fa ? 1 : 0][fb ? 1 : 0];
-        const float uu = max3f(sa.x, pv.x, md.x);
-        const float ll = min3f(sa.y, pv.y, md.y);
-        if (t < cnt_in) acc2 = acc_dist<P>(acc2, Qv.yr[t], ll, uu);
-    }
-    return acc2;
-}
-
-// Widened-window test (MT > 0, pa0 = PA0): the window of position t,
-// [i - w, i + w], widened outward to whole chunks, is chunks
-// lane + D0 + fa .. lane + E0 + fb; cw[fa][fb] holds the (max, min) of the
-// projection over those chunks.  The envelope over a window that contains
-// the true one bounds U(H) from above and L(H) from below, so the second sum
-// taken with it is at most LB_Keogh(y, H)^p, and LB_Keogh^p plus it is a
-// lower bound of LB_Improved^p (Sec. 8): a cheap first test of the second pass.
-template <int P, int MT, int PA0>
-__device__ __forceinline__ float lbi_coarse(const float2 (&cw)[2][2], const LbiQuery<MT> &Qv, int cnt_in) {
-    constexpr int PB0 = (MT - PA0) & (MT - 1);
-    float acc = 0.0f;
-#pragma unroll
-    for (int t = 0; t < MT; ++t) {
-        const bool fa = PA0 + t >= MT, fb = PB0 + t >= MT;
-        const float2 e = cw[fa ? 1 : 0][fb ? 1 : 0];
-        if (t < cnt_in) acc = acc_dist<P>(acc, Qv.yr[t], e.y, e.x);
-    }
-    return acc;
-}
-
-// (max, min) over the chunks lo .. hi (clamped to the 32 chunks; chunks past
-// the series hold neutral totals) from the table T_j[c] = chunks c .. c+2^j-1.
-__device__ __forceinline__ float2 lbi_chunk_range(const float2 *T, int lo, int hi) {
-    lo = max(lo, 0);
-    hi = min(hi, 31);
-    float2 r = make_float2(-kInf, kInf);
-    if (lo <= hi) {
-        const int k = 31 - __clz(hi - lo + 1);
-        const float2 t1 = T[k * 32 + lo], t2 = T[k * 32 + hi - (1 << k) + 1];
-        r = make_float2(fmaxf(t1.x, t2.x), fminf(t1.y, t2.y));
-    }
-    return r;
-}
-
-// Returns LB_Improved^p, or a smaller bound when the pair fails a test:
-// LB_Keogh^p alone when !do_lbi or when it already exceeds keogh_thr, and
-// LB_Keogh^p plus the widened-window second sum when that exceeds
-// keogh_thr.  *lbk_out receives LB_Keogh^p.  lbk_known >= 0: LB_Keogh^p of
-// the pair, already computed and tested by the caller (the first sum is then
-// not formed again).
-template <int P, int MT>
-__device__ __forceinline__ float warp_lb_improved(const float *__restrict__ x, const LbiQuery<MT> &Qv, int n, int w,
-                                                  float *scratch, bool vec, const LbiChunk<MT> *pre = nullptr,
-                                                  bool do_lbi = true, float keogh_thr = kInf,
-                                                  float *lbk_out = nullptr, float lbk_known = -1.0f) {
+template <int P>
+__global__ void __launch_bounds__(256)
+k_lbi_single(const float *__restrict__ cand, int64_t N, const float *__restrict__ q, const float *__restrict__ U,
+             const float *__restrict__ L, const float *__restrict__ XU, const float *__restrict__ XL,
+             const float *__restrict__ UL, const float *__restrict__ LU, int n, float *__restrict__ out) {
     const int lane = threadIdx.x & 31;
-    const LbiGeom g = lbi_geom(n);
-    const int m = MT > 0 ? MT : g.m;
-    const int lg = g.lg;
-    const LbiCols cols = lbi_cols(n, w);
-    const int W = cols.width, PLc = cols.left;
-    float2 *Pre = reinterpret_cast<float2 *>(scratch);  // [m][W] (max, min)
-    float2 *Suf = Pre + W * m;                           // [m][W]
-    float2 *T = Suf + W * m;                             // [6][32]
-    float *Hs = reinterpret_cast<float *>(T + 6 * 32);   // [m][32]
-    const float NEG = -kInf, POS = kInf;
-    const int i0 = lane * m;
-    const int cnt_in = max(0, min(m, n - i0));
-    const int pa0 = (-w) & (m - 1), D0 = (-w) >> lg;
-    const int E0 = w >> lg;
-    float acc1 = 0.0f;
-    float cmax = NEG, cmin = POS;  // chunk totals of the projection
-    float h[MT > 0 ? MT : 1];
-    // first pass: projection H (Eq. 1) and LB_Keogh^p
-    if constexpr (MT > 0) {
-        LbiChunk<MT> own;
-        if (pre == nullptr) lbi_load_chunk<MT>(own, x, n, vec);
-        const float *xv = pre ? pre->v : own.v;
-#pragma unroll
-        for (int t = 0; t < MT; ++t) {
-            const float hv = fminf(fmaxf(xv[t], Qv.l[t]), Qv.u[t]);  // Eq. 1 (L <= U)
-            const float d = fabsf(xv[t] - hv);
-            if (t < cnt_in) {
-                acc1 = (P == 1) ? acc1 + d : fmaf(d, d, acc1);
-                h[t] = hv;
-                cmax = fmaxf(cmax, hv);
-                cmin = fminf(cmin, hv);
-            } else {
-                h[t] = NEG;
-            }
-        }
-    } else {
-        for (int t = 0; t < m; ++t) {
-            float hv = NEG;
-            if (t < cnt_in) {
-                const float xv = __ldg(x + i0 + t);
-                hv = fminf(fmaxf(xv, Qv.L(t, lane, m)), Qv.U(t, lane, m));
-                const float d = fabsf(xv - hv);
-                acc1 = (P == 1) ? acc1 + d : fmaf(d, d, acc1);
-                cmax = fmaxf(cmax, hv);
-                cmin = fminf(cmin, hv);
-            }
-            Hs[t * 32 + lane] = hv;
-        }
-    }
-    if (lbk_known >= 0.0f) {
-        acc1 = (lane == 0) ? lbk_known : 0.0f;
-    } else {
-        const float lbk = warp_sum(acc1);
-        if (lbk_out) *lbk_out = lbk;
-        if (!do_lbi || lbk > keogh_thr) return lbk;
-        acc1 = (lane == 0) ? lbk : 0.0f;
-    }
-    // table over chunk totals: T_j[c] = max/min of chunks c .. c + 2^j - 1
-    {
-        float tmax = cmax, tmin = cmin;
-        T[lane] = make_float2(tmax, tmin);
-#pragma unroll
-        for (int j = 1; j < 6; ++j) {
-            const int hh = 1 << (j - 1);
-            const float omax = __shfl_down_sync(0xffffffffu, tmax, hh);
-            const float omin = __shfl_down_sync(0xffffffffu, tmin, hh);
-            if (lane + hh < 32) {
-                tmax = fmaxf(tmax, omax);
-                tmin = fminf(tmin, omin);
-            }
-            T[j * 32 + lane] = make_float2(tmax, tmin);
-        }
-    }
-    __syncwarp();
-    const bool windows_span_chunks = 2 * w >= m;
-    if (windows_span_chunks && keogh_thr < kInf) {
-        // widened-window test
-        float2 cw[2][2];
-#pragma unroll
-        for (int fa = 0; fa < 2; ++fa)
-#pragma unroll
-            for (int fb = 0; fb < 2; ++fb) cw[fa][fb] = lbi_chunk_range(T, lane + D0 + fa, lane + E0 + fb);
-        float acc2 = 0.0f;
-        if constexpr (MT > 0) {
-            switch (pa0) {
-#define LBI_COARSE_CASE(A)                                                          \
-    case A:                                                                         \
-        if constexpr (A < MT) acc2 = lbi_coarse<P, MT, A>(cw, Qv, cnt_in);          \
-        break;
-                LBI_COARSE_CASE(0) LBI_COARSE_CASE(1) LBI_COARSE_CASE(2) LBI_COARSE_CASE(3)
-                LBI_COARSE_CASE(4) LBI_COARSE_CASE(5) LBI_COARSE_CASE(6) LBI_COARSE_CASE(7)
-#undef LBI_COARSE_CASE
-                default: break;
-            }
-        } else {
-            const int pb0 = w & (m - 1);
-            for (int t = 0; t < cnt_in; ++t) {
-                const bool fa = pa0 + t >= m, fb = pb0 + t >= m;
-                const float2 e = fa ? (fb ? cw[1][1] : cw[1][0]) : (fb ? cw[0][1] : cw[0][0]);
-                acc2 = acc_dist<P>(acc2, Qv.Y(t, lane, m), e.y, e.x);
-            }
-        }
-        const float wide = warp_sum(acc1 + acc2);
-        if (wide > keogh_thr) {
-            __syncwarp();  // scratch is reused by the next pair
-            return wide;
-        }
-    }
-    // second pass, exact windows: prefix and suffix (max, min) of each chunk
-    if constexpr (MT > 0) {
-        if (!windows_span_chunks) {
-            // windows can lie inside a chunk: keep h for the direct scan
-#pragma unroll
-            for (int t = 0; t < MT; ++t) Hs[t * 32 + lane] = h[t];
-        }
-        float pmax = NEG, pmin = POS;
-#pragma unroll
-        for (int t = 0; t < MT; ++t) {
-            pmax = fmaxf(pmax, h[t]);
-            pmin = (t < cnt_in) ? fminf(pmin, h[t]) : pmin;
-            Pre[t * W + PLc + lane] = make_float2(pmax, pmin);
-        }
-        float smax = NEG, smin = POS;
-#pragma unroll
-        for (int t = MT - 1; t >= 0; --t) {
-            smax = fmaxf(smax, h[t]);
-            smin = (t < cnt_in) ? fminf(smin, h[t]) : smin;
-            Suf[t * W + PLc + lane] = make_float2(smax, smin);
-        }
-    } else {
-        float pmax = NEG, pmin = POS;
-        for (int t = 0; t < m; ++t) {
-            if (t < cnt_in) {
-                const float hv = Hs[t * 32 + lane];
-                pmax = fmaxf(pmax, hv);
-                pmin = fminf(pmin, hv);
-            }
-            Pre[t * W + lane] = make_float2(pmax, pmin);
-        }
-        float smax = NEG, smin = POS;
-        for (int t = m - 1; t >= 0; --t) {
-            if (t < cnt_in) {
-                const float hv = Hs[t * 32 + lane];
-                smax = fmaxf(smax, hv);
-                smin = fminf(smin, hv);
-            }
-            Suf[t * W + lane] = make_float2(smax, smin);
-        }
-    }
-    __syncwarp();
-    float acc2 = 0.0f;
-    if (MT > 0 && windows_span_chunks) {
-        // Window of i = lane*M + t: [a, b] = [i - w, i + w]; chunk(a) = lane + da_t
-        // at position pa_t and chunk(b) = lane + db_t at position pb_t, where
-        // da_t = D0 + fa_t and db_t = E0 + fb_t with 0/1 flags that depend on t
-        // and w only.  Beyond the series the padded columns are neutral, so the
-        // prefix/suffix lookups need no clamping.  The whole chunks strictly
-        // between take one of four ranges per lane; their max/min come from the
-        // chunk table once per pair and are selected per position.
-        float2 mid[2][2];
-#pragma unroll
-        for (int fa = 0; fa < 2; ++fa)
-#pragma unroll
-            for (int fb = 0; fb < 2; ++fb) {
-                const int lo = lane + D0 + fa + 1, hi = lane + E0 + fb - 1;
-                mid[fa][fb] = (lo <= hi) ? lbi_chunk_range(T, lo, hi) : make_float2(NEG, POS);
-            }
-        if constexpr (MT > 0) {
-            const float2 *sufb = Suf + PLc + D0 + lane;
-            const float2 *preb = Pre + PLc + E0 + lane;
-            switch (pa0) {
-#define LBI_PASS3_CASE(A)                                                                          \
-    case A:                                                                                        \
-        if constexpr (A < MT) acc2 = lbi_pass3<P, MT, A>(sufb, preb, W, mid, Qv, cnt_in);          \
-        break;
-                LBI_PASS3_CASE(0) LBI_PASS3_CASE(1) LBI_PASS3_CASE(2) LBI_PASS3_CASE(3)
-                LBI_PASS3_CASE(4) LBI_PASS3_CASE(5) LBI_PASS3_CASE(6) LBI_PASS3_CASE(7)
-#undef LBI_PASS3_CASE
-                default: break;
-            }
-        }
-    } else {
-#pragma unroll 1
-        for (int t = 0; t < cnt_in; ++t) {
-            const int i = i0 + t;
-            const int a = max(0, i - w), b = min(n - 1, i + w);
-            const int ca = a >> lg, pa = a & (m - 1);
-            const int cb = b >> lg, pb = b & (m - 1);
-            float uu, ll;
-            if (ca == cb && pa > 0 && pb < m - 1 && b < n - 1) {
-                // window strictly inside one chunk (only when 2w + 2 < m)
-                uu = NEG;
-                ll = POS;
-                for (int k = pa; k <= pb; ++k) {
-                    const float hv = Hs[k * 32 + ca];
-                    uu = fmaxf(uu, hv);
-                    ll = fminf(ll, hv);
-                }
-            } else if (ca == cb) {
-                // the window starts the chunk (prefix) or reaches its end (suffix)
-                const float2 v = (pa == 0) ? Pre[pb * W + PLc + cb] : Suf[pa * W + PLc + ca];
-                uu = v.x;
-                ll = v.y;
-            } else {
-                const float2 sa = Suf[pa * W + PLc + ca], pb2 = Pre[pb * W + PLc + cb];
-                uu = fmaxf(sa.x, pb2.x);
-                ll = fminf(sa.y, pb2.y);
-                const int cnt = cb - ca - 1;
-                if (cnt > 0) {
-                    const int k = 31 - __clz(cnt);
-                    const float2 t1 = T[k * 32 + ca + 1], t2 = T[k * 32 + cb - (1 << k)];
-                    uu = max3f(uu, t1.x, t2.x);
-                    ll = min3f(ll, t1.y, t2.y);
-                }
-            }
-            acc2 = acc_dist<P>(acc2, Qv.Y(t, lane, m), ll, uu);
-        }
-    }
-    __syncwarp();  // scratch is reused by the next pair
-    return warp_sum(acc1 + acc2);
-}
-
-// All N candidates against one query, no threshold.
-template <int P, int MT>
-__global__ void __launch_bounds__(128)
-k_lbi_single(const float *__restrict__ cand, int64_t N, const float *__restrict__ q,
-             const float *__restrict__ U, const float *__restrict__ L, int n, int w,
-             float *__restrict__ out, bool vec) {
-    extern __shared__ __align__(16) float sm[];
-    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float *sq = sm;
-    float *scratch = sm + lbi_query_floats(n) + (size_t)wid * lbi_scratch_floats(n, w);
-    LbiQuery<MT> Qv;
-    lbi_load_query<MT>(Qv, q, U, L, n, sq);
-    lbi_init_scratch<MT>(scratch, n, w);
-    __syncthreads();
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + wid; c < N; c += warps) {
-        float v = warp_lb_improved<P, MT>(cand + c * n, Qv, n, w, scratch, vec);
+    for (int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < N; c += warps) {
+        const int64_t o = c * n;
+        float a1 = 0.0f, a2 = 0.0f;
+        for (int i = lane; i < n; i += 32) {
+            a1 = acc_dist<P>(a1, __ldg(cand + o + i), __ldg(L + i), __ldg(U + i));
+            a2 = acc_dist<P>(a2, __ldg(q + i), fminf(__ldg(XL + o + i), __ldg(LU + i)),
+                             fmaxf(__ldg(XU + o + i), __ldg(UL + i)));
+        }
+        const float v = warp_sum(a1 + a2);
         if (lane == 0) out[c] = root_p(v, P);
     }
 }
 
-template <int P, int MT>
-static void lbi_single_go(const float *cand, int64_t N, const float *q, const float *U, const float *L, int n,
-                          int w, float *out, bool vec, cudaStream_t s) {
-    const int64_t per_warp = (int64_t)lbi_scratch_floats(n, w) * sizeof(float);
-    const int64_t per_query = (int64_t)lbi_query_floats(n) * sizeof(float);
-    const int warps = (int)std::min<int64_t>(4, std::max<int64_t>(1, (200 * 1024 - per_query) / per_warp));
-    const size_t smem = (size_t)per_query + (size_t)warps * per_warp;
-    const int blocks = (int)std::min<int64_t>((N + warps - 1) / warps, (int64_t)device_sm_count() * 16);
-    cudaFuncSetAttribute(k_lbi_single<P, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_lbi_single<P, MT><<<blocks, warps * 32, smem, s>>>(cand, N, q, U, L, n, w, out, vec);
-}
-
-template <int P>
-static void lbi_single_dispatch(const float *cand, int64_t N, const float *q, const float *U, const float *L,
-                                int n, int w, float *out, bool vec, cudaStream_t s) {
-    switch (lbi_geom(n).m) {
-        case 1: lbi_single_go<P, 1>(cand, N, q, U, L, n, w, out, vec, s); break;
-        case 2: lbi_single_go<P, 2>(cand, N, q, U, L, n, w, out, vec, s); break;
-        case 4: lbi_single_go<P, 4>(cand, N, q, U, L, n, w, out, vec, s); break;
-        case 8: lbi_single_go<P, 8>(cand, N, q, U, L, n, w, out, vec, s); break;
-        default: lbi_single_go<P, 0>(cand, N, q, U, L, n, w, out, vec, s); break;
-    }
-}
-
-cudaError_t launch_lbi_single(const float *cand, int64_t N, const float *q, const float *U,
-                              const float *L, int n, int w, int p, float *out, cudaStream_t s) {
+cudaError_t launch_lbi_single(const float *cand, int64_t N, const float *q, const float *U, const float *L,
+                              const float *XU, const float *XL, const float *UL, const float *LU, int n, int p,
+                              float *out, cudaStream_t s) {
     if (N <= 0) return cudaSuccess;
-    w = std::min(w, n - 1);
-    const bool vec = (n % 4 == 0) && ((reinterpret_cast<uintptr_t>(cand) & 15) == 0);
-    if (p == 1) lbi_single_dispatch<1>(cand, N, q, U, L, n, w, out, vec, s);
-    else lbi_single_dispatch<2>(cand, N, q, U, L, n, w, out, vec, s);
+    const int blocks = (int)std::min<int64_t>((N + 7) / 8, (int64_t)device_sm_count() * 16);
+    if (p == 1) k_lbi_single<1><<<blocks, 256, 0, s>>>(cand, N, q, U, L, XU, XL, UL, LU, n, out);
+    else k_lbi_single<2><<<blocks, 256, 0, s>>>(cand, N, q, U, L, XU, XL, UL, LU, n, out);
     return cudaGetLastError();
 }
 
