@@ -406,3 +406,14 @@ def test_classification_nearest_neighbours_match_the_oracle(api, p):
         if nn[t] != oi[0, 0]:  # a near-tie fp32 cannot order: same distance
             assert close(oracle.dtw(db[nn[t]], ts[t], w, oracle_p(p)), od[0, 0]), (t, nn[t], oi[0, 0])
         assert close(d[t, nn[t]], od[0, 0]), t
+
+
+@pytest.mark.parametrize("p", [1, 2])
+@pytest.mark.parametrize("n,w", [(200, 20), (201, 20), (301, 30), (1002, 100)])
+def test_knn_filter_layouts(api, p, n, w):
+    # the filter's row layouts besides the compiled fast one: 8 elements per
+    # lane with rows shorter than 256 (16-byte pieces, then 4-byte copies when
+    # n % 4 != 0) and streamed long rows with 4-byte loads (n % 4 != 0)
+    db = synth.random_walks(600, n, seed=90 + n)
+    qs = synth.random_walks(5, n, seed=91 + n, stream=synth.STREAM_QUERY)
+    _knn_case(api, db, qs, w, p, 2)
