@@ -243,6 +243,11 @@ def stage_rates(prof, a, steps, peaks, stats):
     if prof["dtw"]["launches"] and stats.get("dtw_cells"):
         cells = stats["dtw_cells"] / (ms("dtw") / 1e3)
         out["dtw"] = {"ms": ms("dtw"), "cells_per_s": cells, "frac_alu": cells * 3 / 1e12 / alu_peak}
+        if stats.get("dtw_lane_rows"):
+            # thread-per-pair kernel: share of the rows its warps stepped that
+            # belonged to a live pair (a warp steps until its longest pair ends)
+            rows = stats["dtw_cells"] / (2 * min(a.w, a.n - 1) + 1)
+            out["dtw"]["lane_use"] = rows / stats["dtw_lane_rows"]
     if prof["seed_dtw"]["launches"] and stats.get("seed_cells"):
         cells = stats["seed_cells"] / (ms("seed_dtw") / 1e3)
         out["seed_dtw"] = {"ms": ms("seed_dtw"), "cells_per_s": cells, "frac_alu": cells * 3 / 1e12 / alu_peak}

@@ -70,6 +70,9 @@ typedef struct {
     int64_t dtw_abandoned;   /* of which abandoned early (row minimum above the threshold) */
     int64_t dtw_cells;       /* band cells evaluated by those DTWs (rows x (2w+1)) */
     int64_t seed_cells;      /* band cells evaluated by the seed DTWs */
+    int64_t dtw_lane_rows;   /* thread-per-pair DTW: rows its warps stepped, 32 per row of a
+                                chunk's longest pair (rows of dtw_cells / this = lane use);
+                                0 when the warp path ran the stage */
 } dtw_stats;
 
 typedef struct {

@@ -47,6 +47,7 @@ class Stats(ctypes.Structure):
         ("dtw_abandoned", ctypes.c_int64),
         ("dtw_cells", ctypes.c_int64),
         ("seed_cells", ctypes.c_int64),
+        ("dtw_lane_rows", ctypes.c_int64),
     ]
 
     def as_dict(self) -> dict:

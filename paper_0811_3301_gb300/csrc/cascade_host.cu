@@ -384,6 +384,7 @@ void cascade_stats(const CascadePlan &pl, int64_t Q, const unsigned long long *h
     st->dtw_abandoned += (int64_t)h[CNT_DTW_ABANDONED];
     st->dtw_cells += (int64_t)h[CNT_DTW_ROWS] * (2 * pl.we + 1);
     st->seed_cells += (int64_t)h[CNT_NUM + CNT_DTW_ROWS] * (2 * pl.we + 1);
+    st->dtw_lane_rows += (int64_t)h[CNT_DTW_LANE_ROWS];
 }
 
 }  // namespace dtwk

@@ -260,6 +260,7 @@ enum {
     CNT_DTW_ABANDONED = 4,  // of which abandoned early
     CNT_DTW_ROWS = 5,       // DP rows evaluated
     CNT_SUMMARY_PASS = 6,   // non-seed pairs with piecewise-sum bound <= thr
+    CNT_DTW_LANE_ROWS = 7,  // thread-per-pair DTW: 32 x the longest pair's rows, per chunk of 32
     CNT_NUM = 8
 };
 

@@ -266,7 +266,7 @@ k_dtw_reg4(DtwJob j, int e, int wl, bool xvec) {
     const int n = j.n;
     const int ylen = j.qc.ylen;
     if (j.npairs_dev) j.npairs = (int64_t)*j.npairs_dev;
-    unsigned long long n_skip = 0, n_comp = 0, n_aband = 0, n_rows = 0;
+    unsigned long long n_skip = 0, n_comp = 0, n_aband = 0, n_rows = 0, n_lane_rows = 0;
     for (;;) {
         unsigned long long chunk = 0;
         if (lane == 0) chunk = atomicAdd(j.cursor, 1ull);
@@ -286,6 +286,7 @@ k_dtw_reg4(DtwJob j, int e, int wl, bool xvec) {
                 ++n_skip;
             }
         }
+        int my_rows = 0;
         if (valid) {
             ++n_comp;
             const float *x = j.db + (int64_t)c * n;
@@ -376,6 +377,7 @@ k_dtw_reg4(DtwJob j, int e, int wl, bool xvec) {
                 }
             }
             n_rows += rows;
+            my_rows = rows;
             float d = kInf;
 #pragma unroll
             for (int k = 0; k < C; ++k) d = sel_eq(k, wl, D[k], d);
@@ -387,6 +389,8 @@ k_dtw_reg4(DtwJob j, int e, int wl, bool xvec) {
             j.res[pi] = j.root_out ? root_p(d, P) : d;
             if (!abandoned && j.bsf) update_threshold(j.bsf, j.gmin, j.k, q, c % j.k, d);
         }  // valid
+        // the warp steps until the chunk's longest pair ends
+        n_lane_rows += 32ull * __reduce_max_sync(0xffffffffu, (unsigned)my_rows);
     }
     if (j.counters) {
         n_skip = __reduce_add_sync(0xffffffffu, (unsigned)n_skip);
@@ -399,6 +403,7 @@ k_dtw_reg4(DtwJob j, int e, int wl, bool xvec) {
             if (n_skip) atomicAdd(j.counters + CNT_DTW_SKIP, n_skip);
             if (n_comp) atomicAdd(j.counters + CNT_DTW_COMPUTED, n_comp);
             if (n_aband) atomicAdd(j.counters + CNT_DTW_ABANDONED, n_aband);
+            if (n_lane_rows) atomicAdd(j.counters + CNT_DTW_LANE_ROWS, n_lane_rows);
         }
     }
 }
