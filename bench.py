@@ -11,8 +11,11 @@ LB_Improved of the LB_Keogh survivors, DTW of the LB_Improved survivors and
 the ordered top-k.  The same step under DTW_2 is reported beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py --data shapes --N 50000 --n 1024 --Q 500 --w 102   # shape-like series
   python bench.py --workload batched   # mixed-length batches through the index
   python bench.py --workload serve     # Poisson arrivals through the request server
+  python bench.py --workload triangle  # App. B: triangle-inequality violations
+  python bench.py --workload classify  # App. C: 1-NN classification, DTW_1/2/4/inf
 
 Under torchrun each rank holds the whole database and runs its own batch of
 queries (weak scaling; the only collectives are the timing barrier and the
