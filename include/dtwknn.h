@@ -274,8 +274,8 @@ enum {
 };
 
 /* Cascade parameters of one (n, w, k); see dtw_options for parts, seeds and dtw_path.
- * seg_len: candidates per filter segment (512, 1024 or 2048; 0: 2048 for n <= 256,
- * else 1024). ms: time of the
+ * seg_len: candidates per filter segment (512, 1024, 2048 or 4096; 0: for n <= 256
+ * 4096 when the bucket holds 65,536 series or more, else 2048; 1024 for longer series). ms: time of the
  * tuning sample in milliseconds, or -1 when the values are the defaults. */
 typedef struct {
     int32_t parts;

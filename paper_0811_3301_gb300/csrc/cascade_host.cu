@@ -146,8 +146,9 @@ CascadePlan make_plan(int64_t N, int64_t Qmax, int n, int w, int p, int k, const
     if (Qc < 1) Qc = 1;
     pl.Qc = Qc;
     // filter segments: longer ones amortise more of a CTA's setup; for series
-    // up to 256 (chunks in registers) 2048 measured fastest, 1024 otherwise
-    pl.seg_len = seg_len > 0 ? seg_len : (n <= 256 ? 2048 : 1024);
+    // up to 256 (chunks in registers) 4096 measured fastest on large databases
+    // (2048 keeps enough CTAs on smaller ones), 1024 for longer series
+    pl.seg_len = seg_len > 0 ? seg_len : (n <= 256 ? (N >= 65536 ? 4096 : 2048) : 1024);
     pl.dtw_path = o.dtw_path;
     // The DTW stage takes every query's lowest-bound pairs first (a multiple
     // of 32, at least 2k), so that each query's threshold falls to near its

@@ -53,7 +53,8 @@ struct CascadeWs {
 
 // o.parts: 0 = default (n/8 for n >= 64, else off), -1 = off, else d.
 // o.seeds: 0 = default (16); clamped to [k, 32] and to N.
-// seg_len: 0 = default (2048 for n <= 256, else 1024); filter_warps: 0 = default.
+// seg_len: 0 = default (for n <= 256: 4096 when N >= 65536, else 2048; 1024 for
+// longer series); filter_warps: 0 = default.
 CascadePlan make_plan(int64_t N, int64_t Qmax, int n, int w, int p, int k, const dtw_options &o,
                       int seg_len = 0, int filter_warps = 0);
 CascadeWs carve_ws(const CascadePlan &pl, Carve &cv);

@@ -550,7 +550,7 @@ dtw_status tune_group(dtw_index *ix, int b, int w, int k, const float *qdev, int
     std::vector<int> seeds_c;
     for (int sd : {std::max(k, 4), 8, 16, 32})
         if (sd >= k && sd <= 32 && std::find(seeds_c.begin(), seeds_c.end(), sd) == seeds_c.end()) seeds_c.push_back(sd);
-    const std::vector<int> seg_c{512, 1024, 2048};
+    const std::vector<int> seg_c{512, 1024, 2048, 4096};
     std::vector<int> path_c{1};
     if (dtw_lanes_cl(n, we) > 0) {
         path_c.push_back(2);
@@ -848,11 +848,12 @@ dtw_status dtw_index_set_tuning(dtw_index *ix, int32_t n, int32_t w, int32_t k, 
     set_error_message("");
     if (!ix || !t) return ix_fail(DTW_ERR_INVALID_ARG, "null pointer");
     if (t->parts < -1 || t->parts > n || t->seeds < 0 || t->seeds > 32 ||
-        (t->seg_len != 0 && t->seg_len != 512 && t->seg_len != 1024 && t->seg_len != 2048) || t->dtw_path < 0 ||
+        (t->seg_len != 0 && t->seg_len != 512 && t->seg_len != 1024 && t->seg_len != 2048 && t->seg_len != 4096) ||
+        t->dtw_path < 0 ||
         t->dtw_path > 3 ||
         t->filter_warps < 0 || t->filter_warps > 8)
         return ix_fail(DTW_ERR_INVALID_ARG, "tuning out of range (parts in [-1, n], seeds in [0, 32], seg_len "
-                                            "0/512/1024/2048, dtw_path 0-3, filter_warps 0-8)");
+                                            "0/512/1024/2048/4096, dtw_path 0-3, filter_warps 0-8)");
     if (w < 0 || k < 1 || k > DTW_MAX_K) return ix_fail(DTW_ERR_INVALID_ARG, "w or k out of range");
     std::lock_guard<std::mutex> lk(ix->mu);
     if (find_bucket(ix, n) < 0) return ix_fail(DTW_ERR_NO_BUCKET, "no bucket of length %d", n);

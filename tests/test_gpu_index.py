@@ -147,7 +147,7 @@ def test_autotune_changes_speed_not_results(api, dbs, batch, reference):
         np.testing.assert_array_equal(gd.cpu().numpy(), reference[1])
         for n in BUCKETS:
             t = ix.get_tuning(n, n // 10, 1)
-            assert t["ms"] > 0 and t["seg_len"] in (0, 512, 1024, 2048)
+            assert t["ms"] > 0 and t["seg_len"] in (0, 512, 1024, 2048, 4096)
             assert t["parts"] == -1 or 1 <= t["parts"] <= n
         # explicit tuning: every parameter set gives the same answer
         n = 128
