@@ -48,7 +48,7 @@ METRIC = "exact 1-NN DTW queries/s (LB_Improved cascade)"
 # DRAM bytes per launch of the filter kernel at the default workload, from one
 # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum); valid for that
 # workload and the kernel as captured (profiles/k_lbi_filter_traffic_*.md)
-FILTER_TRAFFIC = {"workload": (100_000, 256, 25, 1000), "bytes": 1.26196e9,
+FILTER_TRAFFIC = {"workload": (100_000, 256, 25, 1000), "bytes": 1.30071e9,
                   "source": "profiles/k_lbi_filter_traffic_rw100k_n256_w25_q1000.md"}
 L2_BYTES = 129 * 2**20
 
