@@ -68,7 +68,7 @@ def test_bruteforce_enumerator_counts_delannoy():
     assert cnt == 48639
 
 
-@pytest.mark.parametrize("p", [1, 2, 0])
+@pytest.mark.parametrize("p", [1, 2, 4, 0])
 def test_dtw_matches_bruteforce_integer_series(p):
     rng = np.random.default_rng(11)
     for n in range(1, 8):
@@ -79,7 +79,7 @@ def test_dtw_matches_bruteforce_integer_series(p):
                 assert oracle.dtw_pow(x, y, w, p) == brute_dtw_pow(x, y, w, p), (n, w, x, y)
 
 
-@pytest.mark.parametrize("p", [1, 2])
+@pytest.mark.parametrize("p", [1, 2, 4])
 def test_dtw_matches_bruteforce_real_series(p):
     rng = np.random.default_rng(12)
     for n in (5, 8):
@@ -140,7 +140,7 @@ def _walks(count, n, seed):
     return synth.random_walks(count, n, seed=seed)
 
 
-@pytest.mark.parametrize("p", [1, 2, 0])
+@pytest.mark.parametrize("p", [1, 2, 4, 0])
 def test_w0_is_lp_distance(p):
     for x, y in zip(_walks(5, 40, 1), _walks(5, 40, 2)):
         d = np.abs(x.astype(np.float64) - y.astype(np.float64))
@@ -161,7 +161,7 @@ def test_prop1_value_separated_dtw1_is_l1():
             assert oracle.dtw_pow(y, x, w, 1) == pytest.approx(l1, rel=1e-12)
 
 
-@pytest.mark.parametrize("p", [1, 2, 0])
+@pytest.mark.parametrize("p", [1, 2, 4, 0])
 def test_constant_series_lemma(p):
     rng = np.random.default_rng(6)
     for trial in range(6):
@@ -172,6 +172,15 @@ def test_constant_series_lemma(p):
         ref = d.max() if p == 0 else np.sum(d ** p)
         for w in (0, 2, n):
             assert oracle.dtw_pow(x, y, w, p) == pytest.approx(ref, rel=1e-12)
+
+
+def test_dtw_nonincreasing_in_p():
+    # App. A: DTW_p (root taken) does not increase with p, DTW_inf the smallest
+    for x, y in zip(_walks(6, 30, 7), _walks(6, 30, 8)):
+        for w in (0, 3, 30):
+            vals = [oracle.dtw(x, y, w, p) for p in (1, 2, 4, 0)]
+            for a, b in zip(vals, vals[1:]):
+                assert a >= b * (1 - 1e-12), (w, vals)
 
 
 @pytest.mark.parametrize("p", [1, 2])
