@@ -606,18 +606,27 @@ def serve_run(api, ix, lens, queries, ks, arrivals, **cfg):
     info = srv.info()
     srv.close()
     comp = [got[t] for t in tickets if t in got]
+    out = latency_summary(comp)
+    out.update({"offered_qps": Q / float(arrivals[-1]) if Q > 1 else None, "requests": Q,
+                "batches": info["batches"], "mean_batch": len(comp) / max(1, info["batches"]),
+                "max_batch": info["max_batch_seen"], "max_inflight_batches": info["max_inflight_batches"]})
+    return out, comp
+
+
+def latency_summary(comp):
+    """Latency (completion - arrival) and queueing delay (admission - arrival)
+    percentiles in ms, and throughput over the span from the first arrival to
+    the last completion, of server completions (dicts with arrival_ns,
+    admit_ns, done_ns and status)."""
     lat = np.array([(c["done_ns"] - c["arrival_ns"]) / 1e6 for c in comp])
     wait = np.array([(c["admit_ns"] - c["arrival_ns"]) / 1e6 for c in comp])
     first = min(c["arrival_ns"] for c in comp)
     last = max(c["done_ns"] for c in comp)
-    return {"offered_qps": Q / float(arrivals[-1]) if Q > 1 else None, "requests": Q, "completed": len(comp),
-            "failed": sum(1 for c in comp if c["status"] != 0),
+    return {"completed": len(comp), "failed": sum(1 for c in comp if c["status"] != 0),
             "throughput_qps": len(comp) / ((last - first) / 1e9),
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-            "mean_ms": float(lat.mean()), "queue_p50_ms": float(np.percentile(wait, 50)),
-            "queue_p99_ms": float(np.percentile(wait, 99)), "batches": info["batches"],
-            "mean_batch": len(comp) / max(1, info["batches"]), "max_batch": info["max_batch_seen"],
-            "max_inflight_batches": info["max_inflight_batches"]}, comp
+            "p999_ms": float(np.percentile(lat, 99.9)), "mean_ms": float(lat.mean()),
+            "queue_p50_ms": float(np.percentile(wait, 50)), "queue_p99_ms": float(np.percentile(wait, 99))}
 
 
 def run_serve(a):
@@ -672,9 +681,10 @@ def run_serve(a):
     sampler.stop()
     best = max(runs, key=lambda r: r["batched"]["throughput_qps"])
     return {
-        "metric": "exact k-NN DTW queries/s and p50/p99 latency, Poisson arrivals, continuous batching",
+        "metric": "exact k-NN DTW queries/s and p50/p99/p99.9 latency, Poisson arrivals, continuous batching",
         "value": best["batched"]["throughput_qps"], "unit": "queries/s", "n_gpus": 1,
         "p50_ms": best["batched"]["p50_ms"], "p99_ms": best["batched"]["p99_ms"],
+        "p999_ms": best["batched"]["p999_ms"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded random walks)",
         "config": {"workload": "serving: Poisson arrivals at %s q/s, query lengths from %s, resident random walks %s, "

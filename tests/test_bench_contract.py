@@ -25,3 +25,19 @@ def test_reference_arm_prints_one_contract_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert d["config"]["N"] == 1500 and d["config"]["n"] == 64 and "workload" in d["config"]
+
+
+def test_latency_summary():
+    sys.path.insert(0, ROOT)
+    import bench
+
+    # 1,000 requests arriving 1 ms apart, each done 2 ms after arrival (the
+    # last one 12 ms), admitted 0.5 ms after arrival
+    comp = [{"arrival_ns": i * 1_000_000, "admit_ns": i * 1_000_000 + 500_000,
+             "done_ns": i * 1_000_000 + (12_000_000 if i == 999 else 2_000_000), "status": 0} for i in range(1000)]
+    comp[3]["status"] = 4
+    s = bench.latency_summary(comp)
+    assert s["completed"] == 1000 and s["failed"] == 1
+    assert s["p50_ms"] == 2.0 and s["p99_ms"] == 2.0 and 2.0 < s["p999_ms"] < 12.0
+    assert s["queue_p50_ms"] == 0.5
+    assert abs(s["throughput_qps"] - 1000 / 1.011) < 1e-6
