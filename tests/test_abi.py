@@ -133,3 +133,23 @@ def test_server_rejects_bad_arguments_on_host(native):
     assert native.lib.dtw_server_destroy(None) == 0
     t0 = native.lib.dtw_monotonic_ns()
     assert native.lib.dtw_monotonic_ns() >= t0 > 0
+
+
+def test_header_compiles_as_c99_and_cxx(tmp_path):
+    # the C ABI must be usable from plain C (no C++ types in the signatures)
+    import shutil
+    import subprocess
+
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not available")
+    src = tmp_path / "use_abi.c"
+    src.write_text('#include "dtwknn.h"\n'
+                   "int main(void) { dtw_stats s; dtw_options o; dtw_tuning t; (void)s; (void)o; (void)t;\n"
+                   "  return DTW_P_INF + DTW_OK; }\n")
+    inc = os.path.join(ROOT, "include")
+    for cmd in ([gcc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I", inc, "-fsyntax-only", str(src)],
+                [shutil.which("g++") or "g++", "-std=c++17", "-Wall", "-Werror", "-I", inc, "-fsyntax-only",
+                 "-x", "c++", str(src)]):
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
