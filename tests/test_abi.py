@@ -92,6 +92,23 @@ def test_single_op_calls_validate_on_host(native):
     assert native.lib.lb_keogh(buf, 0, buf, buf, 16, 1, buf, None) == 0
 
 
+def test_p_values_per_entry_point(native):
+    # dtw_band (and dtw_band_noalloc) take p = 1, 2, 4 and DTW_P_INF (0); the
+    # bounds and the cascade take p = 1, 2 only
+    buf = (ctypes.c_float * 16)()
+    idx = (ctypes.c_int64 * 4)()
+    for p in (1, 2, 4, 0):
+        assert native.lib.dtw_band(buf, buf, 0, 0, 16, 1, p, math.inf, buf, None) == 0, p  # N = 0: no work
+        assert native.lib.dtw_band_noalloc(buf, buf, 0, 0, 16, 1, p, math.inf, buf, None) == 0, p
+    for p in (3, 5, -1):
+        assert native.lib.dtw_band(buf, buf, 0, 0, 16, 1, p, math.inf, buf, None) == 1, p
+        assert native.lib.dtw_band_noalloc(buf, buf, 0, 0, 16, 1, p, math.inf, buf, None) == 1, p
+    for p in (4, 0):
+        st, text = _status(native, lambda: native.lib.knn_search(buf, 1, buf, 1, 16, 1, p, 1, idx, buf, None, None))
+        assert st == 1 and "p=" in text, text
+        assert native.lib.lb_keogh(buf, 1, buf, buf, 16, p, buf, None) == 1
+
+
 def test_bad_mode_and_slack_rejected(native):
     buf = (ctypes.c_float * 16)()
     idx = (ctypes.c_int64 * 4)()
