@@ -68,11 +68,14 @@ typedef struct {
     int64_t pruned_improved; /* pairs discarded by LB_Improved */
     int64_t dtw_computed;    /* non-seed pairs whose DTW was started */
     int64_t dtw_abandoned;   /* of which abandoned early (row minimum above the threshold) */
-    int64_t dtw_cells;       /* band cells evaluated by those DTWs (rows x (2w+1)) */
-    int64_t seed_cells;      /* band cells evaluated by the seed DTWs */
+    int64_t dtw_cells;       /* in-band cells (|i - j| <= w) of the DP rows those DTWs evaluated;
+                                a completed pair has n (2w + 1) - w (w + 1) */
+    int64_t seed_cells;      /* in-band cells evaluated by the seed DTWs */
     int64_t dtw_lane_rows;   /* thread-per-pair DTW: rows its warps stepped, 32 per row of a
-                                chunk's longest pair (rows of dtw_cells / this = lane use);
+                                chunk's longest pair (dtw_rows / this = lane use);
                                 0 when the warp path ran the stage */
+    int64_t dtw_rows;        /* DP rows evaluated by the non-seed DTWs */
+    int64_t seed_rows;       /* DP rows evaluated by the seed DTWs */
 } dtw_stats;
 
 typedef struct {
@@ -225,8 +228,9 @@ dtw_status dtw_profile_read(dtw_profile *out, int32_t reset);
  * query copies: about 16 * (n + w + 2*C + 8) bytes per query row, with C the band
  * slot count, plus 256 bytes) does not fit returns DTW_ERR_INVALID_ARG.  All
  * calls share the array, so calls that overlap on the GPU race.  The first
- * call on a device looks up the array's device address; make it before any
- * stream capture.
+ * call in each CUDA context of a device (the primary context is created anew
+ * after cudaDeviceReset) looks up the array's device address and keeps it for
+ * that context's later calls; make that first call before any stream capture.
  */
 dtw_status dtw_band_noalloc(const float *x, const float *y, int64_t N, int32_t y_stride,
                             int32_t n, int32_t w, int32_t p, float threshold, float *out,

@@ -118,40 +118,46 @@ double oracle_lb_keogh_pow(const float *x, const double *U, const double *L, int
 }
 
 /*
- * LB_Improved_p(x, y)^p = LB_Keogh_p(x, y)^p + LB_Keogh_p(y, H(x, y))^p
- * (Sec. 8).  The second term measures y against the envelope, with the same
- * w, of the projection x' = H(x, y).  U, L are the envelope of y.
- * If first_pass is non-null it receives LB_Keogh_p(x, y)^p.
+ * The second term of LB_Improved (Sec. 8): LB_Keogh_p(y, H(x, y))^p, the
+ * distance from y to the envelope, with the same w, of the projection
+ * H(x, y) of x onto the envelope U = U(y), L = L(y) (Eq. 1).
  */
-double oracle_lb_improved_pow(const float *x, const float *y, const double *U, const double *L,
-                              int64_t n, int64_t w, int p, double *first_pass)
+double oracle_lb_improved_second_pow(const float *x, const float *y, const double *U, const double *L,
+                                     int64_t n, int64_t w, int p)
 {
     w = clamp_w(n, w);
     double *xd = (double *)malloc((size_t)n * sizeof(double));
     double *yd = (double *)malloc((size_t)n * sizeof(double));
-    double *xp = (double *)malloc((size_t)n * sizeof(double));
-    double *Up = (double *)malloc((size_t)n * sizeof(double));
-    double *Lp = (double *)malloc((size_t)n * sizeof(double));
+    double *H = (double *)malloc((size_t)n * sizeof(double));
+    double *UH = (double *)malloc((size_t)n * sizeof(double));
+    double *LH = (double *)malloc((size_t)n * sizeof(double));
     for (int64_t i = 0; i < n; ++i) {
         xd[i] = (double)x[i];
         yd[i] = (double)y[i];
     }
-    /* first pass: x' = H(x, y) and LB_Keogh_p(x, y)^p */
-    oracle_projection(xd, U, L, n, xp);
-    double beta = 0.0;
-    for (int64_t i = 0; i < n; ++i)
-        beta += abs_pow(xd[i], xp[i], p);
-    if (first_pass)
-        *first_pass = beta;
-    /* second pass: envelope of x', then LB_Keogh_p(y, x')^p */
-    oracle_envelope_d(xp, n, w, Up, Lp);
-    beta += oracle_lb_keogh_pow_d(yd, Up, Lp, n, p);
+    oracle_projection(xd, U, L, n, H);
+    oracle_envelope_d(H, n, w, UH, LH);
+    double r = oracle_lb_keogh_pow_d(yd, UH, LH, n, p);
     free(xd);
     free(yd);
-    free(xp);
-    free(Up);
-    free(Lp);
-    return beta;
+    free(H);
+    free(UH);
+    free(LH);
+    return r;
+}
+
+/*
+ * LB_Improved_p(x, y)^p = LB_Keogh_p(x, y)^p + LB_Keogh_p(y, H(x, y))^p
+ * (Sec. 8), U, L the envelope of y.  If first_pass is non-null it receives
+ * the first term, LB_Keogh_p(x, y)^p.
+ */
+double oracle_lb_improved_pow(const float *x, const float *y, const double *U, const double *L,
+                              int64_t n, int64_t w, int p, double *first_pass)
+{
+    double first = oracle_lb_keogh_pow(x, U, L, n, p);
+    if (first_pass)
+        *first_pass = first;
+    return first + oracle_lb_improved_second_pow(x, y, U, L, n, w, p);
 }
 
 /*
@@ -312,12 +318,16 @@ void oracle_knn_bruteforce(const float *db, int64_t N, const float *y, int64_t n
 }
 
 /*
- * The sequential scans of Algorithm 2 (mode 0: LB_Keogh, then DTW) and
- * Algorithm 3 (mode 1: LB_Keogh, then LB_Improved, then DTW), in candidate
- * order, generalised from 1-NN to k-NN: b is the k-th best DTW_p^p found so
- * far (+inf until k candidates have been evaluated) and a candidate goes on
- * to the next stage only while its bound is below b, as in both algorithms.
- * Comparisons are in power space (beta against DTW_p^p).
+ * Exact k-NN by one pass over the candidates in index order with lower-bound
+ * pruning: the scans of Algorithm 2 (mode 0) and Algorithm 3 (mode 1) of
+ * Sec. 7 and 8, generalised from 1-NN to k-NN.  Let b be the k-th smallest
+ * DTW_p^p among the candidates evaluated so far (+inf until there are k).
+ * Since LB_Keogh_p^p <= LB_Improved_p^p <= DTW_p^p (Sec. 7, Sec. 8), a
+ * candidate with a bound >= b cannot displace any of the current k (on a
+ * tie the lower index, already held, wins), so its DTW is not needed.  Mode
+ * 0 tests LB_Keogh alone; mode 1 tests LB_Keogh and, if that passes,
+ * LB_Improved = LB_Keogh + the second term.  Bounds and b are compared in
+ * power space.
  *
  * stats (nullable) receives: [0] candidates, [1] discarded by LB_Keogh,
  * [2] discarded by LB_Improved, [3] full DTW computed.
@@ -328,47 +338,30 @@ void oracle_knn_cascade(const float *db, int64_t N, const float *y, int64_t n, i
     w = clamp_w(n, w);
     double *U = (double *)malloc((size_t)n * sizeof(double));
     double *L = (double *)malloc((size_t)n * sizeof(double));
-    double *xd = (double *)malloc((size_t)n * sizeof(double));
-    double *yd = (double *)malloc((size_t)n * sizeof(double));
-    double *xp = (double *)malloc((size_t)n * sizeof(double));
-    double *Up = (double *)malloc((size_t)n * sizeof(double));
-    double *Lp = (double *)malloc((size_t)n * sizeof(double));
     double *kd = (double *)malloc((size_t)k * sizeof(double));
     int64_t *ki = (int64_t *)malloc((size_t)k * sizeof(int64_t));
     int64_t st[4] = {0, 0, 0, 0};
 
-    for (int64_t i = 0; i < n; ++i)
-        yd[i] = (double)y[i];
-    oracle_envelope_d(yd, n, w, U, L); /* once per query */
+    oracle_envelope(y, n, w, U, L); /* the query's envelope, once */
     topk_init(kd, ki, k);
-
     for (int64_t c = 0; c < N; ++c) {
         const float *x = db + c * n;
-        double b = kd[k - 1];
+        const double b = kd[k - 1];
         st[0] += 1;
-        /* copy x to x' and accumulate LB_Keogh (first pass) */
-        for (int64_t i = 0; i < n; ++i)
-            xd[i] = (double)x[i];
-        oracle_projection(xd, U, L, n, xp);
-        double beta = 0.0;
-        for (int64_t i = 0; i < n; ++i)
-            beta += abs_pow(xd[i], xp[i], p);
-        if (!(beta < b)) {
+        double bound = oracle_lb_keogh_pow(x, U, L, n, p);
+        if (!(bound < b)) {
             st[1] += 1;
             continue;
         }
         if (mode == 1) {
-            /* second pass: envelope of x', distance from y to it */
-            oracle_envelope_d(xp, n, w, Up, Lp);
-            beta += oracle_lb_keogh_pow_d(yd, Up, Lp, n, p);
-            if (!(beta < b)) {
+            bound += oracle_lb_improved_second_pow(x, y, U, L, n, w, p);
+            if (!(bound < b)) {
                 st[2] += 1;
                 continue;
             }
         }
         st[3] += 1;
-        double t = oracle_dtw_pow(x, y, n, w, p);
-        topk_insert(kd, ki, k, t, c);
+        topk_insert(kd, ki, k, oracle_dtw_pow(x, y, n, w, p), c);
     }
     for (int j = 0; j < k; ++j) {
         out_idx[j] = ki[j];
@@ -378,11 +371,6 @@ void oracle_knn_cascade(const float *db, int64_t N, const float *y, int64_t n, i
         memcpy(stats, st, sizeof(st));
     free(U);
     free(L);
-    free(xd);
-    free(yd);
-    free(xp);
-    free(Up);
-    free(Lp);
     free(kd);
     free(ki);
 }

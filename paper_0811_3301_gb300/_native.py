@@ -48,6 +48,8 @@ class Stats(ctypes.Structure):
         ("dtw_cells", ctypes.c_int64),
         ("seed_cells", ctypes.c_int64),
         ("dtw_lane_rows", ctypes.c_int64),
+        ("dtw_rows", ctypes.c_int64),
+        ("seed_rows", ctypes.c_int64),
     ]
 
     def as_dict(self) -> dict:

@@ -17,7 +17,7 @@ namespace dtwk {
 // ---------------------------------------------------------------------------
 static thread_local char g_err[512] = "";
 
-static dtw_status fail(dtw_status st, const char *fmt, ...) {
+dtw_status fail(dtw_status st, const char *fmt, ...) {
     va_list ap;
     va_start(ap, fmt);
     vsnprintf(g_err, sizeof(g_err), fmt, ap);
@@ -109,7 +109,7 @@ static dtw_status check_dtw_p(int32_t n, int32_t w, int32_t p) {
 }
 
 // A threshold on DTW_p in the units the kernels compare (DTW_p^p; DTW_inf itself).
-static float threshold_power(float t, int32_t p) {
+float threshold_power(float t, int32_t p) {
     if (std::isinf(t)) return INFINITY;
     if (p == 2) return t * t;
     if (p == 4) return (t * t) * (t * t);
@@ -125,6 +125,25 @@ static dtw_status check_band(int32_t n, int32_t w) {
 
 static cudaError_t launch_dtw(const DtwJob &j, const DtwGeom &g, cudaStream_t s) {
     return launch_dtw_by_p(j, g, s);
+}
+
+dtw_status check_dtw_band_args(const float *x, const float *y, int64_t N, int32_t y_stride, int32_t n, int32_t w,
+                               int32_t p, float threshold, const float *out, bool *empty) {
+    *empty = false;
+    dtw_status st = check_dtw_p(n, w, p);
+    if (st != DTW_OK) return st;
+    if ((st = check_band(n, w)) != DTW_OK) return st;
+    if (N < 0 || N > INT32_MAX) return fail(DTW_ERR_INVALID_ARG, "N=%lld out of range", (long long)N);
+    if (y_stride != 0 && y_stride != n)
+        return fail(DTW_ERR_INVALID_ARG, "y_stride=%d must be 0 or n=%d", y_stride, n);
+    if (std::isnan(threshold) || threshold < 0.0f)
+        return fail(DTW_ERR_INVALID_ARG, "threshold must be >= 0 or +INF");
+    if (N == 0) {
+        *empty = true;
+        return DTW_OK;
+    }
+    if (!x || !y || !out) return fail(DTW_ERR_INVALID_ARG, "null pointer");
+    return DTW_OK;
 }
 
 }  // namespace dtwk
@@ -227,16 +246,9 @@ dtw_status lb_improved(const float *cand, int64_t N, const float *q, const float
 dtw_status dtw_band(const float *x, const float *y, int64_t N, int32_t y_stride, int32_t n, int32_t w,
                     int32_t p, float threshold, float *out, void *stream) {
     g_err[0] = 0;
-    dtw_status st = check_dtw_p(n, w, p);
-    if (st != DTW_OK) return st;
-    if ((st = check_band(n, w)) != DTW_OK) return st;
-    if (N < 0 || N > INT32_MAX) return fail(DTW_ERR_INVALID_ARG, "N=%lld out of range", (long long)N);
-    if (y_stride != 0 && y_stride != n)
-        return fail(DTW_ERR_INVALID_ARG, "y_stride=%d must be 0 or n=%d", y_stride, n);
-    if (std::isnan(threshold) || threshold < 0.0f)
-        return fail(DTW_ERR_INVALID_ARG, "threshold must be >= 0 or +INF");
-    if (N == 0) return DTW_OK;
-    if (!x || !y || !out) return fail(DTW_ERR_INVALID_ARG, "null pointer");
+    bool empty = false;
+    dtw_status st = check_dtw_band_args(x, y, N, y_stride, n, w, p, threshold, out, &empty);
+    if (st != DTW_OK || empty) return st;
     cudaStream_t s = (cudaStream_t)stream;
     const int we = w < n - 1 ? w : n - 1;
     const DtwGeom g = dtw_geom(n, we);

@@ -383,9 +383,11 @@ void cascade_stats(const CascadePlan &pl, int64_t Q, const unsigned long long *h
     st->pruned_improved += (int64_t)h[CNT_KEOGH_PASS] - (int64_t)h[CNT_LBI_PASS] + (int64_t)h[CNT_DTW_SKIP];
     st->dtw_computed += (int64_t)h[CNT_DTW_COMPUTED];
     st->dtw_abandoned += (int64_t)h[CNT_DTW_ABANDONED];
-    st->dtw_cells += (int64_t)h[CNT_DTW_ROWS] * (2 * pl.we + 1);
-    st->seed_cells += (int64_t)h[CNT_NUM + CNT_DTW_ROWS] * (2 * pl.we + 1);
+    st->dtw_cells += (int64_t)h[CNT_DTW_CELLS];
+    st->seed_cells += (int64_t)h[CNT_NUM + CNT_DTW_CELLS];
     st->dtw_lane_rows += (int64_t)h[CNT_DTW_LANE_ROWS];
+    st->dtw_rows += (int64_t)h[CNT_DTW_ROWS];
+    st->seed_rows += (int64_t)h[CNT_NUM + CNT_DTW_ROWS];
 }
 
 }  // namespace dtwk

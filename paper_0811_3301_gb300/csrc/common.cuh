@@ -261,10 +261,32 @@ enum {
     CNT_DTW_ROWS = 5,       // DP rows evaluated
     CNT_SUMMARY_PASS = 6,   // non-seed pairs with piecewise-sum bound <= thr
     CNT_DTW_LANE_ROWS = 7,  // thread-per-pair DTW: 32 x the longest pair's rows, per chunk of 32
-    CNT_NUM = 8
+    CNT_DTW_CELLS = 8,      // in-band cells of the DP rows evaluated (band_cells per pair)
+    CNT_NUM = 9
 };
 
+// In-band cells of rows 0..r-1 of the band DTW (|i - j| <= w, 0 <= j < n):
+// row i holds min(n - 1, i + w) - max(0, i - w) + 1 cells.  In closed form,
+// sum_{i<r} min(n, i + w + 1) - sum_{i<r} max(0, i - w); r = n gives
+// n (2w + 1) - w (w + 1) for w <= n - 1.
+__host__ __device__ inline long long tri_num(long long m) { return m > 0 ? m * (m + 1) / 2 : 0LL; }
+__host__ __device__ inline long long band_cells(long long r, long long n, long long w) {
+    if (r <= 0) return 0;
+    return r * (r - 1) / 2 + r * (w + 1) - tri_num(r - n + w) - tri_num(r - 1 - w);
+}
+
 int device_sm_count();
+
+// Host-side argument handling shared by entry points in several translation
+// units (api.cu).  fail() records the calling thread's dtw_last_error message
+// and returns st.
+dtw_status fail(dtw_status st, const char *fmt, ...);
+// The checks of dtw_band's arguments (n, w, p, the band width, N, y_stride,
+// the threshold, the pointers); DTW_OK with *empty = true when N == 0.
+dtw_status check_dtw_band_args(const float *x, const float *y, int64_t N, int32_t y_stride, int32_t n, int32_t w,
+                               int32_t p, float threshold, const float *out, bool *empty);
+// A threshold on DTW_p in the units the kernels compare (DTW_p^p; DTW_inf itself).
+float threshold_power(float t, int32_t p);
 
 cudaError_t launch_triangle_ratio(const float *dxy, const float *dyz, const float *dxz, int64_t N, float *out,
                                   cudaStream_t s);

@@ -103,7 +103,8 @@ k_dtw_reg(DtwJob j, int e, int wl) {
     const int n = j.n;
     const int ylen = j.qc.ylen, padl = j.qc.padl;
     if (j.npairs_dev) j.npairs = (int64_t)*j.npairs_dev;
-    unsigned long long n_skip = 0, n_comp = 0, n_aband = 0, n_rows = 0;
+    const int wb = min(j.w, n - 1);
+    unsigned long long n_skip = 0, n_comp = 0, n_aband = 0, n_rows = 0, n_cells = 0;
     for (;;) {
         unsigned long long chunk = 0;
         if (lane == 0) chunk = atomicAdd(j.cursor, 1ull);
@@ -170,6 +171,7 @@ k_dtw_reg(DtwJob j, int e, int wl) {
             }
         }
         n_rows += rows;
+        n_cells += (unsigned long long)band_cells(rows, n, wb);
         float d = kInf;
 #pragma unroll
         for (int k = 0; k < C; ++k) d = sel_eq(k, wl, D[k], d);
@@ -191,8 +193,11 @@ k_dtw_reg(DtwJob j, int e, int wl) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) n_rows += __shfl_xor_sync(0xffffffffu, n_rows, o);
         rows_w = n_rows;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) n_cells += __shfl_xor_sync(0xffffffffu, n_cells, o);
         if (lane == 0) {
             if (rows_w) atomicAdd(j.counters + CNT_DTW_ROWS, rows_w);
+            if (n_cells) atomicAdd(j.counters + CNT_DTW_CELLS, n_cells);
             if (n_skip) atomicAdd(j.counters + CNT_DTW_SKIP, n_skip);
             if (n_comp) atomicAdd(j.counters + CNT_DTW_COMPUTED, n_comp);
             if (n_aband) atomicAdd(j.counters + CNT_DTW_ABANDONED, n_aband);
@@ -266,7 +271,8 @@ k_dtw_reg4(DtwJob j, int e, int wl, bool xvec) {
     const int n = j.n;
     const int ylen = j.qc.ylen;
     if (j.npairs_dev) j.npairs = (int64_t)*j.npairs_dev;
-    unsigned long long n_skip = 0, n_comp = 0, n_aband = 0, n_rows = 0, n_lane_rows = 0;
+    const int wb = min(j.w, n - 1);
+    unsigned long long n_skip = 0, n_comp = 0, n_aband = 0, n_rows = 0, n_lane_rows = 0, n_cells = 0;
     for (;;) {
         unsigned long long chunk = 0;
         if (lane == 0) chunk = atomicAdd(j.cursor, 1ull);
@@ -377,6 +383,7 @@ k_dtw_reg4(DtwJob j, int e, int wl, bool xvec) {
                 }
             }
             n_rows += rows;
+            n_cells += (unsigned long long)band_cells(rows, n, wb);
             my_rows = rows;
             float d = kInf;
 #pragma unroll
@@ -398,8 +405,11 @@ k_dtw_reg4(DtwJob j, int e, int wl, bool xvec) {
         n_aband = __reduce_add_sync(0xffffffffu, (unsigned)n_aband);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) n_rows += __shfl_xor_sync(0xffffffffu, n_rows, o);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) n_cells += __shfl_xor_sync(0xffffffffu, n_cells, o);
         if (lane == 0) {
             if (n_rows) atomicAdd(j.counters + CNT_DTW_ROWS, n_rows);
+            if (n_cells) atomicAdd(j.counters + CNT_DTW_CELLS, n_cells);
             if (n_skip) atomicAdd(j.counters + CNT_DTW_SKIP, n_skip);
             if (n_comp) atomicAdd(j.counters + CNT_DTW_COMPUTED, n_comp);
             if (n_aband) atomicAdd(j.counters + CNT_DTW_ABANDONED, n_aband);
@@ -433,7 +443,7 @@ k_dtw_wide(DtwJob j) {
     const int lane_dead = (top + 1) / CL, c_dead = (top + 1) % CL;  // slot 2w+1
     const int lane_diag = w / CL, c_diag = w % CL;                  // slot of column i
     if (j.npairs_dev) j.npairs = (int64_t)*j.npairs_dev;
-    unsigned long long n_skip = 0, n_comp = 0, n_aband = 0, n_rows = 0;
+    unsigned long long n_skip = 0, n_comp = 0, n_aband = 0, n_rows = 0, n_cells = 0;
     for (;;) {
         unsigned long long pw = 0;
         if (lane == 0) pw = atomicAdd(j.cursor, 1ull);
@@ -513,12 +523,17 @@ k_dtw_wide(DtwJob j) {
                 thr = __shfl_sync(0xffffffffu, thr, 0);
                 if (rowmin > thr) {  // uniform: every lane sees lane_top's value
                     abandoned = true;
-                    n_rows += (unsigned long long)max(0, min(n, (t - lane_top) / 2 + 1));
+                    const int rows = max(0, min(n, (t - lane_top) / 2 + 1));
+                    n_rows += (unsigned long long)rows;
+                    n_cells += (unsigned long long)band_cells(rows, n, w);
                     break;
                 }
             }
         }
-        if (!abandoned) n_rows += (unsigned long long)n;
+        if (!abandoned) {
+            n_rows += (unsigned long long)n;
+            n_cells += (unsigned long long)band_cells(n, n, w);
+        }
         float dv = kInf;
 #pragma unroll
         for (int u = 0; u < CL; ++u) dv = sel_eq(u, c_diag, D[u], dv);
@@ -533,6 +548,7 @@ k_dtw_wide(DtwJob j) {
     }
     if (j.counters && lane == 0) {
         if (n_rows) atomicAdd(j.counters + CNT_DTW_ROWS, n_rows);
+        if (n_cells) atomicAdd(j.counters + CNT_DTW_CELLS, n_cells);
         if (n_skip) atomicAdd(j.counters + CNT_DTW_SKIP, n_skip);
         if (n_comp) atomicAdd(j.counters + CNT_DTW_COMPUTED, n_comp);
         if (n_aband) atomicAdd(j.counters + CNT_DTW_ABANDONED, n_aband);

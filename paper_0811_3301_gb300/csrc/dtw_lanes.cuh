@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(kDtwThreads, (CL <= 13 ? 4 : (CL <= 20 ? 3 : 1
     const int64_t qstride = (int64_t)4 * j.qc.ylen;
     constexpr int kIdle = 1 << 30;
     if (j.npairs_dev) j.npairs = (int64_t)*j.npairs_dev;
-    unsigned long long n_skip = 0, n_comp = 0, n_aband = 0, n_rows = 0;
+    unsigned long long n_skip = 0, n_comp = 0, n_aband = 0, n_rows = 0, n_cells = 0;
 
     float DX[CL], DY[CL], yX[CL], yY[CL];
     float nxt[4] = {0.0f, 0.0f, 0.0f, 0.0f};  // next-row x and window values of sets X and Y
@@ -282,11 +282,13 @@ __global__ void __launch_bounds__(kDtwThreads, (CL <= 13 ? 4 : (CL <= 20 ? 3 : 1
                 if (gl == 0) {
                     if (ab) {
                         ++n_aband;
-                        const int rows = (t - T0[ps] - lane_top) / 2;
-                        n_rows += (unsigned long long)max(0, min(n, rows));
+                        const int rows = max(0, min(n, (t - T0[ps] - lane_top) / 2));
+                        n_rows += (unsigned long long)rows;
+                        n_cells += (unsigned long long)band_cells(rows, n, w);
                         val = kInf;
                     } else {
                         n_rows += (unsigned long long)n;
+                        n_cells += (unsigned long long)band_cells(n, n, w);
                     }
                     if (!j.bsf && val > j.fixed_thr) val = kInf;
                     j.res[spi[ps]] = j.root_out ? root_p(val, P) : val;
@@ -305,6 +307,7 @@ __global__ void __launch_bounds__(kDtwThreads, (CL <= 13 ? 4 : (CL <= 20 ? 3 : 1
         if (lane == 0 && n_skip) atomicAdd(j.counters + CNT_DTW_SKIP, n_skip);
         if (gl == 0) {
             if (n_rows) atomicAdd(j.counters + CNT_DTW_ROWS, n_rows);
+            if (n_cells) atomicAdd(j.counters + CNT_DTW_CELLS, n_cells);
             if (n_comp) atomicAdd(j.counters + CNT_DTW_COMPUTED, n_comp);
             if (n_aband) atomicAdd(j.counters + CNT_DTW_ABANDONED, n_aband);
         }
