@@ -207,7 +207,8 @@ enum {
     DTW_STAGE_DTW = 6,
     DTW_STAGE_FINALIZE = 7,
     DTW_STAGE_DB_PREP = 8, /* per-call database terms: part sums, row envelopes */
-    DTW_NUM_STAGES = 9
+    DTW_STAGE_GROUP = 9,   /* survivors of the bounds grouped by query and ordered by bound */
+    DTW_NUM_STAGES = 10
 };
 typedef struct {
     double ms[DTW_NUM_STAGES];

@@ -56,9 +56,9 @@ class Stats(ctypes.Structure):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
 
 
-NUM_STAGES = 9
+NUM_STAGES = 10
 STAGE_NAMES = ["envelope", "lb_keogh", "seed_select", "seed_dtw", "seed_kth", "lb_improved", "dtw", "finalize",
-               "db_prep"]
+               "db_prep", "group"]
 
 
 class Profile(ctypes.Structure):

@@ -49,9 +49,9 @@ cudaError_t profile_collect(double *ms, int64_t *launches, bool reset) {
     return cudaSuccess;
 }
 
-static const char *const kStageNames[DTW_NUM_STAGES] = {"envelope",    "lb_keogh", "seed_select",
-                                                         "seed_dtw",    "seed_kth", "lb_improved",
-                                                         "dtw",         "finalize", "db_prep"};
+static const char *const kStageNames[DTW_NUM_STAGES] = {"envelope", "lb_keogh",    "seed_select", "seed_dtw",
+                                                         "seed_kth", "lb_improved", "dtw",         "finalize",
+                                                         "db_prep",  "group"};
 
 // Marks a stage with an NVTX range (host side, for timeline tools; no cost
 // without one attached) and, when profiling is on and the stream is not being
@@ -331,6 +331,9 @@ cudaError_t cascade_run(const CascadePlan &pl, const CascadeWs &l, const float *
             StageTimer tm(DTW_STAGE_LB_IMPROVED, s);
             RUN_TRY(cudaMemsetAsync(l.qcount, 0, (size_t)qn * sizeof(int32_t), s));
             RUN_TRY(launch_lbi_filter(b, s));
+        }
+        {
+            StageTimer tm(DTW_STAGE_GROUP, s);
             RUN_TRY(launch_group_by_query(b, s));
         }
         DtwJob jp = js;

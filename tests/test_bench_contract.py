@@ -35,9 +35,19 @@ def test_latency_summary():
     # last one 12 ms), admitted 0.5 ms after arrival
     comp = [{"arrival_ns": i * 1_000_000, "admit_ns": i * 1_000_000 + 500_000,
              "done_ns": i * 1_000_000 + (12_000_000 if i == 999 else 2_000_000), "status": 0} for i in range(1000)]
-    comp[3]["status"] = 4
     s = bench.latency_summary(comp)
-    assert s["completed"] == 1000 and s["failed"] == 1
+    assert s["completed"] == 1000 and s["failed"] == 0 and s["all_ok"]
     assert s["p50_ms"] == 2.0 and s["p99_ms"] == 2.0 and 2.0 < s["p999_ms"] < 12.0
     assert s["queue_p50_ms"] == 0.5
     assert abs(s["throughput_qps"] - 1000 / 1.011) < 1e-6
+    # a timed-out request (status 4) and a failed one (status 2) enter neither
+    # the throughput nor the latencies; the last request (12 ms) times out
+    comp[3]["status"] = 2
+    comp[999]["status"] = 4
+    s = bench.latency_summary(comp)
+    assert s["completed"] == 1000 and s["succeeded"] == 998 and s["failed"] == 2 and s["timed_out"] == 1
+    assert not s["all_ok"]
+    assert s["p999_ms"] == 2.0
+    assert abs(s["throughput_qps"] - 998 / 1.000) < 1e-6
+    none = bench.latency_summary([dict(comp[0], status=4)])
+    assert none["succeeded"] == 0 and none["throughput_qps"] == 0.0 and none["p50_ms"] is None
