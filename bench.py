@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--parts", type=int, default=0, help="piecewise-sum parts (0: default n/8, -1: off)")
     ap.add_argument("--dtw-path", type=int, default=0, help="DTW kernel: 0 auto, 1 thread per pair, 2 warp per pair, "
                     "3 main stage on two 16-lane groups per warp")
+    ap.add_argument("--filter-path", type=int, default=0,
+                    help="LB_Keogh/LB_Improved filter kernel: 0 auto, 1 one warp per pair, 2 batches of eight pairs")
     ap.add_argument("--no-p2", action="store_true", help="skip the DTW_2 side measurement")
     ap.add_argument("--no-extra", action="store_true",
                     help="default workload only: skip the bounded batched and serving runs added to its line")
@@ -376,7 +378,7 @@ def run_ours(a):
             dist.barrier()
             torch.cuda.synchronize()
 
-    kw = {"seeds": a.seeds, "parts": a.parts, "dtw_path": a.dtw_path}
+    kw = {"seeds": a.seeds, "parts": a.parts, "dtw_path": a.dtw_path, "filter_path": a.filter_path}
 
     def step(p):
         return api.knn_search(db, qs, a.w, p, a.k, **kw)

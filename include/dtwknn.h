@@ -92,6 +92,10 @@ typedef struct {
                          pair for long series or wide bands, else one thread per pair),
                          1 one thread per pair where the band fits, 2 one warp per pair,
                          3 one warp per two pairs (16-lane groups) where the band allows */
+    int32_t filter_path; /* LB_Keogh / LB_Improved filter kernel: 0 chooses (batches of eight
+                            pairs per warp for series of 128 or 256 elements with the
+                            piecewise-sum pre-filter, else one warp per pair), 1 one warp
+                            per pair, 2 batches where they apply */
 } dtw_options;
 
 /*

@@ -357,7 +357,7 @@ dtw_status knn_search_ex(const float *db, int64_t N, const float *queries, int64
     if (N < 0 || N > INT32_MAX / 2) return fail(DTW_ERR_INVALID_ARG, "N=%lld out of range", (long long)N);
     if (Q < 0 || Q > INT32_MAX / 2) return fail(DTW_ERR_INVALID_ARG, "Q=%lld out of range", (long long)Q);
     if (k < 1 || k > DTW_MAX_K) return fail(DTW_ERR_INVALID_ARG, "k=%d outside [1, %d]", k, DTW_MAX_K);
-    dtw_options o{DTW_MODE_IMPROVED, 1e-6f, 0, 0, 0};
+    dtw_options o{DTW_MODE_IMPROVED, 1e-6f, 0, 0, 0, 0};
     if (opt) o = *opt;
     if (o.parts < -1 || o.parts > n) return fail(DTW_ERR_INVALID_ARG, "parts=%d outside [-1, n=%d]", o.parts, n);
     if (o.mode < DTW_MODE_IMPROVED || o.mode > DTW_MODE_NOPRUNE)
@@ -365,6 +365,8 @@ dtw_status knn_search_ex(const float *db, int64_t N, const float *queries, int64
     if (!(o.slack >= 0.0f) || std::isinf(o.slack)) return fail(DTW_ERR_INVALID_ARG, "slack must be finite and >= 0");
     if (o.seeds < 0) return fail(DTW_ERR_INVALID_ARG, "seeds=%d must be >= 0", o.seeds);
     if (o.dtw_path < 0 || o.dtw_path > 3) return fail(DTW_ERR_INVALID_ARG, "dtw_path=%d outside [0, 3]", o.dtw_path);
+    if (o.filter_path < 0 || o.filter_path > 2)
+        return fail(DTW_ERR_INVALID_ARG, "filter_path=%d outside [0, 2]", o.filter_path);
     if (stats) memset(stats, 0, sizeof(*stats));
     if (Q == 0) return DTW_OK;
     if (!queries || !out_idx || !out_dist || (N > 0 && !db)) return fail(DTW_ERR_INVALID_ARG, "null pointer");
@@ -388,7 +390,7 @@ dtw_status knn_search_ex(const float *db, int64_t N, const float *queries, int64
         x.PX = pl.summary ? cv.take<float>((size_t)N * pl.parts) : nullptr;
         x.XU = plan_needs_db_envelope(pl) ? cv.take<float>((size_t)N * n) : nullptr;
         x.XL = plan_needs_db_envelope(pl) ? cv.take<float>((size_t)N * n) : nullptr;
-        x.counters = cv.take<unsigned long long>(2 * CNT_NUM);
+        x.counters = cv.take<unsigned long long>(CNT_ALLOC);
         x.xmax = cv.take<unsigned long long>(1);
         x.out_idx = oi_dev ? nullptr : cv.take<int64_t>((size_t)Q * k);
         x.out_dist = od_dev ? nullptr : cv.take<float>((size_t)Q * k);
@@ -410,7 +412,7 @@ dtw_status knn_search_ex(const float *db, int64_t N, const float *queries, int64
     }
     int64_t *oidx = oi_dev ? out_idx : x.out_idx;
     float *odist = od_dev ? out_dist : x.out_dist;
-    CUDA_TRY(cudaMemsetAsync(x.counters, 0, 2 * CNT_NUM * sizeof(unsigned long long), s));
+    CUDA_TRY(cudaMemsetAsync(x.counters, 0, CNT_ALLOC * sizeof(unsigned long long), s));
     unsigned *xmax_bits = reinterpret_cast<unsigned *>(x.xmax);
     // part sums and row envelopes of the database, once per call
     CUDA_TRY(prepare_database(pl, dbd, x.PX, xmax_bits, x.XU, x.XL, s));
@@ -432,9 +434,14 @@ dtw_status knn_search_ex(const float *db, int64_t N, const float *queries, int64
     if (!od_dev)
         CUDA_TRY(cudaMemcpyAsync(out_dist, x.out_dist, (size_t)Q * k * sizeof(float), cudaMemcpyDeviceToHost, s));
     if (stats || !oi_dev || !od_dev) {
-        unsigned long long h[2 * CNT_NUM];
-        if (stats) CUDA_TRY(cudaMemcpyAsync(h, x.counters, sizeof(h), cudaMemcpyDeviceToHost, s));
+        // a synchronising call also reports a bounded device-side wait that
+        // gave up (the outputs are then not valid)
+        unsigned long long h[CNT_ALLOC];
+        CUDA_TRY(cudaMemcpyAsync(h, x.counters, sizeof(h), cudaMemcpyDeviceToHost, s));
         CUDA_TRY(cudaStreamSynchronize(s));
+        if (h[CNT_ERR] != 0)
+            return fail((dtw_status)h[CNT_ERR], "a device-side wait of the cascade gave up (status %llu)",
+                        (unsigned long long)h[CNT_ERR]);
         if (stats) cascade_stats(pl, Q, h, stats);
     }
     return DTW_OK;

@@ -156,12 +156,20 @@ CascadePlan make_plan(int64_t N, int64_t Qmax, int n, int w, int p, int k, const
     // sooner.  The order changes which non-neighbours are computed, never
     // the result.
     pl.order_first = pl.mode == DTW_MODE_NOPRUNE ? 0 : 32 * ((k + 15) / 16);
+    // filter kernel: pairs in batches of eight per warp where that kernel
+    // applies (the default), else one warp per pair
+    const bool batch_ok = N > 0 && lbi_batch_applies(n, pl.summary, pl.mode == DTW_MODE_IMPROVED);
+    pl.filter_path = (batch_ok && o.filter_path != 1) ? 2 : 1;
     pl.filter_warps = lbi_filter_warps(n, pl.we, std::max(pl.S, 1), pl.seg_len, p, filter_warps);
     const int64_t nsegs = N > 0 ? (N + pl.seg_len - 1) / pl.seg_len : 1;
     pl.nseg = (int)nsegs * pl.filter_warps;
-    // filter CTAs: about eight waves of four CTAs per SM; each takes enough
-    // consecutive segments of its query to amortise the query staging
-    const int64_t target = (int64_t)device_sm_count() * 32;
+    // filter CTAs: about sixteen waves of four CTAs per SM; each takes a few
+    // consecutive segments of its query to amortise the query staging, and
+    // the CTAs of all queries that scan one group of segments run close
+    // together, so the group's rows stay in L2 (two segments of 4,096
+    // candidates: about 1.1x the algorithmic DRAM bytes, against 1.8x with
+    // five)
+    const int64_t target = (int64_t)device_sm_count() * 64;
     int64_t spc = (Qc * nsegs) / target;
     pl.seg_per_cta = (int)std::max<int64_t>(1, std::min<int64_t>(spc, nsegs));
     return pl;
@@ -273,6 +281,8 @@ cudaError_t cascade_run(const CascadePlan &pl, const CascadeWs &l, const float *
     b.seg_len = pl.seg_len;
     b.seg_per_cta = pl.seg_per_cta;
     b.filter_warps = pl.filter_warps;
+    b.filter_path = pl.filter_path;
+    b.dev_err = reinterpret_cast<unsigned *>(counters + CNT_ERR);
     b.nseg = N > 0 ? pl.nseg : 0;
     b.seg_start = l.seg_start;
     b.seg_count = l.seg_count;

@@ -39,6 +39,7 @@ struct CascadePlan {
     int nseg;        // sub-segments per query
     int seg_per_cta; // filter segments per CTA
     int dtw_path;    // 0 auto, 1 thread per pair, 2 warp per pair (main DTW stage)
+    int filter_path; // 1 one warp per pair, 2 batches of eight pairs per warp
     int order_first; // pairs per query the DTW stage takes first, by ascending bound (0: filter order)
 };
 
@@ -63,8 +64,8 @@ size_t cascade_ws_bytes(const CascadePlan &pl);
 // One run over qn <= pl.Qc queries q [qn][n] (device).  PX [N][parts] and
 // xmax_bits are the database part sums and max |x| (launch_summarize), used
 // when pl.summary; XU, XL [N][n] the database rows' envelopes for band pl.we
-// (launch_envelope), used when pl.mode is DTW_MODE_IMPROVED.  counters: 2 * CNT_NUM device counters (run counters, then
-// seed-stage counters), accumulated, zeroed by the caller.  Outputs
+// (launch_envelope), used when pl.mode is DTW_MODE_IMPROVED.  counters: CNT_ALLOC device words (run counters, seed-stage
+// counters, the error word CNT_ERR), accumulated, zeroed by the caller.  Outputs
 // out_idx/out_dist [qn][k] (device).  Asynchronous on s; allocates nothing.
 cudaError_t cascade_run(const CascadePlan &pl, const CascadeWs &ws, const float *db, const float *PX,
                         const unsigned *xmax_bits, const float *XU, const float *XL, const float *q, int qn,
@@ -81,7 +82,7 @@ cudaError_t prepare_database(const CascadePlan &pl, const float *db, float *PX, 
                              float *XL, cudaStream_t s);
 
 // Adds the statistics of Q queries run under pl, from the host copy of the
-// 2 * CNT_NUM counters, to st.
+// CNT_ALLOC counter words, to st.
 void cascade_stats(const CascadePlan &pl, int64_t Q, const unsigned long long *h, dtw_stats *st);
 
 // Stage timing (dtw_profile_enable / dtw_profile_read).  Stages launched while

@@ -200,6 +200,8 @@ struct CascadeBufs {
     int seg_len, nseg;    // nseg: sub-segments per query (segments x filter warps)
     int seg_per_cta;      // consecutive segments one filter CTA handles
     int filter_warps;     // warps per filter CTA (one sub-segment each)
+    int filter_path;      // 1 one warp per pair, 2 batches of eight pairs per warp (resolved by the plan)
+    unsigned *dev_err;    // a kernel's bounded wait that gave up records its dtw_status here (0: none)
     int32_t *seg_start;   // [Q][nseg]
     int32_t *seg_count;   // [Q][nseg]
     // work cursors and counters
@@ -217,6 +219,9 @@ cudaError_t launch_lbi_filter(const CascadeBufs &b, cudaStream_t s);
 // warps per filter CTA (one sub-segment each): `want` (1..8) if its shared
 // memory fits a CTA, else fewer; want = 0 chooses from the occupancy
 int lbi_filter_warps(int n, int w, int S, int seg_len, int p, int want = 0);
+// The batched filter (filter_path 2) serves series of 128 or 256 elements
+// with the piecewise-sum pre-filter and LB_Improved on.
+bool lbi_batch_applies(int n, bool summary, bool lbi_inline);
 cudaError_t launch_finalize(const CascadeBufs &b, cudaStream_t s);
 cudaError_t launch_group_by_query(const CascadeBufs &b, cudaStream_t s);
 
@@ -264,6 +269,11 @@ enum {
     CNT_DTW_CELLS = 8,      // in-band cells of the DP rows evaluated (band_cells per pair)
     CNT_NUM = 9
 };
+// A run's counter block: CNT_NUM run counters, CNT_NUM seed-stage counters,
+// then one word where a kernel whose bounded wait gave up records its
+// dtw_status (0: none).
+constexpr int CNT_ERR = 2 * CNT_NUM;
+constexpr int CNT_ALLOC = 2 * CNT_NUM + 1;
 
 // In-band cells of rows 0..r-1 of the band DTW (|i - j| <= w, 0 <= j < n):
 // row i holds min(n - 1, i + w) - max(0, i - w) + 1 cells.  In closed form,

@@ -263,7 +263,7 @@ BatchLayout layout_batch(Carve &cv, int64_t Q, int64_t total, int64_t gout, int 
     L.gdist = cv.take<float>((size_t)std::max<int64_t>(gout, 1));
     L.oidx = cv.take<int64_t>((size_t)std::max<int64_t>(Q * k_stride, 1));
     L.odist = cv.take<float>((size_t)std::max<int64_t>(Q * k_stride, 1));
-    L.counters = cv.take<unsigned long long>(std::max<size_t>(groups.size(), 1) * 2 * CNT_NUM);
+    L.counters = cv.take<unsigned long long>(std::max<size_t>(groups.size(), 1) * CNT_ALLOC);
     L.ws.resize(groups.size());
     if (shared_ws) {
         const size_t off0 = cv.off;
@@ -402,7 +402,7 @@ static cudaError_t enqueue_batch(dtw_index *ix, Slot &sl, const Batch &bt, const
     const bool per_query = (bt.flags & DTW_BATCH_PER_QUERY) != 0;
     const bool serial = per_query || (bt.flags & DTW_BATCH_SERIAL) != 0;
     cudaError_t e;
-    if ((e = cudaMemsetAsync(L.counters, 0, std::max<size_t>(G, 1) * 2 * CNT_NUM * sizeof(unsigned long long), s)) !=
+    if ((e = cudaMemsetAsync(L.counters, 0, std::max<size_t>(G, 1) * CNT_ALLOC * sizeof(unsigned long long), s)) !=
         cudaSuccess)
         return e;
     if ((e = launch_gather(L.staged, L.map, bt.Q, L.grouped, s)) != cudaSuccess) return e;
@@ -417,7 +417,7 @@ static cudaError_t enqueue_batch(dtw_index *ix, Slot &sl, const Batch &bt, const
         const GroupRun &gr = bt.groups[g];
         const Bucket &bk = ix->buckets[gr.bucket];
         cudaStream_t gs = serial ? s : sl.pool[gr.stream];
-        unsigned long long *cnt = L.counters + g * 2 * CNT_NUM;
+        unsigned long long *cnt = L.counters + g * CNT_ALLOC;
         const int64_t step = per_query ? 1 : gr.pl.Qc;
         for (int64_t q0 = 0; q0 < gr.qn; q0 += step) {
             const int qn = (int)std::min<int64_t>(step, gr.qn - q0);
@@ -517,7 +517,7 @@ dtw_status run_batch(dtw_index *ix, Slot &sl, Batch &bt, const float *queries, b
         IX_TRY(cudaMemcpyAsync(out_dist, L.odist, (size_t)bt.Q * bt.k_stride * sizeof(float), kind, s));
     }
     if (counters_host)
-        IX_TRY(cudaMemcpyAsync(counters_host, L.counters, bt.groups.size() * 2 * CNT_NUM * sizeof(unsigned long long),
+        IX_TRY(cudaMemcpyAsync(counters_host, L.counters, bt.groups.size() * CNT_ALLOC * sizeof(unsigned long long),
                                cudaMemcpyDeviceToHost, s));
     IX_TRY(cudaEventRecord(sl.done, s));
     return DTW_OK;
@@ -569,7 +569,7 @@ dtw_status tune_group(dtw_index *ix, int b, int w, int k, const float *qdev, int
     Carve cv0;
     cv0.take<int64_t>((size_t)qn * k);
     cv0.take<float>((size_t)qn * k);
-    cv0.take<unsigned long long>(2 * CNT_NUM);
+    cv0.take<unsigned long long>(CNT_ALLOC);
     const size_t head = cv0.off;
     char *buf = nullptr;
     cudaError_t e = cudaMalloc(&buf, head + ws_max);
@@ -581,7 +581,7 @@ dtw_status tune_group(dtw_index *ix, int b, int w, int k, const float *qdev, int
     cv.base = buf;
     int64_t *oidx = cv.take<int64_t>((size_t)qn * k);
     float *odist = cv.take<float>((size_t)qn * k);
-    unsigned long long *cnt = cv.take<unsigned long long>(2 * CNT_NUM);
+    unsigned long long *cnt = cv.take<unsigned long long>(CNT_ALLOC);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -704,7 +704,7 @@ bool ptr_on_device(const void *p) {
 void batch_stats(const Batch &bt, const unsigned long long *h, dtw_stats *st) {
     memset(st, 0, sizeof(*st));
     for (size_t g = 0; g < bt.groups.size(); ++g)
-        cascade_stats(bt.groups[g].pl, bt.groups[g].qn, h + g * 2 * CNT_NUM, st);
+        cascade_stats(bt.groups[g].pl, bt.groups[g].qn, h + g * CNT_ALLOC, st);
 }
 
 }  // namespace dtwk
@@ -731,7 +731,7 @@ dtw_status dtw_index_create(int32_t p, const dtw_options *opt, dtw_index **out) 
     if (!out) return ix_fail(DTW_ERR_INVALID_ARG, "null pointer");
     *out = nullptr;
     if (p != 1 && p != 2) return ix_fail(DTW_ERR_INVALID_ARG, "p=%d must be 1 or 2", p);
-    dtw_options o{DTW_MODE_IMPROVED, 1e-6f, 0, 0, 0};
+    dtw_options o{DTW_MODE_IMPROVED, 1e-6f, 0, 0, 0, 0};
     if (opt) o = *opt;
     if (o.mode < DTW_MODE_IMPROVED || o.mode > DTW_MODE_NOPRUNE)
         return ix_fail(DTW_ERR_INVALID_ARG, "mode=%d unknown", o.mode);
@@ -739,6 +739,8 @@ dtw_status dtw_index_create(int32_t p, const dtw_options *opt, dtw_index **out) 
     if (o.seeds < 0) return ix_fail(DTW_ERR_INVALID_ARG, "seeds=%d must be >= 0", o.seeds);
     if (o.parts < -1) return ix_fail(DTW_ERR_INVALID_ARG, "parts=%d must be >= -1", o.parts);
     if (o.dtw_path < 0 || o.dtw_path > 3) return ix_fail(DTW_ERR_INVALID_ARG, "dtw_path=%d outside [0, 3]", o.dtw_path);
+    if (o.filter_path < 0 || o.filter_path > 2)
+        return ix_fail(DTW_ERR_INVALID_ARG, "filter_path=%d outside [0, 2]", o.filter_path);
     auto *ix = new dtw_index();
     ix->p = p;
     ix->opt = o;
@@ -888,7 +890,7 @@ dtw_status dtw_index_search(dtw_index *ix, const float *queries, int64_t Q, cons
         bt = std::move(again);
     }
     std::vector<unsigned long long> h;
-    if (stats) h.assign(bt.groups.size() * 2 * CNT_NUM, 0);
+    if (stats) h.assign(bt.groups.size() * CNT_ALLOC, 0);
     if ((st = run_batch(ix, ix->slot, bt, queries, q_dev, out_idx, out_dist, oi_dev, s, stats ? h.data() : nullptr)) !=
         DTW_OK)
         return st;

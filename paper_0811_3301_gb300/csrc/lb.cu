@@ -608,6 +608,80 @@ __device__ __forceinline__ float warp_lbi_env(const CascadeBufs &b, int q, int c
     return warp_sum(acc + (lane == 0 ? first : 0.0f));
 }
 
+// Phase 1 of a filter segment [c0, c1) for the calling warp: the stored
+// bounds of its share of the segment (candidates c0 + wid * 32 + lane, then
+// in strides of the CTA's warps) are tested against thr_m, and the
+// candidates that pass are compacted, in order, into the warp's buffers
+// (seeds hold NaN in the matrix and never pass).  Eight loads per lane are
+// issued before any is tested, so that the scan waits on memory once per
+// eight rows of 32.  The matrix is read once: its loads are marked
+// evict-first, so that the segment's rows, which every query's CTA reads,
+// stay in L2.  Returns the number of candidates kept.
+__device__ __forceinline__ int scan_segment(const float *__restrict__ lbrow, int c0, int c1, int wid, int stride,
+                                            float thr_m, int32_t *surv_c, float *surv_v) {
+    const int lane = threadIdx.x & 31;
+    int cnt1 = 0;
+    for (int base0 = c0 + wid * 32; base0 < c1; base0 += 8 * stride) {
+        float v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int c = base0 + u * stride + lane;
+            v[u] = c < c1 ? __ldcs(lbrow + c) : kInf;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int c = base0 + u * stride + lane;
+            const bool pass = c < c1 && v[u] <= thr_m;
+            const unsigned m = __ballot_sync(0xffffffffu, pass);
+            if (pass) {
+                const int slot = cnt1 + __popc(m & ((1u << lane) - 1));
+                surv_c[slot] = c;
+                surv_v[slot] = v[u];
+            }
+            cnt1 += __popc(m);
+        }
+    }
+    __syncwarp();
+    return cnt1;
+}
+
+// Writes the warp's cnt survivors of segment sg (candidates surv_c, bounds
+// surv_v) as one contiguous block of the pair list and records its start and
+// length as sub-segment (q, sg, wid); adds the stage counters (cnt1
+// candidates passed the stored bound, kp of them LB_Keogh when the matrix
+// held the piecewise-sum bound).
+__device__ __forceinline__ void emit_survivors(const CascadeBufs &b, int q, int sg, int nsegs, int nw, int wid, int cnt,
+                                               int cnt1, unsigned long long kp, const int32_t *surv_c,
+                                               const float *surv_v) {
+    const int lane = threadIdx.x & 31;
+    const unsigned long long pk = (unsigned long long)cnt1;
+    unsigned long long base = 0;
+    if (lane == 0 && cnt > 0) base = atomicAdd(b.pair_count, (unsigned long long)cnt);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    const int64_t sub = ((int64_t)q * nsegs + sg) * nw + wid;
+    if (lane == 0) {
+        b.seg_start[sub] = (int32_t)base;
+        b.seg_count[sub] = cnt;
+        if (cnt) atomicAdd(b.qcount + q, cnt);
+        if (b.counters) {
+            if (b.summary) {
+                if (pk) atomicAdd(b.counters + CNT_SUMMARY_PASS, pk);
+                if (kp) atomicAdd(b.counters + CNT_KEOGH_PASS, kp);
+            } else if (pk) {
+                atomicAdd(b.counters + CNT_KEOGH_PASS, pk);
+            }
+            if (cnt && b.mode != DTW_MODE_IMPROVED) atomicAdd(b.counters + CNT_LBI_PASS, (unsigned long long)cnt);
+            if (cnt && b.lbi_inline) atomicAdd(b.counters + CNT_LBI_PASS, (unsigned long long)cnt);
+        }
+    }
+    __syncwarp();
+    for (int t = lane; t < cnt; t += 32) {
+        const unsigned long long o = base + t;
+        b.pairs_u[o] = Pair{q, surv_c[t]};
+        b.lbi_u[o] = surv_v[t];
+    }
+}
+
 template <int P, int MT, bool FAST>
 __global__ void __launch_bounds__(256, 2) k_lbi_filter(CascadeBufs b, bool vec_arg) {
     // FAST (see env_issue): 16-byte rows of exactly 32 MT elements, the
@@ -646,35 +720,7 @@ __global__ void __launch_bounds__(256, 2) k_lbi_filter(CascadeBufs b, bool vec_a
     if (sg >= nsegs) break;
     const int c0 = sg * b.seg_len;
     const int c1 = min(b.N, c0 + b.seg_len);
-    // phase 1: matrix test over this warp's share of the segment; the
-    // survivors are compacted into the warp's buffer (seeds hold NaN in the
-    // matrix and never pass).  Eight loads per lane are issued before any is
-    // tested, so that the scan waits on memory once per eight rows of 32.
-    // The matrix is read once: its loads are marked evict-first, so that
-    // the segment's rows, which every query's CTA reads, stay in L2.
-    int cnt1 = 0;
-    for (int base0 = c0 + wid * 32; base0 < c1; base0 += 8 * stride) {
-        float v[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int c = base0 + u * stride + lane;
-            v[u] = c < c1 ? __ldcs(lbrow + c) : kInf;
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int c = base0 + u * stride + lane;
-            const bool pass = c < c1 && v[u] <= thr_m;
-            const unsigned m = __ballot_sync(0xffffffffu, pass);
-            if (pass) {
-                const int slot = cnt1 + __popc(m & ((1u << lane) - 1));
-                surv_c[slot] = c;
-                surv_v[slot] = v[u];
-            }
-            cnt1 += __popc(m);
-        }
-    }
-    __syncwarp();
-    const unsigned long long pk = (unsigned long long)cnt1;
+    const int cnt1 = scan_segment(lbrow, c0, c1, wid, stride, thr_m, surv_c, surv_v);
     unsigned long long kp = 0;  // LB_Keogh survivors (summary mode)
     // phase 2: LB_Keogh (when the matrix held the pre-filter bound) and
     // LB_Improved of each survivor, warp per pair, the rows of the next
@@ -721,33 +767,204 @@ __global__ void __launch_bounds__(256, 2) k_lbi_filter(CascadeBufs b, bool vec_a
     } else {
         cnt = cnt1;
     }
-    unsigned long long base = 0;
-    if (lane == 0 && cnt > 0) base = atomicAdd(b.pair_count, (unsigned long long)cnt);
-    base = __shfl_sync(0xffffffffu, base, 0);
-    const int64_t sub = ((int64_t)q * nsegs + sg) * nw + wid;
-    if (lane == 0) {
-        b.seg_start[sub] = (int32_t)base;
-        b.seg_count[sub] = cnt;
-        if (cnt) atomicAdd(b.qcount + q, cnt);
-        if (b.counters) {
-            if (b.summary) {
-                if (pk) atomicAdd(b.counters + CNT_SUMMARY_PASS, pk);
-                if (kp) atomicAdd(b.counters + CNT_KEOGH_PASS, kp);
-            } else if (pk) {
-                atomicAdd(b.counters + CNT_KEOGH_PASS, pk);
-            }
-            if (cnt && b.mode != DTW_MODE_IMPROVED) atomicAdd(b.counters + CNT_LBI_PASS, (unsigned long long)cnt);
-            if (cnt && b.lbi_inline) atomicAdd(b.counters + CNT_LBI_PASS, (unsigned long long)cnt);
-        }
-    }
-    __syncwarp();
-    for (int t = lane; t < cnt; t += 32) {
-        const unsigned long long o = base + t;
-        b.pairs_u[o] = Pair{q, surv_c[t]};
-        b.lbi_u[o] = surv_v[t];
-    }
+    emit_survivors(b, q, sg, nsegs, nw, wid, cnt, cnt1, kp, surv_c, surv_v);
     __syncwarp();  // the survivor buffer is refilled by the next segment
     }  // segments of this CTA
+}
+
+// ---------------------------------------------------------------------------
+// Query terms and pair sums of the batched filter (k_lbi_batch below), in
+// packed fp32x2 arithmetic: lane l holds the query terms of its 16-byte
+// pieces l, l + 32, ... of a row of 32 MT elements, two indices per float2.
+// The second sum's term is restated as
+//   d(y, [min(XL, LU), max(XU, UL)]) = max(min(y - XU, A), min(XL - y, B), 0)
+// with the per-query constants A = y - U(L) and B = L(U) - y: rounding is
+// monotone, so fl(y - max(XU, UL)) = min(fl(y - XU), fl(y - UL)) and
+// fl(min(XL, LU) - y) = min(fl(XL - y), fl(LU - y)), and every term equals
+// the one k_lbi_filter forms.
+// ---------------------------------------------------------------------------
+template <int MT>
+struct QueryPacked {
+    float2 u[MT / 2], l[MT / 2], y[MT / 2], a[MT / 2], b[MT / 2];
+};
+
+template <int MT>
+struct RowsPacked {
+    float4 x[MT / 4], xu[MT / 4], xl[MT / 4];
+};
+
+template <int MT>
+__device__ __forceinline__ void query_load_packed(QueryPacked<MT> &Q, const CascadeBufs &b, int q) {
+    const int lane = threadIdx.x & 31;
+    const int64_t o = (int64_t)q * (32 * MT) + 4 * lane;
+#pragma unroll
+    for (int j = 0; j < MT / 4; ++j) {
+        const float4 u = ldg4(b.U + o + 128 * j), l = ldg4(b.L + o + 128 * j), y = ldg4(b.queries + o + 128 * j);
+        const float4 ul = ldg4(b.UL + o + 128 * j), lu = ldg4(b.LU + o + 128 * j);
+        Q.u[2 * j] = make_float2(u.x, u.y);
+        Q.u[2 * j + 1] = make_float2(u.z, u.w);
+        Q.l[2 * j] = make_float2(l.x, l.y);
+        Q.l[2 * j + 1] = make_float2(l.z, l.w);
+        Q.y[2 * j] = make_float2(y.x, y.y);
+        Q.y[2 * j + 1] = make_float2(y.z, y.w);
+        Q.a[2 * j] = make_float2(y.x - ul.x, y.y - ul.y);
+        Q.a[2 * j + 1] = make_float2(y.z - ul.z, y.w - ul.w);
+        Q.b[2 * j] = make_float2(lu.x - y.x, lu.y - y.y);
+        Q.b[2 * j + 1] = make_float2(lu.z - y.z, lu.w - y.w);
+    }
+}
+
+// This lane's parts of LB_Keogh^p (s1) and of the second sum (s2) of one pair.
+template <int P, int MT>
+__device__ __forceinline__ void pair_sums(const QueryPacked<MT> &Q, const RowsPacked<MT> &r, float &s1, float &s2) {
+    const float2 m1 = make_float2(-1.0f, -1.0f);
+    float2 a1 = make_float2(0.0f, 0.0f), a2 = make_float2(0.0f, 0.0f);
+#pragma unroll
+    for (int j = 0; j < MT / 4; ++j)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int t = 2 * j + h;
+            const float2 x = h ? make_float2(r.x[j].z, r.x[j].w) : make_float2(r.x[j].x, r.x[j].y);
+            const float2 xu = h ? make_float2(r.xu[j].z, r.xu[j].w) : make_float2(r.xu[j].x, r.xu[j].y);
+            const float2 xl = h ? make_float2(r.xl[j].z, r.xl[j].w) : make_float2(r.xl[j].x, r.xl[j].y);
+            const float2 d1 = __ffma2_rn(Q.u[t], m1, x);  // x - U
+            const float2 d2 = __ffma2_rn(x, m1, Q.l[t]);  // L - x
+            const float2 k = make_float2(max3f(d1.x, d2.x, 0.0f), max3f(d1.y, d2.y, 0.0f));
+            a1 = (P == 1) ? __fadd2_rn(a1, k) : __ffma2_rn(k, k, a1);
+            const float2 e1 = __ffma2_rn(xu, m1, Q.y[t]);  // y - XU
+            const float2 e2 = __ffma2_rn(Q.y[t], m1, xl);  // XL - y
+            const float2 g = make_float2(max3f(fminf(e1.x, Q.a[t].x), fminf(e2.x, Q.b[t].x), 0.0f),
+                                         max3f(fminf(e1.y, Q.a[t].y), fminf(e2.y, Q.b[t].y), 0.0f));
+            a2 = (P == 1) ? __fadd2_rn(a2, g) : __ffma2_rn(g, g, a2);
+        }
+    s1 = a1.x + a1.y;
+    s2 = a2.x + a2.y;
+}
+
+// ---------------------------------------------------------------------------
+// Filter with batched reductions: the compiled fast case of k_lbi_filter
+// (rows of exactly 32 MT elements, MT = 4 or 8, 16-byte pieces, the
+// piecewise-sum pre-filter and LB_Improved on), with the same row ring, the
+// same terms (formed by pair_sums above) and the same tests, but the pairs
+// of a warp taken eight at a time.  Each lane keeps its partial sums of the eight pairs (LB_Keogh and
+// the second sum: 16 values) in registers; one transposed butterfly then
+// reduces all 16 over the warp (each exchange step halves the values a lane
+// holds), so that lane 2j ends with pair j's LB_Keogh and lane 16 + 2j with
+// its second sum.  The eight decisions and the survivors' compaction are
+// made by eight lanes at once.  Against one reduction chain and one round of
+// single-lane bookkeeping per pair, this removes about half of the
+// instructions a pair costs and the serial shuffle latency between pairs.
+// ---------------------------------------------------------------------------
+constexpr int kLbiBatch = 8;
+
+// v[16] over the warp: lane l returns the warp sum of v[(l >> 1) & 15].
+__device__ __forceinline__ float warp_sum16_transposed(float (&v)[16]) {
+    const int lane = threadIdx.x & 31;
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const float send = b4 ? v[i] : v[i + 8];
+        const float keep = b4 ? v[i + 8] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float send = b3 ? v[i] : v[i + 4];
+        const float keep = b3 ? v[i + 4] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const float send = b2 ? v[i] : v[i + 2];
+        const float keep = b2 ? v[i + 2] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    float r = (b1 ? v[1] : v[0]) + __shfl_xor_sync(0xffffffffu, b1 ? v[0] : v[1], 2);
+    return r + __shfl_xor_sync(0xffffffffu, r, 1);
+}
+
+template <int P, int MT>
+__global__ void __launch_bounds__(256, 2) k_lbi_batch(CascadeBufs b) {
+    static_assert(MT == 4 || MT == 8, "rows of 128 or 256 elements");
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int nw = blockDim.x >> 5;
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int q = blockIdx.x;
+    const int per_warp_cap = b.seg_len / nw + 32;
+    float *ring = reinterpret_cast<float *>(smraw) + (size_t)wid * env_ring_floats<MT>();
+    int32_t *surv_c = reinterpret_cast<int32_t *>(smraw) + (size_t)nw * env_ring_floats<MT>() +
+                      (size_t)wid * 2 * per_warp_cap;
+    float *surv_v = reinterpret_cast<float *>(surv_c + per_warp_cap);
+    QueryPacked<MT> Qp;
+    query_load_packed<MT>(Qp, b, q);
+    const float bq = (b.mode == DTW_MODE_NOPRUNE) ? kInf : load_threshold(b.bsf + q);
+    const float thr = bq * (1.0f + b.slack);
+    const float thr_m = thr * b.summary_scale;  // the matrix holds the piecewise-sum bound
+    const int nsegs = b.nseg / nw;
+    float *lbrow = b.lb + (int64_t)q * b.N;
+    const int stride = nw * 32;
+    for (int sj = 0; sj < b.seg_per_cta; ++sj) {
+        const int sg = blockIdx.y * b.seg_per_cta + sj;
+        if (sg >= nsegs) break;
+        const int c0 = sg * b.seg_len;
+        const int c1 = min(b.N, c0 + b.seg_len);
+        const int cnt1 = scan_segment(lbrow, c0, c1, wid, stride, thr_m, surv_c, surv_v);
+        unsigned long long kp = 0;
+        int cnt = 0;
+#pragma unroll
+        for (int e = 0; e < kEnvStages - 1; ++e) {
+            if (e < cnt1) env_issue<MT, true>(ring, e, b, surv_c[e], true, true);
+            cp_async_commit();
+        }
+        for (int e0 = 0; e0 < cnt1; e0 += kLbiBatch) {
+            float v[16];
+#pragma unroll
+            for (int u = 0; u < kLbiBatch; ++u) {
+                const int e = e0 + u;
+                float a1 = 0.0f, a2 = 0.0f;
+                if (e < cnt1) {
+                    // the stage refilled here was read (and used) by pair e - 1
+                    const int ahead = e + kEnvStages - 1;
+                    if (ahead < cnt1) env_issue<MT, true>(ring, ahead % kEnvStages, b, surv_c[ahead], true, true);
+                    cp_async_commit();
+                    cp_async_wait<kEnvStages - 1>();
+                    RowsPacked<MT> R;
+                    const float *stage = ring + (size_t)(e % kEnvStages) * 3 * 32 * MT;
+#pragma unroll
+                    for (int jj = 0; jj < MT / 4; ++jj) {
+                        R.x[jj] = *reinterpret_cast<const float4 *>(stage + 4 * (lane + 32 * jj));
+                        R.xu[jj] = *reinterpret_cast<const float4 *>(stage + 32 * MT + 4 * (lane + 32 * jj));
+                        R.xl[jj] = *reinterpret_cast<const float4 *>(stage + 64 * MT + 4 * (lane + 32 * jj));
+                    }
+                    pair_sums<P, MT>(Qp, R, a1, a2);
+                }
+                v[u] = a1;
+                v[u + 8] = a2;
+            }
+            // lane 2j: pair j's LB_Keogh^p; lane 16 + 2j: its second sum
+            const float s1 = warp_sum16_transposed(v);
+            const float s2 = __shfl_down_sync(0xffffffffu, s1, 16);
+            const int j = lane >> 1;
+            const bool decides = lane < 16 && !(lane & 1) && e0 + j < cnt1;
+            const int cc = decides ? surv_c[e0 + j] : 0;
+            const float val = s1 > thr ? s1 : s1 + s2;
+            const bool pass = decides && val <= thr;
+            const unsigned m = __ballot_sync(0xffffffffu, pass);
+            kp += __popc(__ballot_sync(0xffffffffu, decides && s1 <= thr));
+            __syncwarp();  // every decider has read its candidate before the list is rewritten
+            if (pass) {
+                const int r = cnt + __popc(m & ((1u << lane) - 1));
+                surv_c[r] = cc;  // r <= e0 + j: survivors stay in place or move down
+                surv_v[r] = val;
+                lbrow[cc] = s1;  // LB_Keogh^p, where the DTW stage's cumulative bound starts
+            }
+            cnt += __popc(m);
+            __syncwarp();
+        }
+        cp_async_wait<0>();  // only empty groups remain
+        emit_survivors(b, q, sg, nsegs, nw, wid, cnt, cnt1, kp, surv_c, surv_v);
+        __syncwarp();  // the survivor buffer is refilled by the next segment
+    }
 }
 
 // chunk length the filter keeps in registers (0: strided loads)
@@ -796,6 +1013,19 @@ static void lbi_filter_dispatch(const CascadeBufs &b, bool vec, cudaStream_t s) 
     }
 }
 
+bool lbi_batch_applies(int n, bool summary, bool lbi_inline) { return (n == 128 || n == 256) && summary && lbi_inline; }
+
+template <int P, int MT>
+static void lbi_batch_go(const CascadeBufs &b, cudaStream_t s) {
+    const int nw = b.filter_warps;
+    const size_t smem = lbi_filter_smem(b.n, b.S, b.seg_len, nw);
+    const int nsegs = b.nseg / nw;
+    const dim3 grid(b.Q, (nsegs + b.seg_per_cta - 1) / b.seg_per_cta);
+    auto kern = k_lbi_batch<P, MT>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kern<<<grid, nw * 32, smem, s>>>(b);
+}
+
 cudaError_t launch_lbi_filter(const CascadeBufs &b, cudaStream_t s) {
     if (b.N <= 0 || b.Q <= 0) return cudaSuccess;
     if (b.lbi_inline && (b.XU == nullptr || b.XL == nullptr || b.UL == nullptr || b.LU == nullptr))
@@ -804,6 +1034,16 @@ cudaError_t launch_lbi_filter(const CascadeBufs &b, cudaStream_t s) {
     // envelope rows and the query envelopes always do)
     const bool vec = (b.n % 4 == 0) && ((reinterpret_cast<uintptr_t>(b.db) & 15) == 0) &&
                      ((reinterpret_cast<uintptr_t>(b.queries) & 15) == 0);
+    if (b.filter_path == 2 && vec && lbi_batch_applies(b.n, b.summary != 0, b.lbi_inline != 0)) {
+        if (b.n == 256) {
+            if (b.p == 1) lbi_batch_go<1, 8>(b, s);
+            else lbi_batch_go<2, 8>(b, s);
+        } else {
+            if (b.p == 1) lbi_batch_go<1, 4>(b, s);
+            else lbi_batch_go<2, 4>(b, s);
+        }
+        return cudaGetLastError();
+    }
     if (b.p == 1) lbi_filter_dispatch<1>(b, vec, s);
     else lbi_filter_dispatch<2>(b, vec, s);
     return cudaGetLastError();

@@ -66,7 +66,7 @@ struct Admission {
     size_t bound() const {
         const size_t G = groups.size();
         return ws + 2 * ((size_t)total * 4 + 256) + (size_t)Q * sizeof(QMap) + 256 + (size_t)gout * 12 + 512 +
-               (size_t)Q * kmax * 12 + 512 + (G + 1) * 2 * CNT_NUM * 8 + 256 + 4096;
+               (size_t)Q * kmax * 12 + 512 + (G + 1) * CNT_ALLOC * 8 + 256 + 4096;
     }
 };
 

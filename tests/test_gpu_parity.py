@@ -417,3 +417,22 @@ def test_knn_filter_layouts(api, p, n, w):
     db = synth.random_walks(600, n, seed=90 + n)
     qs = synth.random_walks(5, n, seed=91 + n, stream=synth.STREAM_QUERY)
     _knn_case(api, db, qs, w, p, 2)
+
+
+@pytest.mark.parametrize("p", [1, 2])
+@pytest.mark.parametrize("n,w", [(256, 25), (128, 12)])
+def test_filter_paths_agree(api, p, n, w):
+    # one warp per pair (1) and batches of eight pairs per warp (2) give the
+    # same neighbours; with more queries
+    # than one CTA wave and segments with ragged tails
+    db = synth.random_walks(9_000, n, seed=150 + n)
+    qs = synth.random_walks(70, n, seed=151 + n, stream=synth.STREAM_QUERY)
+    out = {}
+    for path in (1, 2):
+        for k in (1, 7):
+            out[path, k] = api.knn_search(cuda(db), cuda(qs), w, p, k, filter_path=path)
+    for k in (1, 7):
+        for path in (2,):
+            assert torch.equal(out[path, k][0], out[1, k][0]) and torch.equal(out[path, k][1], out[1, k][1])
+    ri, rd, _ = oracle.knn_cascade(db, qs[:12], w, p, 7, mode=1, threads=8)
+    assert_knn(db, qs[:12], w, p, 7, out[2, 7][0][:12], out[2, 7][1][:12], ri, rd)
