@@ -80,7 +80,7 @@ def parse():
     ap.add_argument("--bucket-N", type=int, default=20_000, help="batched: series per length bucket")
     ap.add_argument("--batch-Q", type=int, default=4096, help="batched: queries per batch")
     ap.add_argument("--batch-ks", default="1,10", help="batched: neighbour counts, one run each")
-    ap.add_argument("--batch-arms", default="graph,streams,serial,per_query",
+    ap.add_argument("--batch-arms", default="graph,persistent,streams,serial,per_query",
                     help="batched: execution arms to time")
     ap.add_argument("--serve-rates", default="1000,5000,20000", help="serve: Poisson arrival rates (queries/s)")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="serve: arrival window per rate")
@@ -515,14 +515,15 @@ def extra_workloads(a):
 
     b = copy.copy(a)
     b.steps, b.warmup = min(a.steps, 5), min(max(a.warmup, 1), 2)
-    b.batch_arms = "graph,per_query"
+    b.batch_arms = "graph,persistent,per_query"
     b.per_query_steps = 1
     out = {}
     t0 = time.time()
     r = run_batched(b)
     out["batched"] = {
         "metric": r["metric"], "value": r["value"], "unit": r["unit"], "ms_per_step": r["ms_per_step"],
-        "e2e": r["e2e"], "vs_per_query": r["vs_per_query"], "config": r["config"], "clocks": r["clocks"],
+        "e2e": r["e2e"], "vs_per_query": r["vs_per_query"], "persistent_vs_per_query": r["persistent_vs_per_query"],
+        "persistent_vs_graph": r["persistent_vs_graph"], "config": r["config"], "clocks": r["clocks"],
         "per_k": {k: {"arms": v["arms"], "e2e": v["e2e"], "autotune_seconds": v["autotune_seconds"]}
                   for k, v in r["per_k"].items()},
         "wall_s": time.time() - t0}
@@ -573,7 +574,8 @@ def run_batched(a):
     flush = torch.empty(256 * 2**20 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
     arms_wanted = [x for x in a.batch_arms.split(",") if x]
-    arm_kw = {"graph": {"graph": True}, "streams": {}, "serial": {"serial": True}, "per_query": {"per_query": True}}
+    arm_kw = {"graph": {"graph": True}, "streams": {}, "serial": {"serial": True}, "per_query": {"per_query": True},
+              "persistent": {"graph": True, "persistent": True}}
     sampler = ClockSampler(0)
     t_wall0 = time.time()
     per_k = {}
@@ -581,6 +583,8 @@ def run_batched(a):
     for k in [int(x) for x in a.batch_ks.split(",") if x]:
         t0 = time.perf_counter()
         ref_i, ref_d = ix.search_flat(flat, lens, ws, k, autotune=True)
+        if "persistent" in arms_wanted:  # the persistent arm's chunk length
+            ix.search_flat(flat, lens, ws, k, autotune=True, persistent=True)
         torch.cuda.synchronize()
         tune_s = time.perf_counter() - t0
         arms = {}
@@ -646,6 +650,11 @@ def run_batched(a):
                 "d2h_bytes_per_step": per_k[ks[0]]["e2e"]["d2h_bytes_per_step"]},
         "vs_per_query": {k: (per_k[k]["arms"]["graph"]["value"] / per_k[k]["arms"]["per_query"]["value"])
                          for k in ks if "graph" in per_k[k]["arms"] and "per_query" in per_k[k]["arms"]},
+        "persistent_vs_per_query": {k: (per_k[k]["arms"]["persistent"]["value"] /
+                                        per_k[k]["arms"]["per_query"]["value"])
+                                    for k in ks if "persistent" in per_k[k]["arms"] and "per_query" in per_k[k]["arms"]},
+        "persistent_vs_graph": {k: (per_k[k]["arms"]["persistent"]["value"] / per_k[k]["arms"]["graph"]["value"])
+                                for k in ks if "persistent" in per_k[k]["arms"] and "graph" in per_k[k]["arms"]},
         "per_k": per_k, "index": info, "clocks": clocks,
     }
     return out

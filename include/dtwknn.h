@@ -268,6 +268,22 @@ dtw_status dtw_band_noalloc(const float *x, const float *y, int64_t N, int32_t y
  *   DTW_BATCH_PER_QUERY run every query as its own cascade (one query per
  *                       launch of each stage), one after another: the
  *                       unbatched baseline.  GRAPH is ignored with it.
+ *   DTW_BATCH_PERSISTENT after each group's first stages (envelopes, the
+ *                       stored bound of every pair, seeds and their
+ *                       threshold), run the rest of the cascade for all
+ *                       groups in one persistent launch over a device queue
+ *                       of (query, candidate chunk) items: each warp takes an
+ *                       item and runs LB_Keogh, LB_Improved and the band DTW
+ *                       (one warp per pair) on that chunk, against the
+ *                       query's live threshold, which every completed DTW
+ *                       lowers at once; one more launch forms every query's
+ *                       top-k.  Needs the default cascade mode, p in {1, 2},
+ *                       bands 2w + 1 <= 512 and groups small enough for one
+ *                       cascade run (about 2^27 / N queries); otherwise the
+ *                       call fails with DTW_ERR_INVALID_ARG.  With AUTOTUNE
+ *                       the candidate chunk length is also timed (512 to
+ *                       4096) the first time, on the batch itself.
+ *                       Combines with GRAPH; not with SERIAL or PER_QUERY.
  * Memory: the index grows a device arena for the largest batch seen (growth
  * synchronises the device and drops the cached graphs) and a pinned host map
  * of one entry per query.  Calls on one index are serialised by a mutex, and
@@ -279,7 +295,8 @@ enum {
     DTW_BATCH_GRAPH = 1,
     DTW_BATCH_AUTOTUNE = 2,
     DTW_BATCH_SERIAL = 4,
-    DTW_BATCH_PER_QUERY = 8
+    DTW_BATCH_PER_QUERY = 8,
+    DTW_BATCH_PERSISTENT = 16
 };
 
 /* Cascade parameters of one (n, w, k); see dtw_options for parts, seeds and dtw_path.

@@ -91,7 +91,7 @@ class IndexStats(ctypes.Structure):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
 
 
-BATCH_GRAPH, BATCH_AUTOTUNE, BATCH_SERIAL, BATCH_PER_QUERY = 1, 2, 4, 8
+BATCH_GRAPH, BATCH_AUTOTUNE, BATCH_SERIAL, BATCH_PER_QUERY, BATCH_PERSISTENT = 1, 2, 4, 8, 16
 
 
 class ServerConfig(ctypes.Structure):

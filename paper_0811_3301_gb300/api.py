@@ -263,7 +263,7 @@ class DtwIndex:
         return st.as_dict()
 
     def search_flat(self, flat: torch.Tensor, lengths, w, k, *, k_stride: int | None = None, graph: bool = False,
-                    autotune: bool = False, serial: bool = False, per_query: bool = False,
+                    autotune: bool = False, serial: bool = False, per_query: bool = False, persistent: bool = False,
                     out_idx: torch.Tensor | None = None, out_dist: torch.Tensor | None = None,
                     return_stats: bool = False):
         """Batched search over queries concatenated in `flat` (1-D float32, host or CUDA).
@@ -288,7 +288,8 @@ class DtwIndex:
         if out_dist is None:
             out_dist = torch.empty((Q, k_stride), dtype=torch.float32, device=dev, pin_memory=pin)
         flags = ((N.BATCH_GRAPH if graph else 0) | (N.BATCH_AUTOTUNE if autotune else 0) |
-                 (N.BATCH_SERIAL if serial else 0) | (N.BATCH_PER_QUERY if per_query else 0))
+                 (N.BATCH_SERIAL if serial else 0) | (N.BATCH_PER_QUERY if per_query else 0) |
+                 (N.BATCH_PERSISTENT if persistent else 0))
         st = N.Stats()
         N.check(N.lib.dtw_index_search(self._h, _ptr(flat) if flat.numel() else None, Q,
                                        lens.ctypes.data, ws.ctypes.data, ks.ctypes.data, k_stride, flags,

@@ -216,27 +216,10 @@ size_t cascade_ws_bytes(const CascadePlan &pl) {
 // ---------------------------------------------------------------------------
 // one run over qn <= Qc queries
 // ---------------------------------------------------------------------------
-cudaError_t cascade_run(const CascadePlan &pl, const CascadeWs &l, const float *db, const float *PX,
-                        const unsigned *xmax_bits, const float *XU, const float *XL, const float *q, int qn,
-                        int64_t *out_idx, float *out_dist, unsigned long long *counters, cudaStream_t s) {
-    if (plan_needs_db_envelope(pl) && (XU == nullptr || XL == nullptr)) return cudaErrorInvalidValue;
-    const int n = pl.n, we = pl.we, p = pl.p, k = pl.k;
+CascadeBufs cascade_bufs(const CascadePlan &pl, const CascadeWs &l, const float *db, const float *XU, const float *XL,
+                         const float *q, int qn, int64_t *out_idx, float *out_dist, unsigned long long *counters) {
     const int64_t N = pl.N;
     const int64_t Nc = N > 0 ? N : 1;
-    unsigned long long *pair_count = l.misc + 0;
-    unsigned long long *cur_seed = l.misc + 1;
-    unsigned long long *cur_pairs = l.misc + 2;
-    unsigned long long *pair_total = l.misc + 4;
-    unsigned long long *seed_counters = counters + CNT_NUM;
-    RUN_TRY(cudaMemsetAsync(l.misc, 0, 8 * sizeof(unsigned long long), s));
-    QueryCopies qc;
-    qc.data = l.copies;
-    qc.padl = pl.g.padl;
-    qc.ylen = pl.g.ylen;
-    {
-        StageTimer tm(DTW_STAGE_ENVELOPE, s);
-        RUN_TRY(launch_envelope(q, qn, n, we, l.U, l.L, qc, pl.g.padl, s, l.UL, l.LU));
-    }
     CascadeBufs b{};
     b.db = db;
     b.queries = q;
@@ -246,13 +229,15 @@ cudaError_t cascade_run(const CascadePlan &pl, const CascadeWs &l, const float *
     b.LU = l.LU;
     b.XU = XU;
     b.XL = XL;
-    b.qc = qc;
+    b.qc.data = l.copies;
+    b.qc.padl = pl.g.padl;
+    b.qc.ylen = pl.g.ylen;
     b.N = (int)N;
     b.Q = qn;
-    b.n = n;
-    b.w = we;
-    b.p = p;
-    b.k = k;
+    b.n = pl.n;
+    b.w = pl.we;
+    b.p = pl.p;
+    b.k = pl.k;
     b.mode = pl.mode;
     b.slack = pl.slack;
     b.lb = l.lb;
@@ -269,15 +254,15 @@ cudaError_t cascade_run(const CascadePlan &pl, const CascadeWs &l, const float *
     b.qstart = l.qstart;
     b.qstart_b = l.qstart_b;
     b.order_first = pl.order_first;
-    b.pair_total = pair_total;
+    b.pair_total = l.misc + 4;
     b.lbi_inline = pl.mode == DTW_MODE_IMPROVED ? 1 : 0;
     b.summary = pl.summary ? 1 : 0;
-    b.summary_scale = (pl.summary && p == 2) ? (float)pl.pg.smax : 1.0f;
+    b.summary_scale = (pl.summary && pl.p == 2) ? (float)pl.pg.smax : 1.0f;
     b.pairs = l.pairs;
     b.pair_lbi = l.pair_lbi;
     b.pair_res = l.pair_res;
     b.pair_cap = (int64_t)qn * Nc;
-    b.pair_count = pair_count;
+    b.pair_count = l.misc + 0;
     b.seg_len = pl.seg_len;
     b.seg_per_cta = pl.seg_per_cta;
     b.filter_warps = pl.filter_warps;
@@ -286,57 +271,84 @@ cudaError_t cascade_run(const CascadePlan &pl, const CascadeWs &l, const float *
     b.nseg = N > 0 ? pl.nseg : 0;
     b.seg_start = l.seg_start;
     b.seg_count = l.seg_count;
-    b.cursor = cur_pairs;
+    b.cursor = l.misc + 2;
     b.counters = counters;
     b.out_idx = out_idx;
     b.out_dist = out_dist;
+    return b;
+}
 
+// The DTW job of a run's seed pairs (their results go to the seed slots).
+static DtwJob seed_job(const CascadePlan &pl, const CascadeWs &l, const CascadeBufs &b) {
+    DtwJob js{};
+    js.db = b.db;
+    js.n = pl.n;
+    js.w = pl.we;
+    js.p = pl.p;
+    js.k = pl.k;
+    js.qc = b.qc;
+    js.pairs = l.seed_pairs;
+    js.npairs = (int64_t)b.Q * pl.S;
+    js.slack = pl.slack;
+    js.bsf = l.bsf;
+    js.gmin = l.gmin;
+    js.res = l.seed_res;
+    js.cursor = l.misc + 1;
+    js.counters = b.counters + CNT_NUM;
+    // On the warp path, where each warp computes its seeds one after another,
+    // they run with early abandoning against the live threshold, which the
+    // seeds that complete first set and lower (an abandoned seed's DTW
+    // exceeds a threshold that is itself at least the final k-th best
+    // distance, so it cannot be a neighbour).  One thread per pair runs all
+    // seeds at once, so there the checks would only cost.
+    js.lanes = use_lanes(pl, js.npairs, false);
+    js.abandon = (js.lanes && pl.mode != DTW_MODE_NOPRUNE) ? 1 : 0;
+    return js;
+}
+
+cudaError_t cascade_prefix(const CascadePlan &pl, const CascadeWs &l, const CascadeBufs &b, const float *PX,
+                           const unsigned *xmax_bits, cudaStream_t s) {
+    if (plan_needs_db_envelope(pl) && (b.XU == nullptr || b.XL == nullptr)) return cudaErrorInvalidValue;
+    const int n = pl.n, p = pl.p, qn = b.Q;
+    const int64_t N = pl.N;
+    RUN_TRY(cudaMemsetAsync(l.misc, 0, 8 * sizeof(unsigned long long), s));
+    {
+        StageTimer tm(DTW_STAGE_ENVELOPE, s);
+        RUN_TRY(launch_envelope(b.queries, qn, n, pl.we, l.U, l.L, b.qc, pl.g.padl, s, l.UL, l.LU));
+    }
+    if (N <= 0) return cudaSuccess;
+    {
+        StageTimer tm(DTW_STAGE_LB_KEOGH, s);
+        if (pl.summary) {
+            // piecewise-sum bound of every pair: the tile kernel on the d part sums
+            RUN_TRY(launch_query_summary(l.U, l.L, qn, n, pl.parts, xmax_bits, l.PU, l.PL, 1, s));
+            RUN_TRY(launch_lbk_tile(PX, (int)N, l.PU, l.PL, qn, pl.parts, p, l.lb, l.tile_min, s));
+        } else {
+            RUN_TRY(launch_lbk_tile(b.db, (int)N, l.U, l.L, qn, n, p, l.lb, l.tile_min, s));
+        }
+    }
+    {
+        StageTimer tm(DTW_STAGE_SEED_SELECT, s);
+        RUN_TRY(launch_seed_select(b, s));
+    }
+    {
+        StageTimer tm(DTW_STAGE_SEED_DTW, s);
+        RUN_TRY(launch_dtw_any(seed_job(pl, l, b), pl.g, s));
+    }
+    {
+        StageTimer tm(DTW_STAGE_SEED_KTH, s);
+        RUN_TRY(launch_seed_kth(b, s));
+    }
+    return cudaSuccess;
+}
+
+cudaError_t cascade_run(const CascadePlan &pl, const CascadeWs &l, const float *db, const float *PX,
+                        const unsigned *xmax_bits, const float *XU, const float *XL, const float *q, int qn,
+                        int64_t *out_idx, float *out_dist, unsigned long long *counters, cudaStream_t s) {
+    const CascadeBufs b = cascade_bufs(pl, l, db, XU, XL, q, qn, out_idx, out_dist, counters);
+    RUN_TRY(cascade_prefix(pl, l, b, PX, xmax_bits, s));
+    const int64_t N = pl.N;
     if (N > 0) {
-        {
-            StageTimer tm(DTW_STAGE_LB_KEOGH, s);
-            if (pl.summary) {
-                // piecewise-sum bound of every pair: the tile kernel on the d part sums
-                RUN_TRY(launch_query_summary(l.U, l.L, qn, n, pl.parts, xmax_bits, l.PU, l.PL, 1, s));
-                RUN_TRY(launch_lbk_tile(PX, (int)N, l.PU, l.PL, qn, pl.parts, p, l.lb, l.tile_min, s));
-            } else {
-                RUN_TRY(launch_lbk_tile(db, (int)N, l.U, l.L, qn, n, p, l.lb, l.tile_min, s));
-            }
-        }
-        {
-            StageTimer tm(DTW_STAGE_SEED_SELECT, s);
-            RUN_TRY(launch_seed_select(b, s));
-        }
-        // Seeds.  On the warp path, where each warp computes its seeds one
-        // after another, they run with early abandoning against the live
-        // threshold, which the seeds that complete first set and lower (an
-        // abandoned seed's DTW exceeds a threshold that is itself at least the
-        // final k-th best distance, so it cannot be a neighbour).  One thread
-        // per pair runs all seeds at once, so there the checks would only cost.
-        DtwJob js{};
-        js.db = db;
-        js.n = n;
-        js.w = we;
-        js.p = p;
-        js.k = k;
-        js.qc = qc;
-        js.pairs = l.seed_pairs;
-        js.npairs = (int64_t)qn * pl.S;
-        js.slack = pl.slack;
-        js.bsf = l.bsf;
-        js.gmin = l.gmin;
-        js.res = l.seed_res;
-        js.cursor = cur_seed;
-        js.counters = seed_counters;
-        js.lanes = use_lanes(pl, js.npairs, false);
-        js.abandon = (js.lanes && pl.mode != DTW_MODE_NOPRUNE) ? 1 : 0;
-        {
-            StageTimer tm(DTW_STAGE_SEED_DTW, s);
-            RUN_TRY(launch_dtw_any(js, pl.g, s));
-        }
-        {
-            StageTimer tm(DTW_STAGE_SEED_KTH, s);
-            RUN_TRY(launch_seed_kth(b, s));
-        }
         {
             StageTimer tm(DTW_STAGE_LB_IMPROVED, s);
             RUN_TRY(cudaMemsetAsync(l.qcount, 0, (size_t)qn * sizeof(int32_t), s));
@@ -346,14 +358,14 @@ cudaError_t cascade_run(const CascadePlan &pl, const CascadeWs &l, const float *
             StageTimer tm(DTW_STAGE_GROUP, s);
             RUN_TRY(launch_group_by_query(b, s));
         }
-        DtwJob jp = js;
+        DtwJob jp = seed_job(pl, l, b);
         jp.pairs = l.pairs;
-        jp.npairs = (int64_t)qn * Nc;
-        jp.npairs_dev = pair_total;
+        jp.npairs = (int64_t)qn * N;
+        jp.npairs_dev = b.pair_total;
         jp.pair_lbi = pl.mode == DTW_MODE_NOPRUNE ? nullptr : l.pair_lbi;
         jp.abandon = pl.mode == DTW_MODE_NOPRUNE ? 0 : 1;
         jp.res = l.pair_res;
-        jp.cursor = cur_pairs;
+        jp.cursor = b.cursor;
         jp.counters = counters;
         jp.lanes = use_lanes(pl, jp.npairs, true);
         // the grouped pairs' result slots hold their LB_Keogh^p (k_gather)

@@ -71,6 +71,19 @@ cudaError_t cascade_run(const CascadePlan &pl, const CascadeWs &ws, const float 
                         const unsigned *xmax_bits, const float *XU, const float *XL, const float *q, int qn,
                         int64_t *out_idx, float *out_dist, unsigned long long *counters, cudaStream_t s);
 
+// The device buffers of one run (cascade_run's view of ws and its
+// arguments), for callers that launch stages themselves.
+CascadeBufs cascade_bufs(const CascadePlan &pl, const CascadeWs &ws, const float *db, const float *XU, const float *XL,
+                         const float *q, int qn, int64_t *out_idx, float *out_dist, unsigned long long *counters);
+
+// The first stages of a run (asynchronous on s, allocates nothing): the
+// queries' envelopes and padded copies, the stored bound of every pair (the
+// piecewise-sum bound or LB_Keogh), the seeds, their DTW and the seed
+// threshold.  Afterwards b.bsf / b.gmin hold each query's threshold, b.lb
+// its bounds (NaN at the seeds) and the seed slots their DTW^p.
+cudaError_t cascade_prefix(const CascadePlan &pl, const CascadeWs &ws, const CascadeBufs &b, const float *PX,
+                           const unsigned *xmax_bits, cudaStream_t s);
+
 // Whether a run under pl reads the database envelopes XU, XL.
 inline bool plan_needs_db_envelope(const CascadePlan &pl) { return pl.N > 0 && pl.mode == DTW_MODE_IMPROVED; }
 

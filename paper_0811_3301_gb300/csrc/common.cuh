@@ -70,10 +70,57 @@ __device__ __forceinline__ float dtw_cost(float d, float m) {
     return fmaxf(fabsf(d), m);
 }
 
+__device__ __forceinline__ float4 ldg4(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
+
+// Four consecutive bound terms d(v, [lo, hi])^P added to acc.
+template <int P>
+__device__ __forceinline__ float acc_dist4(float acc, float4 v, float4 lo, float4 hi) {
+    acc = acc_dist<P>(acc, v.x, lo.x, hi.x);
+    acc = acc_dist<P>(acc, v.y, lo.y, hi.y);
+    acc = acc_dist<P>(acc, v.z, lo.z, hi.z);
+    return acc_dist<P>(acc, v.w, lo.w, hi.w);
+}
+__device__ __forceinline__ float4 min4(float4 a, float4 b) {
+    return make_float4(fminf(a.x, b.x), fminf(a.y, b.y), fminf(a.z, b.z), fminf(a.w, b.w));
+}
+__device__ __forceinline__ float4 max4(float4 a, float4 b) {
+    return make_float4(fmaxf(a.x, b.x), fmaxf(a.y, b.y), fmaxf(a.z, b.z), fmaxf(a.w, b.w));
+}
+
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
+}
+
+// Pairs per warp whose bound sums are reduced together (warp_sum16_transposed).
+constexpr int kLbiBatch = 8;
+
+// v[16] over the warp (a transposed butterfly: each exchange step halves the
+// values a lane holds): lane l returns the warp sum of v[(l >> 1) & 15].
+__device__ __forceinline__ float warp_sum16_transposed(float (&v)[16]) {
+    const int lane = threadIdx.x & 31;
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const float send = b4 ? v[i] : v[i + 8];
+        const float keep = b4 ? v[i + 8] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float send = b3 ? v[i] : v[i + 4];
+        const float keep = b3 ? v[i + 4] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const float send = b2 ? v[i] : v[i + 2];
+        const float keep = b2 ? v[i + 2] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    float r = (b1 ? v[1] : v[0]) + __shfl_xor_sync(0xffffffffu, b1 ? v[0] : v[1], 2);
+    return r + __shfl_xor_sync(0xffffffffu, r, 1);
 }
 
 // Non-negative floats order like their bit patterns; +INF is 0x7f800000.

@@ -114,6 +114,7 @@ void slot_release(Slot &sl) {
     for (auto st : sl.pool) cudaStreamSynchronize(st);
     if (sl.arena) cudaFree(sl.arena);
     if (sl.hmap) cudaFreeHost(sl.hmap);
+    if (sl.hptab) cudaFreeHost(sl.hptab);
     for (auto st : sl.pool) cudaStreamDestroy(st);
     for (auto ev : sl.join) cudaEventDestroy(ev);
     if (sl.fork) cudaEventDestroy(sl.fork);
@@ -159,6 +160,23 @@ static dtw_status slot_reserve_map(Slot &sl, int64_t Q) {
         return ix_fail(DTW_ERR_OOM, "pinned query map of %zu entries: %s", want, cudaGetErrorString(e));
     }
     sl.hmap_cap = want;
+    return DTW_OK;
+}
+
+static dtw_status slot_reserve_ptab(Slot &sl, size_t G) {
+    if (sl.hptab_cap >= G) return DTW_OK;
+    IX_TRY(cudaEventSynchronize(sl.hmap_free));
+    if (sl.hptab) cudaFreeHost(sl.hptab);
+    sl.hptab = nullptr;
+    sl.hptab_cap = 0;
+    const size_t want = std::max<size_t>(G, 64);
+    cudaError_t e = cudaHostAlloc((void **)&sl.hptab, want * sizeof(PersistGroup), cudaHostAllocDefault);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        sl.hptab = nullptr;
+        return ix_fail(DTW_ERR_OOM, "pinned group table of %zu entries: %s", want, cudaGetErrorString(e));
+    }
+    sl.hptab_cap = want;
     return DTW_OK;
 }
 
@@ -264,6 +282,8 @@ BatchLayout layout_batch(Carve &cv, int64_t Q, int64_t total, int64_t gout, int 
     L.oidx = cv.take<int64_t>((size_t)std::max<int64_t>(Q * k_stride, 1));
     L.odist = cv.take<float>((size_t)std::max<int64_t>(Q * k_stride, 1));
     L.counters = cv.take<unsigned long long>(std::max<size_t>(groups.size(), 1) * CNT_ALLOC);
+    L.ptab = cv.take<PersistGroup>(std::max<size_t>(groups.size(), 1));
+    L.pcursor = cv.take<unsigned long long>(1);
     L.ws.resize(groups.size());
     if (shared_ws) {
         const size_t off0 = cv.off;
@@ -351,6 +371,29 @@ dtw_status prepare_batch(dtw_index *ix, int64_t Q, const int32_t *q_len, const i
         gr.stream = (int)(g % ix->slot.pool.size());
     }
     bt.gout = gout;
+    if (flags & DTW_BATCH_PERSISTENT) {
+        if (flags & (DTW_BATCH_SERIAL | DTW_BATCH_PER_QUERY))
+            return ix_fail(DTW_ERR_INVALID_ARG, "DTW_BATCH_PERSISTENT does not combine with SERIAL or PER_QUERY");
+        if (ix->p != 1 && ix->p != 2)
+            return ix_fail(DTW_ERR_INVALID_ARG, "DTW_BATCH_PERSISTENT needs p in {1, 2}");
+        for (const auto &gr : bt.groups) {
+            if (gr.pl.mode != DTW_MODE_IMPROVED)
+                return ix_fail(DTW_ERR_INVALID_ARG, "DTW_BATCH_PERSISTENT needs the LB_Improved cascade mode");
+            const PersistShape sh = persist_shape(gr.pl.n, gr.pl.we);
+            if (sh.g == 0)
+                return ix_fail(DTW_ERR_INVALID_ARG, "DTW_BATCH_PERSISTENT: band %d of n=%d exceeds 512",
+                               2 * gr.pl.we + 1, gr.pl.n);
+            // every query-copy index the lane groups read: column -w (row 0, slot 0)
+            // up to n - 1 + w + CL (row n - 1, the top slot of the band's last lane)
+            if (gr.pl.g.padl < gr.pl.we || (int64_t)gr.pl.g.padl + gr.pl.n + gr.pl.we + sh.cl > gr.pl.g.ylen)
+                return ix_fail(DTW_ERR_INTERNAL, "DTW_BATCH_PERSISTENT: query copies too short for n=%d, w=%d",
+                               gr.pl.n, gr.pl.we);
+            if (gr.qn > gr.pl.Qc)
+                return ix_fail(DTW_ERR_INVALID_ARG,
+                               "DTW_BATCH_PERSISTENT: %d queries of length %d exceed one cascade run (%lld)", gr.qn,
+                               gr.pl.n, (long long)gr.pl.Qc);
+        }
+    }
     return DTW_OK;
 }
 
@@ -395,9 +438,100 @@ void fill_map(const Batch &bt, QMap *hmap) {
     }
 }
 
+// The persistent arm's group table (host copy), for the batch laid out as L.
+// Returns the number of work items (total over the groups).
+static int64_t fill_ptab(const dtw_index *ix, const Batch &bt, const BatchLayout &L, PersistGroup *tab) {
+    int64_t items = 0, qbase = 0;
+    for (size_t g = 0; g < bt.groups.size(); ++g) {
+        const GroupRun &gr = bt.groups[g];
+        const Bucket &bk = ix->buckets[gr.bucket];
+        const CascadeWs &ws = L.ws[g];
+        const CascadeBufs b = cascade_bufs(gr.pl, ws, bk.db, gr.XU, gr.XL, L.grouped + gr.qoff, gr.qn,
+                                           L.gidx + gr.ooff, L.gdist + gr.ooff, L.counters + g * CNT_ALLOC);
+        PersistGroup pg{};
+        pg.db = bk.db;
+        pg.XU = gr.XU;
+        pg.XL = gr.XL;
+        pg.queries = b.queries;
+        pg.U = b.U;
+        pg.L = b.L;
+        pg.UL = b.UL;
+        pg.LU = b.LU;
+        pg.qc = b.qc;
+        pg.lb = b.lb;
+        pg.bsf = b.bsf;
+        pg.gmin = b.gmin;
+        pg.seed_pairs = b.seed_pairs;
+        pg.seed_res = b.seed_res;
+        pg.out_idx = b.out_idx;
+        pg.out_dist = b.out_dist;
+        pg.counters = b.counters;
+        pg.N = (int)bk.N;
+        pg.Q = gr.qn;
+        pg.n = gr.pl.n;
+        pg.w = gr.pl.we;
+        pg.p = gr.pl.p;
+        pg.k = gr.pl.k;
+        pg.S = gr.pl.S;
+        pg.chunk = ix->persist_chunk;
+        pg.nchunks = (int)((bk.N + pg.chunk - 1) / pg.chunk);
+        const PersistShape sh = persist_shape(gr.pl.n, gr.pl.we);
+        pg.dg = sh.g;
+        pg.cl = sh.cl;
+        pg.vec = (gr.pl.n % 4 == 0) && ((reinterpret_cast<uintptr_t>(bk.db) & 15) == 0) &&
+                 ((reinterpret_cast<uintptr_t>(b.queries) & 15) == 0);
+        pg.summary = gr.pl.summary ? 1 : 0;
+        pg.slack = gr.pl.slack;
+        pg.summary_scale = b.summary_scale;
+        pg.item0 = items;
+        pg.qbase = qbase;
+        items += (int64_t)pg.Q * pg.nchunks;
+        qbase += pg.Q;
+        tab[g] = pg;
+    }
+    return items;
+}
+
+// Persistent arm: each group's first stages on the pool streams, then one
+// persistent launch over every group's (query, candidate chunk) items and
+// one launch for every query's top-k, then the scatter to batch order.
+static cudaError_t enqueue_batch_persistent(dtw_index *ix, Slot &sl, const Batch &bt, const BatchLayout &L,
+                                            cudaStream_t s, int64_t items) {
+    const size_t G = bt.groups.size();
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(L.counters, 0, std::max<size_t>(G, 1) * CNT_ALLOC * sizeof(unsigned long long), s)) !=
+        cudaSuccess)
+        return e;
+    if ((e = cudaMemsetAsync(L.pcursor, 0, sizeof(unsigned long long), s)) != cudaSuccess) return e;
+    if ((e = launch_gather(L.staged, L.map, bt.Q, L.grouped, s)) != cudaSuccess) return e;
+    std::vector<char> used(sl.pool.size(), 0);
+    if ((e = cudaEventRecord(sl.fork, s)) != cudaSuccess) return e;
+    for (const auto &gr : bt.groups) used[gr.stream] = 1;
+    for (size_t i = 0; i < sl.pool.size(); ++i)
+        if (used[i] && (e = cudaStreamWaitEvent(sl.pool[i], sl.fork, 0)) != cudaSuccess) return e;
+    int64_t queries = 0;
+    for (size_t g = 0; g < G; ++g) {
+        const GroupRun &gr = bt.groups[g];
+        const Bucket &bk = ix->buckets[gr.bucket];
+        const CascadeBufs b = cascade_bufs(gr.pl, L.ws[g], bk.db, gr.XU, gr.XL, L.grouped + gr.qoff, gr.qn,
+                                           L.gidx + gr.ooff, L.gdist + gr.ooff, L.counters + g * CNT_ALLOC);
+        if ((e = cascade_prefix(gr.pl, L.ws[g], b, gr.PX, gr.xmax, sl.pool[gr.stream])) != cudaSuccess) return e;
+        queries += gr.qn;
+    }
+    for (size_t i = 0; i < sl.pool.size(); ++i) {
+        if (!used[i]) continue;
+        if ((e = cudaEventRecord(sl.join[i], sl.pool[i])) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(s, sl.join[i], 0)) != cudaSuccess) return e;
+    }
+    if ((e = launch_persistent(L.ptab, (int)G, items, queries, ix->p, L.pcursor, s)) != cudaSuccess) return e;
+    return launch_scatter(L.gidx, L.gdist, L.map, bt.Q, bt.k_stride, L.oidx, L.odist, s);
+}
+
 // The device work of one batch, from the staged queries and map to the
 // scattered outputs, enqueued on `s` (and the pool, forked from s).
-static cudaError_t enqueue_batch(dtw_index *ix, Slot &sl, const Batch &bt, const BatchLayout &L, cudaStream_t s) {
+static cudaError_t enqueue_batch(dtw_index *ix, Slot &sl, const Batch &bt, const BatchLayout &L, cudaStream_t s,
+                                 int64_t items) {
+    if (bt.flags & DTW_BATCH_PERSISTENT) return enqueue_batch_persistent(ix, sl, bt, L, s, items);
     const size_t G = bt.groups.size();
     const bool per_query = (bt.flags & DTW_BATCH_PER_QUERY) != 0;
     const bool serial = per_query || (bt.flags & DTW_BATCH_SERIAL) != 0;
@@ -436,8 +570,8 @@ static cudaError_t enqueue_batch(dtw_index *ix, Slot &sl, const Batch &bt, const
     return launch_scatter(L.gidx, L.gdist, L.map, bt.Q, bt.k_stride, L.oidx, L.odist, s);
 }
 
-static std::vector<int64_t> graph_key(const Batch &bt) {
-    std::vector<int64_t> key{bt.Q, bt.k_stride, bt.total, bt.flags, (int64_t)bt.groups.size()};
+static std::vector<int64_t> graph_key(const dtw_index *ix, const Batch &bt) {
+    std::vector<int64_t> key{bt.Q, bt.k_stride, bt.total, bt.flags, (int64_t)bt.groups.size(), ix->persist_chunk};
     for (const auto &gr : bt.groups) {
         key.insert(key.end(),
                    {gr.bucket, gr.w, gr.k, gr.qn, gr.pl.parts, gr.pl.S, gr.pl.seg_len, gr.pl.dtw_path,
@@ -458,6 +592,8 @@ dtw_status run_batch(dtw_index *ix, Slot &sl, Batch &bt, const float *queries, b
     layout_batch(sizing, bt.Q, bt.total, bt.gout, bt.k_stride, bt.groups, per_query);
     if ((st = slot_reserve(sl, sizing.off)) != DTW_OK) return st;
     if ((st = slot_reserve_map(sl, bt.Q)) != DTW_OK) return st;
+    const bool persistent = (bt.flags & DTW_BATCH_PERSISTENT) != 0;
+    if (persistent && (st = slot_reserve_ptab(sl, bt.groups.size())) != DTW_OK) return st;
     Carve cv;
     cv.base = sl.arena;
     const BatchLayout L = layout_batch(cv, bt.Q, bt.total, bt.gout, bt.k_stride, bt.groups, per_query);
@@ -470,18 +606,23 @@ dtw_status run_batch(dtw_index *ix, Slot &sl, Batch &bt, const float *queries, b
         IX_TRY(cudaMemcpyAsync(L.staged, queries, (size_t)bt.total * sizeof(float),
                                q_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
     IX_TRY(cudaMemcpyAsync(L.map, sl.hmap, (size_t)bt.Q * sizeof(QMap), cudaMemcpyHostToDevice, s));
+    int64_t items = 0;
+    if (persistent) {
+        items = fill_ptab(ix, bt, L, sl.hptab);
+        IX_TRY(cudaMemcpyAsync(L.ptab, sl.hptab, bt.groups.size() * sizeof(PersistGroup), cudaMemcpyHostToDevice, s));
+    }
     IX_TRY(cudaEventRecord(sl.hmap_free, s));
 
     const bool use_graph = (bt.flags & DTW_BATCH_GRAPH) != 0 && !per_query;
     if (use_graph) {
-        const std::vector<int64_t> key = graph_key(bt);
+        const std::vector<int64_t> key = graph_key(ix, bt);
         GraphEntry *hit = nullptr;
         for (auto &g : sl.graphs)
             if (g.key == key) hit = &g;
         if (!hit) {
             // capture on the slot's own stream; the graph is launched on s
             IX_TRY(cudaStreamBeginCapture(sl.origin, cudaStreamCaptureModeRelaxed));
-            cudaError_t e = enqueue_batch(ix, sl, bt, L, sl.origin);
+            cudaError_t e = enqueue_batch(ix, sl, bt, L, sl.origin, items);
             cudaGraph_t graph = nullptr;
             cudaError_t e2 = cudaStreamEndCapture(sl.origin, &graph);
             if (e != cudaSuccess || e2 != cudaSuccess) {
@@ -508,7 +649,7 @@ dtw_status run_batch(dtw_index *ix, Slot &sl, Batch &bt, const float *queries, b
         IX_TRY(cudaGraphLaunch(hit->exec, s));
         ++sl.replays;
     } else {
-        cudaError_t e = enqueue_batch(ix, sl, bt, L, s);
+        cudaError_t e = enqueue_batch(ix, sl, bt, L, s, items);
         if (e != cudaSuccess) return ix_fail(DTW_ERR_CUDA, "batch launch: %s", cudaGetErrorString(e));
     }
     if (bt.Q > 0) {
@@ -691,6 +832,54 @@ static dtw_status autotune_batch(dtw_index *ix, const Batch &bt, const float *qu
     return DTW_OK;
 }
 
+// Times the persistent arm on the batch itself for candidate chunk lengths
+// (work items of 512 to 4096 candidates) and keeps the fastest for the index.
+// Outputs go to a scratch area of the arena; synchronous.
+static dtw_status tune_persist_chunk(dtw_index *ix, Batch &bt, const float *queries, bool q_dev, cudaStream_t s) {
+    const int keep = ix->persist_chunk;
+    const int flags = bt.flags;
+    bt.flags &= ~DTW_BATCH_GRAPH;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    IX_TRY(cudaEventCreate(&e0));
+    IX_TRY(cudaEventCreate(&e1));
+    int64_t *oi = nullptr;
+    float *od = nullptr;
+    dtw_status st = DTW_OK;
+    cudaError_t ce = cudaMalloc(&oi, (size_t)bt.Q * bt.k_stride * (sizeof(int64_t) + sizeof(float)));
+    if (ce != cudaSuccess) {
+        cudaGetLastError();
+        st = ix_fail(DTW_ERR_OOM, "persistent tuning outputs: %s", cudaGetErrorString(ce));
+    }
+    od = reinterpret_cast<float *>(oi + bt.Q * bt.k_stride);
+    float best_ms = INFINITY;
+    int best = keep;
+    for (int chunk : {512, 1024, 2048, 4096}) {
+        if (st != DTW_OK) break;
+        ix->persist_chunk = chunk;
+        float ms = INFINITY;
+        for (int rep = 0; rep < 3 && st == DTW_OK; ++rep) {
+            if (cudaEventRecord(e0, s) != cudaSuccess) st = ix_fail(DTW_ERR_CUDA, "event record failed");
+            if (st == DTW_OK) st = run_batch(ix, ix->slot, bt, queries, q_dev, oi, od, true, s, nullptr);
+            if (st == DTW_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess))
+                st = ix_fail(DTW_ERR_CUDA, "persistent tuning: %s", cudaGetErrorString(cudaGetLastError()));
+            float t = 0.0f;
+            if (st == DTW_OK && cudaEventElapsedTime(&t, e0, e1) == cudaSuccess && rep > 0) ms = std::min(ms, t);
+        }
+        if (st == DTW_OK && ms < best_ms) {
+            best_ms = ms;
+            best = chunk;
+        }
+    }
+    cudaStreamSynchronize(s);
+    if (oi) cudaFree(oi);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    bt.flags = flags;
+    ix->persist_chunk = st == DTW_OK ? best : keep;
+    if (st == DTW_OK) ix->persist_tuned = true;
+    return st;
+}
+
 bool ptr_on_device(const void *p) {
     cudaPointerAttributes a;
     cudaError_t e = cudaPointerGetAttributes(&a, p);
@@ -869,7 +1058,8 @@ dtw_status dtw_index_search(dtw_index *ix, const float *queries, int64_t Q, cons
                             dtw_stats *stats, void *stream) {
     set_error_message("");
     if (!ix) return ix_fail(DTW_ERR_INVALID_ARG, "null pointer");
-    if (flags & ~(DTW_BATCH_GRAPH | DTW_BATCH_AUTOTUNE | DTW_BATCH_SERIAL | DTW_BATCH_PER_QUERY))
+    if (flags & ~(DTW_BATCH_GRAPH | DTW_BATCH_AUTOTUNE | DTW_BATCH_SERIAL | DTW_BATCH_PER_QUERY |
+                  DTW_BATCH_PERSISTENT))
         return ix_fail(DTW_ERR_INVALID_ARG, "flags=0x%x has unknown bits", flags);
     std::lock_guard<std::mutex> lk(ix->mu);
     DeviceGuard dg(ix->device);
@@ -888,6 +1078,11 @@ dtw_status dtw_index_search(dtw_index *ix, const float *queries, int64_t Q, cons
         Batch again;
         if ((st = prepare_batch(ix, Q, q_len, q_w, q_k, k_stride, flags, again)) != DTW_OK) return st;
         bt = std::move(again);
+        if ((flags & DTW_BATCH_PERSISTENT) && !ix->persist_tuned) {
+            if ((st = tune_persist_chunk(ix, bt, queries, q_dev, s)) != DTW_OK) return st;
+            if ((st = prepare_batch(ix, Q, q_len, q_w, q_k, k_stride, flags, again)) != DTW_OK) return st;
+            bt = std::move(again);
+        }
     }
     std::vector<unsigned long long> h;
     if (stats) h.assign(bt.groups.size() * CNT_ALLOC, 0);

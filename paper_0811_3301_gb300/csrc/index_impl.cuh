@@ -7,6 +7,7 @@
 #include <map>
 
 #include "cascade_host.cuh"
+#include "persist.cuh"
 
 namespace dtwk {
 
@@ -32,6 +33,8 @@ struct Slot {
     size_t arena_cap = 0;
     QMap *hmap = nullptr;  // pinned host copy of the map
     size_t hmap_cap = 0;
+    PersistGroup *hptab = nullptr;  // pinned host copy of the persistent group table
+    size_t hptab_cap = 0;
     cudaEvent_t hmap_free = nullptr;  // the map's last host-to-device copy has completed
     cudaEvent_t done = nullptr;       // the slot's last batch has completed
     cudaStream_t origin = nullptr;    // capture stream
@@ -107,6 +110,8 @@ struct BatchLayout {
     QMap *map;
     int64_t *gidx, *oidx;
     unsigned long long *counters;
+    PersistGroup *ptab;          // the persistent arm's group table (device)
+    unsigned long long *pcursor; // its work-item cursor
     std::vector<CascadeWs> ws;
 };
 
@@ -124,6 +129,8 @@ struct dtw_index {
     std::vector<dtwk::Bucket> buckets;
     std::map<dtwk::TuneKey, dtwk::Tuning> tuned;
     dtwk::Slot slot;  // used by dtw_index_search
+    int persist_chunk = 2048;  // candidates per work item of the persistent arm
+    bool persist_tuned = false;
     std::mutex mu;
 };
 

@@ -96,19 +96,21 @@ def reference(api, dbs, batch):
     return per_group_reference(api, dbs, lens, qs, ws, ks, 5)
 
 
-@pytest.mark.parametrize("mode", ["concurrent", "serial", "per_query", "graph"])
+@pytest.mark.parametrize("mode", ["concurrent", "serial", "per_query", "graph", "persistent", "persistent_graph"])
 def test_batched_equals_knn_search_per_group(api, index, batch, reference, mode):
     lens, qs, ws, ks = batch
-    kw = {"serial": mode == "serial", "per_query": mode == "per_query", "graph": mode == "graph"}
+    kw = {"serial": mode == "serial", "per_query": mode == "per_query", "graph": mode in ("graph", "persistent_graph"),
+          "persistent": mode.startswith("persistent")}
     gi, gd = index.search_flat(cuda(flat_of(qs)), lens, ws, ks, **kw)
     ri, rd = reference
     np.testing.assert_array_equal(gi.cpu().numpy(), ri)
     np.testing.assert_array_equal(gd.cpu().numpy(), rd)
 
 
-def test_batched_matches_oracle_on_a_subset(index, dbs, batch):
+@pytest.mark.parametrize("persistent", [False, True])
+def test_batched_matches_oracle_on_a_subset(index, dbs, batch, persistent):
     lens, qs, ws, ks = batch
-    gi, gd = index.search_flat(cuda(flat_of(qs)), lens, ws, ks)
+    gi, gd = index.search_flat(cuda(flat_of(qs)), lens, ws, ks, persistent=persistent)
     gi, gd = gi.cpu().numpy(), gd.cpu().numpy().astype(np.float64)
     for i in range(0, len(lens), 6):  # 15 queries across all buckets
         n, w, k = int(lens[i]), int(ws[i]), int(ks[i])
@@ -201,3 +203,40 @@ def test_bucket_smaller_than_k_pads_the_tail(api):
 def test_empty_batch(index):
     gi, gd = index.search_flat(cuda(np.zeros(0, np.float32)), np.zeros(0, np.int64), 1, 1)
     assert gi.shape == (0, 1)
+
+
+def test_persistent_arm_tuned_and_replayed(api, dbs, batch, reference):
+    # the persistent launch over every group's (query, chunk) items, with its
+    # chunk length autotuned on the batch, captured as a graph and replayed
+    # with new query values; stats count every pair once
+    lens, qs, ws, ks = batch
+    with api.DtwIndex(P) as ix:
+        for n in BUCKETS:
+            ix.add_bucket(cuda(dbs[n]))
+        gi, gd = ix.search_flat(cuda(flat_of(qs)), lens, ws, ks, persistent=True, autotune=True, graph=True)
+        np.testing.assert_array_equal(gi.cpu().numpy(), reference[0])
+        np.testing.assert_array_equal(gd.cpu().numpy(), reference[1])
+        qs2 = synth.mixed_queries(lens, seed=13)
+        ref2 = per_group_reference(api, dbs, lens, qs2, ws, ks, 5)
+        for _ in range(2):
+            gi, gd = ix.search_flat(cuda(flat_of(qs2)), lens, ws, ks, persistent=True, graph=True)
+            np.testing.assert_array_equal(gi.cpu().numpy(), ref2[0])
+            np.testing.assert_array_equal(gd.cpu().numpy(), ref2[1])
+        assert ix.info()["graph_replays"] >= 2
+        _, _, st = ix.search_flat(cuda(flat_of(qs2)), lens, ws, ks, persistent=True, return_stats=True)
+        pruned = st["pruned_summary"] + st["pruned_keogh"] + st["pruned_improved"]
+        assert st["seeds"] + pruned + st["dtw_computed"] == st["candidates"] == len(lens) * NB
+
+
+def test_persistent_arm_rejects_what_it_does_not_serve(api, index, batch):
+    lens, qs, ws, ks = batch
+    with pytest.raises(api.DtwError) as e:
+        index.search_flat(cuda(flat_of(qs)), lens, ws, ks, persistent=True, serial=True)
+    assert e.value.status == 1
+    with api.DtwIndex(P) as ix:  # band 2 * 300 + 1 = 601 > 512
+        ix.add_bucket(cuda(synth.random_walks(50, 400, seed=4)))
+        q = synth.random_walks(1, 400, seed=3, stream=synth.STREAM_QUERY).reshape(-1)
+        with pytest.raises(api.DtwError) as e:
+            ix.search_flat(cuda(q), [400], 300, 1, persistent=True)
+        assert e.value.status == 1
+        ix.search_flat(cuda(q), [400], 255, 1, persistent=True)  # band 511 is served
