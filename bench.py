@@ -69,6 +69,8 @@ def parse():
                     "3 main stage on two 16-lane groups per warp")
     ap.add_argument("--filter-path", type=int, default=0,
                     help="LB_Keogh/LB_Improved filter kernel: 0 auto, 1 one warp per pair, 2 batches of eight pairs")
+    ap.add_argument("--lb-abandon", type=int, default=0,
+                    help="1: early abandoning inside the LB sums (streamed rows of series longer than 256)")
     ap.add_argument("--no-p2", action="store_true", help="skip the DTW_2 side measurement")
     ap.add_argument("--no-extra", action="store_true",
                     help="default workload only: skip the bounded batched and serving runs added to its line")
@@ -378,7 +380,8 @@ def run_ours(a):
             dist.barrier()
             torch.cuda.synchronize()
 
-    kw = {"seeds": a.seeds, "parts": a.parts, "dtw_path": a.dtw_path, "filter_path": a.filter_path}
+    kw = {"seeds": a.seeds, "parts": a.parts, "dtw_path": a.dtw_path, "filter_path": a.filter_path,
+          "lb_abandon": a.lb_abandon}
 
     def step(p):
         return api.knn_search(db, qs, a.w, p, a.k, **kw)

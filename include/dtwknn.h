@@ -96,6 +96,10 @@ typedef struct {
                             pairs per warp for series of 128 or 256 elements with the
                             piecewise-sum pre-filter, else one warp per pair), 1 one warp
                             per pair, 2 batches where they apply */
+    int32_t lb_abandon;  /* 1: stop summing a pair's LB_Keogh / LB_Improved once the partial
+                            sums (tested every 256 indices) exceed the threshold, on series
+                            longer than 256 whose rows are streamed; 0 or -1: never.  The
+                            result is the same either way */
 } dtw_options;
 
 /*

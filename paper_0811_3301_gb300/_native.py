@@ -70,7 +70,8 @@ class Profile(ctypes.Structure):
 
 class Options(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("slack", ctypes.c_float), ("seeds", ctypes.c_int32),
-                ("parts", ctypes.c_int32), ("dtw_path", ctypes.c_int32), ("filter_path", ctypes.c_int32)]
+                ("parts", ctypes.c_int32), ("dtw_path", ctypes.c_int32), ("filter_path", ctypes.c_int32),
+                ("lb_abandon", ctypes.c_int32)]
 
 
 class Tuning(ctypes.Structure):

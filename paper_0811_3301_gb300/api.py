@@ -151,6 +151,7 @@ def dtw_triangle(x: torch.Tensor, y: torch.Tensor, z: torch.Tensor, w: int, p: i
 
 def knn_search(db: torch.Tensor, queries: torch.Tensor, w: int, p: int, k: int = 1, *, mode: str = "improved",
                slack: float = 1e-6, seeds: int = 0, parts: int = 0, dtw_path: int = 0, filter_path: int = 0,
+               lb_abandon: int = 0,
                out_idx: torch.Tensor | None = None,
                out_dist: torch.Tensor | None = None, return_stats: bool = False):
     """Exact k nearest neighbours of each query row under DTW_p with band w (Sec. 7-8).
@@ -175,7 +176,8 @@ def knn_search(db: torch.Tensor, queries: torch.Tensor, w: int, p: int, k: int =
         out_dist = torch.empty((Q, k), dtype=torch.float32, device=dev, pin_memory=not queries.is_cuda and torch.cuda.is_available())
     if mode not in _MODES:
         raise ValueError("mode must be one of %s" % sorted(_MODES))
-    opt = N.Options(_MODES[mode], float(slack), int(seeds), int(parts), int(dtw_path), int(filter_path))
+    opt = N.Options(_MODES[mode], float(slack), int(seeds), int(parts), int(dtw_path), int(filter_path),
+                    int(lb_abandon))
     st = N.Stats()
     N.check(N.lib.knn_search_ex(_ptr(db), db.shape[0], _ptr(queries), Q, n, int(w), int(p), int(k),
                                 ctypes.byref(opt), _ptr(out_idx), _ptr(out_dist),

@@ -150,6 +150,7 @@ CascadePlan make_plan(int64_t N, int64_t Qmax, int n, int w, int p, int k, const
     // (2048 keeps enough CTAs on smaller ones), 1024 for longer series
     pl.seg_len = seg_len > 0 ? seg_len : (n <= 256 ? (N >= 65536 ? 4096 : 2048) : 1024);
     pl.dtw_path = o.dtw_path;
+    pl.lb_abandon = o.lb_abandon > 0 ? 1 : 0;
     // The DTW stage takes every query's lowest-bound pairs first (a multiple
     // of 32, at least 2k), so that each query's threshold falls to near its
     // final value early and its remaining pairs are skipped or abandoned
@@ -267,6 +268,7 @@ CascadeBufs cascade_bufs(const CascadePlan &pl, const CascadeWs &l, const float 
     b.seg_per_cta = pl.seg_per_cta;
     b.filter_warps = pl.filter_warps;
     b.filter_path = pl.filter_path;
+    b.lb_abandon = pl.lb_abandon;
     b.dev_err = reinterpret_cast<unsigned *>(counters + CNT_ERR);
     b.nseg = N > 0 ? pl.nseg : 0;
     b.seg_start = l.seg_start;

@@ -40,6 +40,7 @@ struct CascadePlan {
     int seg_per_cta; // filter segments per CTA
     int dtw_path;    // 0 auto, 1 thread per pair, 2 warp per pair (main DTW stage)
     int filter_path; // 1 one warp per pair, 2 batches of eight pairs per warp
+    int lb_abandon;  // early abandoning inside the bound sums (streamed long rows)
     int order_first; // pairs per query the DTW stage takes first, by ascending bound (0: filter order)
 };
 

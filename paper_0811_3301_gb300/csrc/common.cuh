@@ -93,6 +93,9 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
+// Indices between the partial-sum tests of the filter's early abandoning.
+constexpr int kLbAbandonSpan = 256;
+
 // Pairs per warp whose bound sums are reduced together (warp_sum16_transposed).
 constexpr int kLbiBatch = 8;
 
@@ -248,6 +251,7 @@ struct CascadeBufs {
     int seg_per_cta;      // consecutive segments one filter CTA handles
     int filter_warps;     // warps per filter CTA (one sub-segment each)
     int filter_path;      // 1 one warp per pair, 2 batches of eight pairs per warp (resolved by the plan)
+    int lb_abandon;       // streamed long rows: stop a pair's sums once their partial values exceed thr
     unsigned *dev_err;    // a kernel's bounded wait that gave up records its dtw_status here (0: none)
     int32_t *seg_start;   // [Q][nseg]
     int32_t *seg_count;   // [Q][nseg]

@@ -920,7 +920,7 @@ dtw_status dtw_index_create(int32_t p, const dtw_options *opt, dtw_index **out) 
     if (!out) return ix_fail(DTW_ERR_INVALID_ARG, "null pointer");
     *out = nullptr;
     if (p != 1 && p != 2) return ix_fail(DTW_ERR_INVALID_ARG, "p=%d must be 1 or 2", p);
-    dtw_options o{DTW_MODE_IMPROVED, 1e-6f, 0, 0, 0, 0};
+    dtw_options o{DTW_MODE_IMPROVED, 1e-6f, 0, 0, 0, 0, 0};
     if (opt) o = *opt;
     if (o.mode < DTW_MODE_IMPROVED || o.mode > DTW_MODE_NOPRUNE)
         return ix_fail(DTW_ERR_INVALID_ARG, "mode=%d unknown", o.mode);

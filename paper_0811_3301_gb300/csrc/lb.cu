@@ -533,10 +533,58 @@ __device__ __forceinline__ float warp_lbi_env(const CascadeBufs &b, int q, int c
             const float *x = b.db + oc, *xu = b.XU + oc, *xl = b.XL + oc;
             const float *U = b.U + oq, *L = b.L + oq, *y = b.queries + oq, *ul = b.UL + oq, *lu = b.LU + oq;
             float a1 = 0.0f, a2 = 0.0f;
+            if (b.lb_abandon) {
+                // Early abandoning inside the sums (the remark on abandoning
+                // the bound sums in the experiments of Sec. 10): every
+                // kLbAbandonSpan indices the partial sums, which only grow,
+                // are compared with thr.  Above it, LB_Keogh decides at once;
+                // if only LB_Keogh + the second sum is, the pair fails
+                // LB_Improved whatever the rest, and only LB_Keogh is
+                // completed (three of the eight rows) to tell which bound
+                // discarded it.
+                int base = 0;
+                bool lbi_out = false;
+                for (; base < n; base += 128) {
+                    const int i = base + 4 * lane;
+                    if (i < n) {
+                        a1 = acc_dist4<P>(a1, ldg4(x + i), ldg4(L + i), ldg4(U + i));
+                        a2 = acc_dist4<P>(a2, ldg4(y + i), min4(ldg4(xl + i), ldg4(lu + i)),
+                                          max4(ldg4(xu + i), ldg4(ul + i)));
+                    }
+                    if ((base + 128) % kLbAbandonSpan == 0 && base + 128 < n) {
+                        float s1 = a1, s12 = a1 + a2;
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) {
+                            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+                            s12 += __shfl_xor_sync(0xffffffffu, s12, o);
+                        }
+                        if (s1 > thr) {
+                            *lbk = s1;
+                            return s1;
+                        }
+                        if (s12 > thr) {
+                            lbi_out = true;
+                            base += 128;
+                            break;
+                        }
+                    }
+                }
+                if (lbi_out) {
+                    for (; base < n; base += 128) {
+                        const int i = base + 4 * lane;
+                        if (i < n) a1 = acc_dist4<P>(a1, ldg4(x + i), ldg4(L + i), ldg4(U + i));
+                    }
+                    const float s1 = warp_sum(a1);
+                    *lbk = s1;
+                    return s1 > thr ? s1 : kInf;  // LB_Improved > thr either way
+                }
+            } else {
 #pragma unroll 2
-            for (int i = 4 * lane; i < n; i += 128) {
-                a1 = acc_dist4<P>(a1, ldg4(x + i), ldg4(L + i), ldg4(U + i));
-                a2 = acc_dist4<P>(a2, ldg4(y + i), min4(ldg4(xl + i), ldg4(lu + i)), max4(ldg4(xu + i), ldg4(ul + i)));
+                for (int i = 4 * lane; i < n; i += 128) {
+                    a1 = acc_dist4<P>(a1, ldg4(x + i), ldg4(L + i), ldg4(U + i));
+                    a2 = acc_dist4<P>(a2, ldg4(y + i), min4(ldg4(xl + i), ldg4(lu + i)),
+                                      max4(ldg4(xu + i), ldg4(ul + i)));
+                }
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {

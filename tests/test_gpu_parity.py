@@ -436,3 +436,20 @@ def test_filter_paths_agree(api, p, n, w):
             assert torch.equal(out[path, k][0], out[1, k][0]) and torch.equal(out[path, k][1], out[1, k][1])
     ri, rd, _ = oracle.knn_cascade(db, qs[:12], w, p, 7, mode=1, threads=8)
     assert_knn(db, qs[:12], w, p, 7, out[2, 7][0][:12], out[2, 7][1][:12], ri, rd)
+
+
+@pytest.mark.parametrize("p", [1, 2])
+@pytest.mark.parametrize("n,w,k", [(1024, 102, 1), (600, 60, 5), (1002, 204, 1)])
+def test_lb_early_abandon_same_result(api, p, n, w, k):
+    # early abandoning inside the bound sums (streamed long rows) changes
+    # which work is done, not the neighbours; the counters still add up
+    db = synth.shapes(3_000, n, seed=80 + n)
+    qs = synth.shapes(12, n, seed=81 + n, stream=synth.STREAM_QUERY)
+    ri, rd, r_st = api.knn_search(cuda(db), cuda(qs), w, p, k, return_stats=True)
+    ai, ad, a_st = api.knn_search(cuda(db), cuda(qs), w, p, k, lb_abandon=1, return_stats=True)
+    assert torch.equal(ai, ri) and torch.equal(ad, rd)
+    for st in (r_st, a_st):
+        pruned = st["pruned_summary"] + st["pruned_keogh"] + st["pruned_improved"]
+        assert st["seeds"] + pruned + st["dtw_computed"] == st["candidates"]
+    oi, od, _ = oracle.knn_cascade(db, qs[:4], w, p, k, mode=1, threads=8)
+    assert_knn(db, qs[:4], w, p, k, ai[:4], ad[:4], oi, od)
