@@ -88,6 +88,8 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="serve: arrival window per rate")
     ap.add_argument("--serve-scale", type=float, default=1.0,
                     help="serve: database size factor (1.0: 1,000,000 x 256 + 200,000 x 1024)")
+    ap.add_argument("--serve-no-tune", action="store_true",
+                    help="serve: skip tuning each (n, w, k) of the index on sample queries before serving")
     ap.add_argument("--serve-secondary", action="store_true",
                     help="serve: also run with small buckets for lengths 128, 512 and 2048")
     ap.add_argument("--classify-dbs", type=int, default=50, help="classify: databases per instance count")
@@ -544,6 +546,7 @@ def extra_workloads(a):
                   "plain": {k: x["plain"][k] for k in ("throughput_qps", "p50_ms", "p99_ms", "succeeded", "failed",
                                                        "all_ok")}}
                  for x in r["runs"]],
+        "capacity": r["capacity"],
         "wall_s": time.time() - t0}
     torch.cuda.empty_cache()
     return out
@@ -730,6 +733,44 @@ def latency_summary(comp):
     return out
 
 
+def bucket_capacity(api, N, ix, lengths, seed, count=256):
+    """Throughput of each (bucket, k) alone through the index (one batch of
+    `count` queries, no graph), with the device time of each cascade stage
+    per query, and the capacity of the serving mix (lengths and k = 1 / 10
+    in equal shares) that these rates allow."""
+    import torch
+
+    out = {}
+    inv = []
+    for n in lengths:
+        qs = synth.random_walks(count, n, seed=seed + 7000 + n, stream=synth.STREAM_QUERY)
+        flat = torch.from_numpy(np.ascontiguousarray(qs.reshape(-1))).cuda()
+        lens = np.full(count, n)
+        for k in (1, 10):
+            ix.search_flat(flat, lens, n // 10, k)
+            torch.cuda.synchronize()
+            N.profile_read(reset=True)
+            N.profile_enable(True)
+            t0 = time.perf_counter()
+            reps = 3
+            for _ in range(reps):
+                ix.search_flat(flat, lens, n // 10, k)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            N.profile_enable(False)
+            prof = N.profile_read(reset=True)
+            qps = count * reps / dt
+            per_q = {st: round(v["ms"] / (count * reps) * 1e3, 3) for st, v in prof.items() if v["launches"]}
+            tot = sum(per_q.values())
+            out["n%d_k%d" % (n, k)] = {"qps": qps, "stage_us_per_query": per_q,
+                                       "dominant_stage": max(per_q, key=per_q.get) if per_q else None,
+                                       "dominant_share": (max(per_q.values()) / tot) if tot else None}
+            inv.append(1.0 / qps)
+    return {"buckets": out, "mix_capacity_qps": len(inv) / sum(inv),
+            "note": "each (length, k) alone, %d queries per batch; the mix capacity is the harmonic mean over the "
+                    "equally likely (length, k) combinations" % count}
+
+
 def run_serve(a):
     """Poisson arrivals of single k-NN queries (DTW_1, half 1-NN and half
     10-NN, w = floor(n/10)) against a resident database of 1,000,000 random
@@ -744,6 +785,8 @@ def run_serve(a):
     build.build()
     from paper_0811_3301_gb300 import api
 
+    from paper_0811_3301_gb300 import _native as N
+
     dev = torch.device("cuda", torch.cuda.current_device())
     sizes = {256: int(1_000_000 * a.serve_scale), 1024: int(200_000 * a.serve_scale)}
     lengths = [256, 1024]
@@ -755,6 +798,17 @@ def run_serve(a):
     for n in sorted(sizes):
         ix.add_bucket(torch.from_numpy(synth.random_walks(sizes[n], n, seed=a.seed + 5000 + n)).to(dev))
     torch.cuda.synchronize()
+    # the index's parameters for each (n, w, k) the stream will ask for, timed
+    # on sample queries of that length (the server uses the index's tuning)
+    tuning = {}
+    t0 = time.perf_counter()
+    if not a.serve_no_tune:
+        for n in lengths:
+            sample = torch.from_numpy(synth.random_walks(256, n, seed=a.seed + 9000 + n,
+                                                         stream=synth.STREAM_QUERY)).to(dev)
+            for k in (1, 10):
+                tuning["n%d_k%d" % (n, k)] = ix.tune(sample, n // 10, k)
+    tune_s = time.perf_counter() - t0
     sampler = ClockSampler(0)
     t_wall0 = time.time()
     runs = []
@@ -780,6 +834,7 @@ def run_serve(a):
     t_wall1 = time.time()
     clocks = sampler.summary(t_wall0, t_wall1)
     sampler.stop()
+    capacity = bucket_capacity(api, N, ix, lengths, a.seed)
     best = max(runs, key=lambda r: r["batched"]["throughput_qps"])
     return {
         "metric": "exact k-NN DTW queries/s and p50/p99/p99.9 latency, Poisson arrivals, continuous batching",
@@ -792,7 +847,8 @@ def run_serve(a):
                                "w = floor(n/10), DTW_1, 1-NN/10-NN mixed 50/50"
                                % (a.serve_rates, lengths, {int(k): v for k, v in sizes.items()}),
                    "server": {"slots": 4, "max_batch": 512, "slot_bytes": 8 << 30}},
-        "runs": runs, "index": ix.info(), "clocks": clocks,
+        "runs": runs, "capacity": capacity, "tuning": tuning, "tune_seconds": tune_s, "index": ix.info(),
+        "clocks": clocks,
     }
 
 
