@@ -66,7 +66,7 @@ def parse():
     ap.add_argument("--seeds", type=int, default=0, help="seed DTWs per query (0: library default)")
     ap.add_argument("--parts", type=int, default=0, help="piecewise-sum parts (0: default n/8, -1: off)")
     ap.add_argument("--dtw-path", type=int, default=0, help="DTW kernel: 0 auto, 1 thread per pair, 2 warp per pair, "
-                    "3 main stage on two 16-lane groups per warp")
+                    "3 main stage on two 16-lane groups per warp, 4 thread per pair in row phases of 64 rows")
     ap.add_argument("--filter-path", type=int, default=0,
                     help="LB_Keogh/LB_Improved filter kernel: 0 auto, 1 one warp per pair, 2 batches of eight pairs")
     ap.add_argument("--lb-abandon", type=int, default=0,
@@ -329,6 +329,8 @@ def roofline(prof, a, steps, peaks, stats):
         band = 2 * min(a.w, a.n - 1) + 1
         lanes = a.dtw_path == 2 or (a.dtw_path == 0 and band > 208)
         name = "k_dtw_lanes" if lanes else ("k_dtw_reg4" if band <= 64 else "k_dtw_reg")
+        if name == "k_dtw_reg4" and dom == "dtw" and per_call > 1:
+            name = "k_dtw_reg4p"  # the main stage in row phases, one launch per phase
         return dict(base, kernel=name, achieved=achieved, frac=(achieved / alu_peak) if achieved else None,
                     cells_per_launch=cells,
                     instruction_mix={"ops_per_cell": 3, "Top_s": (achieved * 3 / DTW_CELL_OPS) if achieved else None})

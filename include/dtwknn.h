@@ -91,7 +91,11 @@ typedef struct {
     int32_t dtw_path; /* DTW kernel of the cascade's DTW stages: 0 chooses (one warp per
                          pair for long series or wide bands, else one thread per pair),
                          1 one thread per pair where the band fits, 2 one warp per pair,
-                         3 one warp per two pairs (16-lane groups) where the band allows */
+                         3 one warp per two pairs (16-lane groups) where the band allows,
+                         4 one thread per pair in launches of 64 rows (pairs still alive
+                         at a launch's last row are resumed by the next one), where the
+                         band fits 64 register slots and n > 128; 0 uses 4 for runs of
+                         at least 2^24 (query, candidate) pairs */
     int32_t filter_path; /* LB_Keogh / LB_Improved filter kernel: 0 chooses (batches of eight
                             pairs per warp for series of 128 or 256 elements with the
                             piecewise-sum pre-filter, else one warp per pair), 1 one warp
@@ -219,8 +223,9 @@ enum {
     DTW_NUM_STAGES = 10
 };
 typedef struct {
-    double ms[DTW_NUM_STAGES];
-    int64_t launches[DTW_NUM_STAGES];
+    double ms[DTW_NUM_STAGES];        /* device time of each stage, summed over its runs */
+    int64_t launches[DTW_NUM_STAGES]; /* kernels each stage launched (the DTW stage in row
+                                         phases: one per phase) */
 } dtw_profile;
 
 dtw_status dtw_profile_enable(int32_t on);

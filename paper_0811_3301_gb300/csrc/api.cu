@@ -364,7 +364,7 @@ dtw_status knn_search_ex(const float *db, int64_t N, const float *queries, int64
         return fail(DTW_ERR_INVALID_ARG, "mode=%d unknown", o.mode);
     if (!(o.slack >= 0.0f) || std::isinf(o.slack)) return fail(DTW_ERR_INVALID_ARG, "slack must be finite and >= 0");
     if (o.seeds < 0) return fail(DTW_ERR_INVALID_ARG, "seeds=%d must be >= 0", o.seeds);
-    if (o.dtw_path < 0 || o.dtw_path > 3) return fail(DTW_ERR_INVALID_ARG, "dtw_path=%d outside [0, 3]", o.dtw_path);
+    if (o.dtw_path < 0 || o.dtw_path > 4) return fail(DTW_ERR_INVALID_ARG, "dtw_path=%d outside [0, 4]", o.dtw_path);
     if (o.filter_path < 0 || o.filter_path > 2)
         return fail(DTW_ERR_INVALID_ARG, "filter_path=%d outside [0, 2]", o.filter_path);
     if (stats) memset(stats, 0, sizeof(*stats));

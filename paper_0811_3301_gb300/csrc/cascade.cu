@@ -255,16 +255,18 @@ __device__ int32_t block_scan_counts(const int32_t *__restrict__ cnt, int32_t *_
 
 __global__ void __launch_bounds__(1024) k_qscan(const int32_t *__restrict__ cnt, int32_t *__restrict__ start,
                                                 int32_t *__restrict__ start_b, int Q, int first,
-                                                unsigned long long *total) {
+                                                unsigned long long *total, unsigned long long *lead_total) {
     if (first <= 0) {
         const int32_t all = block_scan_counts(cnt, start, Q, 0, [](int32_t c) { return c; });
         if (threadIdx.x == 0 && total) *total = (unsigned long long)all;
+        if (threadIdx.x == 0 && lead_total) *lead_total = 0;
         return;
     }
     const int32_t lead = block_scan_counts(cnt, start, Q, 0, [first](int32_t c) { return c < first ? c : first; });
     const int32_t all =
         block_scan_counts(cnt, start_b, Q, lead, [first](int32_t c) { return c > first ? c - first : 0; });
     if (threadIdx.x == 0 && total) *total = (unsigned long long)all;
+    if (threadIdx.x == 0 && lead_total) *lead_total = (unsigned long long)lead;
 }
 
 __device__ __forceinline__ int order_bin(float bound, float scale) {
@@ -357,7 +359,7 @@ __global__ void __launch_bounds__(256) k_gather(CascadeBufs b) {
 cudaError_t launch_group_by_query(const CascadeBufs &b, cudaStream_t s) {
     if (b.Q <= 0 || b.nseg <= 0) return cudaSuccess;
     static_assert(kOrderBins == 256, "k_gather scans the histogram with one thread per bin");
-    k_qscan<<<1, 1024, 0, s>>>(b.qcount, b.qstart, b.qstart_b, b.Q, b.order_first, b.pair_total);
+    k_qscan<<<1, 1024, 0, s>>>(b.qcount, b.qstart, b.qstart_b, b.Q, b.order_first, b.pair_total, b.lead_total);
     k_gather<<<b.Q, 256, 0, s>>>(b);
     return cudaGetLastError();
 }

@@ -21,6 +21,7 @@ static std::mutex g_prof_mu;
 struct StageEvents {
     int stage;
     cudaEvent_t a, b;
+    int kernels;  // kernels the stage launched between the two events
 };
 static std::vector<StageEvents> g_prof_events;
 
@@ -36,7 +37,7 @@ cudaError_t profile_collect(double *ms, int64_t *launches, bool reset) {
         if (e != cudaSuccess) return e;
         if (ev.stage >= 0 && ev.stage < DTW_NUM_STAGES) {
             ms[ev.stage] += t;
-            launches[ev.stage] += 1;
+            launches[ev.stage] += ev.kernels;
         }
     }
     if (reset) {
@@ -69,6 +70,7 @@ struct StageTimer {
             return;
         }
         ev.stage = stage;
+        ev.kernels = 1;
         if (cudaEventCreate(&ev.a) != cudaSuccess || cudaEventCreate(&ev.b) != cudaSuccess) {
             cudaGetLastError();
             return;
@@ -106,6 +108,7 @@ static cudaError_t launch_dtw_any(const DtwJob &j, const DtwGeom &g, cudaStream_
 static int use_lanes(const CascadePlan &pl, int64_t npairs, bool main_stage) {
     if (dtw_lanes_cl(pl.n, pl.we) == 0) return 0;
     if (pl.dtw_path == 3) return main_stage ? 2 : 1;
+    if (pl.dtw_path >= 4) return main_stage ? 0 : ((pl.n >= 512 && npairs < ((int64_t)1 << 17)) ? 1 : 0);
     if (pl.dtw_path == 2) return 1;
     if (pl.dtw_path == 1) return 0;
     if (main_stage) return 0;
@@ -145,11 +148,23 @@ CascadePlan make_plan(int64_t N, int64_t Qmax, int n, int w, int p, int k, const
     if (Qc > Qmax) Qc = Qmax;
     if (Qc < 1) Qc = 1;
     pl.Qc = Qc;
+    // continuation lists of the row phases: pairs still alive at a phase's
+    // end; a pair that finds its list full runs on in place
+    pl.cont_cap = N > 0 ? std::min<int64_t>(Qc * N, Qc * 2048) : 0;
     // filter segments: longer ones amortise more of a CTA's setup; for series
     // up to 256 (chunks in registers) 4096 measured fastest on large databases
     // (2048 keeps enough CTAs on smaller ones), 1024 for longer series
     pl.seg_len = seg_len > 0 ? seg_len : (n <= 256 ? (N >= 65536 ? 4096 : 2048) : 1024);
     pl.dtw_path = o.dtw_path;
+    // The main DTW stage in row phases of 64 rows (k_dtw_reg4p): bands of up
+    // to 64 register slots, series longer than two phases; asked for
+    // (dtw_path 4) or, by default, for runs of at least 2^24 pairs, where the
+    // stage is long enough for the phases' state traffic and extra launches
+    // to pay (100,000 x 256, 1,000 queries: DTW stage 1.44 -> 1.37 ms).
+    const bool phase_ok = !pl.g.wide && pl.g.C <= kDtwGroupMaxC && n > 2 * kDtwPhaseRows &&
+                          pl.mode != DTW_MODE_NOPRUNE && N > 0;
+    const bool phase_big = o.dtw_path == 0 && Qc * N >= ((int64_t)1 << 24);
+    pl.dtw_phase = (phase_ok && (o.dtw_path == 4 || phase_big)) ? kDtwPhaseRows : 0;
     pl.lb_abandon = o.lb_abandon > 0 ? 1 : 0;
     // The DTW stage takes every query's lowest-bound pairs first (a multiple
     // of 32, at least 2k), so that each query's threshold falls to near its
@@ -204,7 +219,11 @@ CascadeWs carve_ws(const CascadePlan &pl, Carve &cv) {
     l.pair_res = cv.take<float>((size_t)Qc * Nc);
     l.seg_start = cv.take<int32_t>((size_t)Qc * pl.nseg);
     l.seg_count = cv.take<int32_t>((size_t)Qc * pl.nseg);
-    l.misc = cv.take<unsigned long long>(8);
+    l.misc = cv.take<unsigned long long>(16);
+    for (int h = 0; h < 2; ++h) {
+        l.cont_state[h] = pl.dtw_phase > 0 ? cv.take<float>((size_t)pl.cont_cap * (pl.g.C + 1)) : nullptr;
+        l.cont_pi[h] = pl.dtw_phase > 0 ? cv.take<int64_t>((size_t)pl.cont_cap) : nullptr;
+    }
     return l;
 }
 
@@ -256,6 +275,7 @@ CascadeBufs cascade_bufs(const CascadePlan &pl, const CascadeWs &l, const float 
     b.qstart_b = l.qstart_b;
     b.order_first = pl.order_first;
     b.pair_total = l.misc + 4;
+    b.lead_total = l.misc + 8;
     b.lbi_inline = pl.mode == DTW_MODE_IMPROVED ? 1 : 0;
     b.summary = pl.summary ? 1 : 0;
     b.summary_scale = (pl.summary && pl.p == 2) ? (float)pl.pg.smax : 1.0f;
@@ -313,7 +333,7 @@ cudaError_t cascade_prefix(const CascadePlan &pl, const CascadeWs &l, const Casc
     if (plan_needs_db_envelope(pl) && (b.XU == nullptr || b.XL == nullptr)) return cudaErrorInvalidValue;
     const int n = pl.n, p = pl.p, qn = b.Q;
     const int64_t N = pl.N;
-    RUN_TRY(cudaMemsetAsync(l.misc, 0, 8 * sizeof(unsigned long long), s));
+    RUN_TRY(cudaMemsetAsync(l.misc, 0, 16 * sizeof(unsigned long long), s));
     {
         StageTimer tm(DTW_STAGE_ENVELOPE, s);
         RUN_TRY(launch_envelope(b.queries, qn, n, pl.we, l.U, l.L, b.qc, pl.g.padl, s, l.UL, l.LU));
@@ -375,7 +395,33 @@ cudaError_t cascade_run(const CascadePlan &pl, const CascadeWs &l, const float *
         jp.tL = jp.abandon ? l.L : nullptr;
         {
             StageTimer tm(DTW_STAGE_DTW, s);
-            RUN_TRY(launch_dtw_any(jp, pl.g, s));
+            if (pl.dtw_phase > 0 && !jp.lanes) {
+                // row phases: every listed pair's first rows (the leading
+                // region's pairs to the end), then the deferred pairs from
+                // one list to the other, a phase per launch
+                unsigned long long *cnt[2] = {l.misc + 9, l.misc + 10};
+                jp.ph.lead = b.lead_total;
+                jp.ph.cap = pl.cont_cap;
+                int h = 0;
+                for (int r0 = 0; r0 < pl.n; r0 += pl.dtw_phase, h ^= 1) {
+                    jp.ph.row_begin = r0;
+                    jp.ph.row_end = std::min(pl.n, r0 + pl.dtw_phase);
+                    const bool first = r0 == 0;
+                    jp.ph.in_state = first ? nullptr : l.cont_state[h ^ 1];
+                    jp.ph.in_pi = first ? nullptr : l.cont_pi[h ^ 1];
+                    jp.ph.in_count = first ? nullptr : cnt[h ^ 1];
+                    jp.ph.out_state = l.cont_state[h];
+                    jp.ph.out_pi = l.cont_pi[h];
+                    jp.ph.out_count = cnt[h];
+                    jp.cursor = l.misc + 11;
+                    RUN_TRY(cudaMemsetAsync(cnt[h], 0, sizeof(unsigned long long), s));
+                    RUN_TRY(cudaMemsetAsync(jp.cursor, 0, sizeof(unsigned long long), s));
+                    RUN_TRY(launch_dtw_phase_by_p(jp, pl.g, s));
+                }
+                tm.ev.kernels = (pl.n + pl.dtw_phase - 1) / pl.dtw_phase;
+            } else {
+                RUN_TRY(launch_dtw_any(jp, pl.g, s));
+            }
         }
     }
     {

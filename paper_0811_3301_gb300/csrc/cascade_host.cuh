@@ -39,6 +39,8 @@ struct CascadePlan {
     int nseg;        // sub-segments per query
     int seg_per_cta; // filter segments per CTA
     int dtw_path;    // 0 auto, 1 thread per pair, 2 warp per pair (main DTW stage)
+    int dtw_phase;   // main DTW stage on the thread-per-pair register path in row phases of this many rows (0: off)
+    int64_t cont_cap;  // entries of each row-phase continuation list
     int filter_path; // 1 one warp per pair, 2 batches of eight pairs per warp
     int lb_abandon;  // early abandoning inside the bound sums (streamed long rows)
     int order_first; // pairs per query the DTW stage takes first, by ascending bound (0: filter order)
@@ -48,6 +50,8 @@ struct CascadePlan {
 struct CascadeWs {
     float *U, *L, *UL, *LU, *copies, *lb, *PU, *PL, *seed_res, *lbi_u, *pair_lbi, *pair_res;
     unsigned long long *tile_min, *misc;
+    float *cont_state[2];    // row-phase continuation lists (dtw_phase > 0)
+    int64_t *cont_pi[2];
     Pair *seed_pairs, *pairs_u, *pairs;
     uint32_t *gmin, *bsf;
     int32_t *qcount, *qstart, *qstart_b, *seg_start, *seg_count;

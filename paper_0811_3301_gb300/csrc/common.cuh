@@ -242,6 +242,7 @@ struct CascadeBufs {
     int32_t *qstart_b;    // [Q], used when order_first > 0
     int order_first;
     unsigned long long *pair_total;  // pairs after grouping
+    unsigned long long *lead_total;  // pairs in the leading region (order_first > 0), else 0
     int lbi_inline;       // the filter computes LB_Improved (warp per pair)
     int summary;          // the matrix holds the piecewise-sum bound; LB_Keogh is computed in the filter
     float summary_scale;  // max_j |C_j| for p = 2 (matrix units), 1 for p = 1
@@ -304,6 +305,25 @@ struct DtwJob {
     // holds each listed pair's LB_Keogh^p on entry, tU/tL [Q][n] the query
     // envelopes.  nullptr: the row minimum alone.
     const float *tU, *tL;
+    // Row phases of the thread-per-pair register kernel (k_dtw_reg4p): the
+    // launch evaluates rows [row_begin, row_end) of its pairs; a pair still
+    // alive at row_end < n is deferred: its band state goes to the out list
+    // and the next launch resumes it.  Pairs read from an in list (in_state
+    // != nullptr) resume at row_begin; listed pairs whose index is below
+    // *lead run to the last row in the first launch.
+    struct Phase {
+        int row_begin, row_end;
+        const unsigned long long *lead;
+        // lists, structure of arrays: state[k * cap + t] (band slots k < C,
+        // then the LB_Keogh prefix at k = C), pi[t] the pair's list index
+        const float *in_state;
+        const int64_t *in_pi;
+        const unsigned long long *in_count;
+        float *out_state;
+        int64_t *out_pi;
+        unsigned long long *out_count;
+        int64_t cap;
+    } ph;
 };
 
 

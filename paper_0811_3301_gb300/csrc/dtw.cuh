@@ -19,6 +19,7 @@ namespace dtwk {
 constexpr int kDtwRegMaxC = 208;  // widest band kept in one thread's registers
 constexpr int kDtwThreads = 128;
 constexpr int kDtwGroupMaxC = 64;  // band widths processed 4 rows per window load
+constexpr int kDtwPhaseRows = 64;  // rows per launch of the row-phase register kernel (a multiple of 8)
 
 struct DtwGeom {
     int C;      // slots per pair (register path) or per warp (wide path)
@@ -92,6 +93,22 @@ cudaError_t launch_dtw_p1(const DtwJob &j, const DtwGeom &g, cudaStream_t s);
 cudaError_t launch_dtw_p2(const DtwJob &j, const DtwGeom &g, cudaStream_t s);
 cudaError_t launch_dtw_p4(const DtwJob &j, const DtwGeom &g, cudaStream_t s);
 cudaError_t launch_dtw_pinf(const DtwJob &j, const DtwGeom &g, cudaStream_t s);
+
+cudaError_t launch_dtw_phase_p1(const DtwJob &j, const DtwGeom &g, cudaStream_t s);
+cudaError_t launch_dtw_phase_p2(const DtwJob &j, const DtwGeom &g, cudaStream_t s);
+cudaError_t launch_dtw_phase_p4(const DtwJob &j, const DtwGeom &g, cudaStream_t s);
+cudaError_t launch_dtw_phase_pinf(const DtwJob &j, const DtwGeom &g, cudaStream_t s);
+
+// One launch of the row-phase register kernel (j.ph), by the job's exponent.
+inline cudaError_t launch_dtw_phase_by_p(const DtwJob &j, const DtwGeom &g, cudaStream_t s) {
+    switch (j.p) {
+        case 1: return launch_dtw_phase_p1(j, g, s);
+        case 2: return launch_dtw_phase_p2(j, g, s);
+        case 4: return launch_dtw_phase_p4(j, g, s);
+        case 0: return launch_dtw_phase_pinf(j, g, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
 
 // DTW of a job by its exponent j.p (1, 2, 4, or 0 for p = infinity).
 inline cudaError_t launch_dtw_by_p(const DtwJob &j, const DtwGeom &g, cudaStream_t s) {

@@ -264,6 +264,86 @@ __device__ __forceinline__ void dtw_row_win(float (&D)[C], float xi, const float
     dtw_cells_win<16, C, P, U>(D, xi, yw);
 }
 
+// Rows i .. i + 3 (those below n) of a thread-per-pair band, four rows per
+// window load: the query window of the group read from copy 0 (y0 + i) with
+// aligned 128-bit loads, x_i .. x_{i+3} with one (xvec) or four loads.  With
+// `tail`, the LB_Keogh terms of these rows are added to lbk_pre when rows
+// remain after them (the cumulative abandon bound, reading 6).
+template <int C, int P, int E>
+__device__ __forceinline__ void reg4_rows(float (&D)[C], const float *__restrict__ x, const float *__restrict__ y0,
+                                          int i, int n, int e, bool xvec, bool tail, const float *tu,
+                                          const float *tl, float &lbk_pre) {
+    float yw[C + 4];
+    const float4 *yb = reinterpret_cast<const float4 *>(y0 + i);
+#pragma unroll
+    for (int v = 0; v < (C + 4) / 4; ++v) {
+        const float4 t = __ldg(yb + v);
+        yw[4 * v] = t.x;
+        yw[4 * v + 1] = t.y;
+        yw[4 * v + 2] = t.z;
+        yw[4 * v + 3] = t.w;
+    }
+    float4 x4;
+    if (xvec && i + 4 <= n) {
+        x4 = __ldg(reinterpret_cast<const float4 *>(x + i));
+    } else {
+        x4.x = __ldg(x + i);
+        x4.y = i + 1 < n ? __ldg(x + i + 1) : 0.0f;
+        x4.z = i + 2 < n ? __ldg(x + i + 2) : 0.0f;
+        x4.w = i + 3 < n ? __ldg(x + i + 3) : 0.0f;
+    }
+    if constexpr (E >= 0) {
+        if (i + 4 <= n) {
+            dtw_row_win_fixed<C, P, 0, E>(D, x4.x, yw);
+            dtw_row_win_fixed<C, P, 1, E>(D, x4.y, yw);
+            dtw_row_win_fixed<C, P, 2, E>(D, x4.z, yw);
+            dtw_row_win_fixed<C, P, 3, E>(D, x4.w, yw);
+        } else {
+            dtw_row_win_fixed<C, P, 0, E>(D, x4.x, yw);
+            if (i + 1 < n) dtw_row_win_fixed<C, P, 1, E>(D, x4.y, yw);
+            if (i + 2 < n) dtw_row_win_fixed<C, P, 2, E>(D, x4.z, yw);
+        }
+    } else {
+        dtw_row_win<C, P, 0>(D, x4.x, yw, e);
+        if (i + 1 < n) dtw_row_win<C, P, 1>(D, x4.y, yw, e);
+        if (i + 2 < n) dtw_row_win<C, P, 2>(D, x4.z, yw, e);
+        if (i + 3 < n) dtw_row_win<C, P, 3>(D, x4.w, yw, e);
+    }
+    if (tail && i + 4 < n) {
+        float4 u4, l4;
+        if (xvec) {
+            u4 = __ldg(reinterpret_cast<const float4 *>(tu + i));
+            l4 = __ldg(reinterpret_cast<const float4 *>(tl + i));
+        } else {
+            u4 = make_float4(__ldg(tu + i), __ldg(tu + i + 1), __ldg(tu + i + 2), __ldg(tu + i + 3));
+            l4 = make_float4(__ldg(tl + i), __ldg(tl + i + 1), __ldg(tl + i + 2), __ldg(tl + i + 3));
+        }
+        lbk_pre = acc_dist<P>(lbk_pre, x4.x, l4.x, u4.x);
+        lbk_pre = acc_dist<P>(lbk_pre, x4.y, l4.y, u4.y);
+        lbk_pre = acc_dist<P>(lbk_pre, x4.z, l4.z, u4.z);
+        lbk_pre = acc_dist<P>(lbk_pre, x4.w, l4.w, u4.w);
+    }
+}
+
+// The abandon test after a row group (every 8 rows): the band's minimum, raised
+// by the LB_Keogh terms of the rows not yet reached (reading 6) when `tail`,
+// against the threshold.  fp32: the two LB_Keogh sums (different orders) each
+// carry at most n u relative error, and the path's remaining additions at
+// most (2n - 1) u; c covers both.
+template <int C>
+__device__ __forceinline__ bool reg4_abandons(const float (&D)[C], int n, bool tail, float lbk_total, float lbk_pre,
+                                              float thr) {
+    float mn = D[0];
+#pragma unroll
+    for (int k = 1; k < C; ++k) mn = fminf(mn, D[k]);
+    if (tail) {
+        const float c = (float)(2 * n + 2) * 5.9604645e-8f;
+        const float rest = fmaxf(0.0f, lbk_total - lbk_pre - c * lbk_total);
+        mn = fmaxf(mn, (mn + rest) * (1.0f - c));
+    }
+    return mn > thr;
+}
+
 template <int C, int P, int E>
 __global__ void __launch_bounds__(kDtwThreads)
 k_dtw_reg4(DtwJob j, int e, int wl, bool xvec) {
@@ -312,70 +392,10 @@ k_dtw_reg4(DtwJob j, int e, int wl, bool xvec) {
             const float *tl = tail ? j.tL + (int64_t)q * n : nullptr;
             float lbk_pre = 0.0f;
             for (int i = 0; i < n; i += 4) {
-                float yw[C + 4];
-                const float4 *yb = reinterpret_cast<const float4 *>(y0 + i);
-#pragma unroll
-                for (int v = 0; v < (C + 4) / 4; ++v) {
-                    const float4 t = __ldg(yb + v);
-                    yw[4 * v] = t.x;
-                    yw[4 * v + 1] = t.y;
-                    yw[4 * v + 2] = t.z;
-                    yw[4 * v + 3] = t.w;
-                }
-                float4 x4;
-                if (xvec && i + 4 <= n) {
-                    x4 = __ldg(reinterpret_cast<const float4 *>(x + i));
-                } else {
-                    x4.x = __ldg(x + i);
-                    x4.y = i + 1 < n ? __ldg(x + i + 1) : 0.0f;
-                    x4.z = i + 2 < n ? __ldg(x + i + 2) : 0.0f;
-                    x4.w = i + 3 < n ? __ldg(x + i + 3) : 0.0f;
-                }
-                if constexpr (E >= 0) {
-                    if (i + 4 <= n) {
-                        dtw_row_win_fixed<C, P, 0, E>(D, x4.x, yw);
-                        dtw_row_win_fixed<C, P, 1, E>(D, x4.y, yw);
-                        dtw_row_win_fixed<C, P, 2, E>(D, x4.z, yw);
-                        dtw_row_win_fixed<C, P, 3, E>(D, x4.w, yw);
-                    } else {
-                        dtw_row_win_fixed<C, P, 0, E>(D, x4.x, yw);
-                        if (i + 1 < n) dtw_row_win_fixed<C, P, 1, E>(D, x4.y, yw);
-                        if (i + 2 < n) dtw_row_win_fixed<C, P, 2, E>(D, x4.z, yw);
-                    }
-                } else {
-                    dtw_row_win<C, P, 0>(D, x4.x, yw, e);
-                    if (i + 1 < n) dtw_row_win<C, P, 1>(D, x4.y, yw, e);
-                    if (i + 2 < n) dtw_row_win<C, P, 2>(D, x4.z, yw, e);
-                    if (i + 3 < n) dtw_row_win<C, P, 3>(D, x4.w, yw, e);
-                }
-                if (tail && i + 4 < n) {
-                    float4 u4, l4;
-                    if (xvec) {
-                        u4 = __ldg(reinterpret_cast<const float4 *>(tu + i));
-                        l4 = __ldg(reinterpret_cast<const float4 *>(tl + i));
-                    } else {
-                        u4 = make_float4(__ldg(tu + i), __ldg(tu + i + 1), __ldg(tu + i + 2), __ldg(tu + i + 3));
-                        l4 = make_float4(__ldg(tl + i), __ldg(tl + i + 1), __ldg(tl + i + 2), __ldg(tl + i + 3));
-                    }
-                    lbk_pre = acc_dist<P>(lbk_pre, x4.x, l4.x, u4.x);
-                    lbk_pre = acc_dist<P>(lbk_pre, x4.y, l4.y, u4.y);
-                    lbk_pre = acc_dist<P>(lbk_pre, x4.z, l4.z, u4.z);
-                    lbk_pre = acc_dist<P>(lbk_pre, x4.w, l4.w, u4.w);
-                }
+                reg4_rows<C, P, E>(D, x, y0, i, n, e, xvec, tail, tu, tl, lbk_pre);
                 if (j.abandon && (i & 4) && i + 4 < n) {
-                    float mn = D[0];
-#pragma unroll
-                    for (int k = 1; k < C; ++k) mn = fminf(mn, D[k]);
                     if (j.bsf) thr = load_threshold(j.bsf + q);
-                    if (tail) {
-                        // fp32: the two LB_Keogh sums (different orders) each
-                        // carry at most n u relative error, and the path's
-                        // remaining additions at most (2n - 1) u; c covers both
-                        const float c = (float)(2 * n + 2) * 5.9604645e-8f;
-                        const float rest = fmaxf(0.0f, lbk_total - lbk_pre - c * lbk_total);
-                        mn = fmaxf(mn, (mn + rest) * (1.0f - c));
-                    }
-                    if (mn > thr) {
+                    if (reg4_abandons<C>(D, n, tail, lbk_total, lbk_pre, thr)) {
                         abandoned = true;
                         rows = i + 4;
                         break;
@@ -407,6 +427,164 @@ k_dtw_reg4(DtwJob j, int e, int wl, bool xvec) {
         for (int o = 16; o > 0; o >>= 1) n_rows += __shfl_xor_sync(0xffffffffu, n_rows, o);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) n_cells += __shfl_xor_sync(0xffffffffu, n_cells, o);
+        if (lane == 0) {
+            if (n_rows) atomicAdd(j.counters + CNT_DTW_ROWS, n_rows);
+            if (n_cells) atomicAdd(j.counters + CNT_DTW_CELLS, n_cells);
+            if (n_skip) atomicAdd(j.counters + CNT_DTW_SKIP, n_skip);
+            if (n_comp) atomicAdd(j.counters + CNT_DTW_COMPUTED, n_comp);
+            if (n_aband) atomicAdd(j.counters + CNT_DTW_ABANDONED, n_aband);
+            if (n_lane_rows) atomicAdd(j.counters + CNT_DTW_LANE_ROWS, n_lane_rows);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Register path in row phases (C <= 64): the rows, cells, abandon test and
+// results of k_dtw_reg4, but one launch evaluates only rows
+// [row_begin, row_end) of its pairs.  A pair still alive at row_end (< n) is
+// deferred: its band (C slots) and LB_Keogh prefix are written to the out
+// list, 32 consecutive pairs of a warp to consecutive entries, and the next
+// launch resumes it from there.  A warp thus steps only until the longest of
+// its pairs ends within the phase, and the next phase's warps are full again
+// with pairs at the same row, so lanes idle for less than a phase; the
+// pairs of a warp still share a row and mostly a query, so the query-window
+// loads stay warp-wide broadcasts.  Listed pairs below *lead (every query's
+// lowest-bound pairs, taken first) run to the last row in the first phase,
+// so that thresholds fall before the bulk is resumed.  If the out list is
+// full, the pair runs on in place.
+// ---------------------------------------------------------------------------
+template <int C, int P, int E>
+__global__ void __launch_bounds__(kDtwThreads, (E >= 0 ? 3 : 2))
+k_dtw_reg4p(DtwJob j, int e, int wl, bool xvec) {
+    const int lane = threadIdx.x & 31;
+    const int n = j.n;
+    const int ylen = j.qc.ylen;
+    const int wb = min(j.w, n - 1);
+    const bool resume = j.ph.in_state != nullptr;
+    const int64_t cap = j.ph.cap;
+    int64_t npairs = j.npairs;
+    if (resume) {
+        const unsigned long long c_in = *j.ph.in_count;
+        npairs = (int64_t)(c_in < (unsigned long long)cap ? c_in : (unsigned long long)cap);
+    } else if (j.npairs_dev) {
+        npairs = (int64_t)*j.npairs_dev;
+    }
+    const int64_t lead = (!resume && j.ph.lead) ? (int64_t)*j.ph.lead : 0;
+    const int r0 = j.ph.row_begin;
+    const bool tail = (P == 1 || P == 2) && j.tU != nullptr && j.abandon;
+    const unsigned long long cells0 = (unsigned long long)band_cells(r0, n, wb);
+    unsigned long long n_skip = 0, n_comp = 0, n_aband = 0, n_rows = 0, n_lane_rows = 0, n_cells = 0;
+    for (;;) {
+        unsigned long long chunk = 0;
+        if (lane == 0) chunk = atomicAdd(j.cursor, 1ull);
+        chunk = __shfl_sync(0xffffffffu, chunk, 0);
+        const int64_t p0 = (int64_t)chunk * 32;
+        if (p0 >= npairs) break;
+        const int64_t t = p0 + lane;
+        bool alive = t < npairs;
+        int64_t pi = 0;
+        int q = 0, c = 0;
+        if (alive) {
+            pi = resume ? j.ph.in_pi[t] : t;
+            const Pair pr = j.pairs[pi];
+            q = pr.q;
+            c = pr.c;
+            if (c < 0) alive = false;
+        }
+        float thr = kInf;
+        if (alive) {
+            thr = j.bsf ? load_threshold(j.bsf + q) : j.fixed_thr;
+            if (!resume && j.pair_lbi && j.pair_lbi[pi] > thr * (1.0f + j.slack)) {
+                j.res[pi] = kInf;
+                alive = false;
+                ++n_skip;
+            }
+        }
+        if (alive && !resume) ++n_comp;
+        // rows this lane runs to in this launch
+        int stop = (pi < lead || j.ph.row_end >= n) ? n : j.ph.row_end;
+        const float *x = j.db + (int64_t)c * n;
+        const float *y0 = j.qc.data + (int64_t)q * 4 * ylen;  // copy 0; row i starts at index i
+        const float *tu = tail ? j.tU + (int64_t)q * n : nullptr;
+        const float *tl = tail ? j.tL + (int64_t)q * n : nullptr;
+        const float lbk_total = (tail && alive) ? j.res[pi] : 0.0f;
+        float D[C];
+        float lbk_pre = 0.0f;
+        if (resume) {
+#pragma unroll
+            for (int k = 0; k < C; ++k) D[k] = alive ? j.ph.in_state[(int64_t)k * cap + t] : kInf;
+            lbk_pre = alive ? j.ph.in_state[(int64_t)C * cap + t] : 0.0f;
+        } else {
+#pragma unroll
+            for (int k = 0; k < C; ++k) D[k] = sel_eq(k, wl, 0.0f, kInf);  // row -1: D(-1,-1) = 0
+        }
+        bool abandoned = false, deferred = false;
+        int i = r0;
+        for (;;) {
+            while (__any_sync(0xffffffffu, alive && i < stop)) {
+                if (alive && i < stop) {
+                    reg4_rows<C, P, E>(D, x, y0, i, n, e, xvec, tail, tu, tl, lbk_pre);
+                    if (j.abandon && (i & 4) && i + 4 < n) {
+                        if (j.bsf) thr = load_threshold(j.bsf + q);
+                        if (reg4_abandons<C>(D, n, tail, lbk_total, lbk_pre, thr)) {
+                            abandoned = true;
+                            alive = false;
+                        }
+                    }
+                    i += 4;
+                }
+            }
+            // pairs alive at the end of the phase move to the out list
+            const bool want = alive && stop < n;
+            const unsigned m = __ballot_sync(0xffffffffu, want);
+            if (m == 0) break;
+            unsigned long long base = 0;
+            const int leader = __ffs(m) - 1;
+            if (lane == leader) base = atomicAdd(j.ph.out_count, (unsigned long long)__popc(m));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (want) {
+                const int64_t slot = (int64_t)base + __popc(m & ((1u << lane) - 1));
+                if (slot < cap) {
+#pragma unroll
+                    for (int k = 0; k < C; ++k) j.ph.out_state[(int64_t)k * cap + slot] = D[k];
+                    j.ph.out_state[(int64_t)C * cap + slot] = lbk_pre;
+                    j.ph.out_pi[slot] = pi;
+                    deferred = true;
+                    alive = false;
+                } else {
+                    stop = n;  // no room: this pair runs on here
+                }
+            }
+            if (!__any_sync(0xffffffffu, alive && i < stop)) break;
+        }
+        const int rows = min(i, n);  // rows evaluated so far (abandoned pairs: through their last group)
+        if (i > r0) {
+            n_rows += (unsigned long long)(rows - r0);
+            n_cells += (unsigned long long)band_cells(rows, n, wb) - cells0;
+        }
+        n_lane_rows += 32ull * __reduce_max_sync(0xffffffffu, (unsigned)(i > r0 ? min(i, n) - r0 : 0));
+        if (abandoned) {
+            ++n_aband;
+            j.res[pi] = kInf;
+        } else if (alive) {
+            // completed: the last row was evaluated
+            float d = kInf;
+#pragma unroll
+            for (int k = 0; k < C; ++k) d = sel_eq(k, wl, D[k], d);
+            if (!j.bsf && d > j.fixed_thr) d = kInf;
+            j.res[pi] = j.root_out ? root_p(d, P) : d;
+            if (j.bsf) update_threshold(j.bsf, j.gmin, j.k, q, c % j.k, d);
+        }
+    }
+    if (j.counters) {
+        n_skip = __reduce_add_sync(0xffffffffu, (unsigned)n_skip);
+        n_comp = __reduce_add_sync(0xffffffffu, (unsigned)n_comp);
+        n_aband = __reduce_add_sync(0xffffffffu, (unsigned)n_aband);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            n_rows += __shfl_xor_sync(0xffffffffu, n_rows, o);
+            n_cells += __shfl_xor_sync(0xffffffffu, n_cells, o);
+        }
         if (lane == 0) {
             if (n_rows) atomicAdd(j.counters + CNT_DTW_ROWS, n_rows);
             if (n_cells) atomicAdd(j.counters + CNT_DTW_CELLS, n_cells);

@@ -119,4 +119,32 @@ cudaError_t launch_dtw_pt(const DtwJob &j, const DtwGeom &g, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// The row-phase thread-per-pair kernel (k_dtw_reg4p) for one launch of
+// j.ph's rows; bands of up to 64 slots on the register path only.
+template <int P>
+cudaError_t launch_dtw_phase_pt(const DtwJob &j, const DtwGeom &g, cudaStream_t s) {
+    if (g.wide || g.C > kDtwGroupMaxC) return cudaErrorInvalidValue;
+    const int64_t warps = (j.npairs + 31) / 32;
+    const bool xvec = (j.n % 4 == 0) && ((reinterpret_cast<uintptr_t>(j.db) & 15) == 0);
+#define DTW_REG4P_FIXED(CC, EE)                                                                       \
+    if (g.C == CC && g.e == EE) {                                                                     \
+        auto kern = k_dtw_reg4p<CC, P, EE>;                                                          \
+        kern<<<launch_detail::blocks_for(kern, warps), kDtwThreads, 0, s>>>(j, g.e, g.wl, xvec);      \
+        return cudaGetLastError();                                                                    \
+    }
+    DTW_REG4P_FIXED(16, 3) DTW_REG4P_FIXED(32, 7) DTW_REG4P_FIXED(48, 11) DTW_REG4P_FIXED(64, 13)
+#undef DTW_REG4P_FIXED
+#define DTW_REG4P_CASE(CC)                                                                            \
+    case CC: {                                                                                        \
+        auto kern = k_dtw_reg4p<CC, P, -1>;                                                          \
+        kern<<<launch_detail::blocks_for(kern, warps), kDtwThreads, 0, s>>>(j, g.e, g.wl, xvec);      \
+        return cudaGetLastError();                                                                    \
+    }
+    switch (g.C) {
+        DTW_REG4P_CASE(16) DTW_REG4P_CASE(32) DTW_REG4P_CASE(48) DTW_REG4P_CASE(64)
+        default: return cudaErrorInvalidValue;
+    }
+#undef DTW_REG4P_CASE
+}
+
 }  // namespace dtwk

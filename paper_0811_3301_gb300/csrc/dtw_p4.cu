@@ -4,5 +4,8 @@
 namespace dtwk {
 
 cudaError_t launch_dtw_p4(const DtwJob &j, const DtwGeom &g, cudaStream_t s) { return launch_dtw_pt<4>(j, g, s); }
+cudaError_t launch_dtw_phase_p4(const DtwJob &j, const DtwGeom &g, cudaStream_t s) {
+    return launch_dtw_phase_pt<4>(j, g, s);
+}
 
 }  // namespace dtwk

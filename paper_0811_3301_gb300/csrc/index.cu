@@ -677,7 +677,8 @@ size_t batch_bytes(const Batch &bt) {
 // keeps the fastest.  The result of the search does not depend on the
 // parameters (the cascade is exact); only its speed does.  Coordinate descent:
 // parts, then seeds, then the filter segment length, then the DTW kernel
-// (thread or warp per pair), each with the others at their best so far.
+// (thread or warp per pair, or thread per pair in row phases), then the
+// filter's warps per CTA, each with the others at their best so far.
 dtw_status tune_group(dtw_index *ix, int b, int w, int k, const float *qdev, int qn, Tuning *out) {
     const Bucket &bk = ix->buckets[b];
     const int n = bk.n;
@@ -697,16 +698,18 @@ dtw_status tune_group(dtw_index *ix, int b, int w, int k, const float *qdev, int
         path_c.push_back(2);
         if (2 * we + 1 <= 512) path_c.push_back(3);
     }
+    if (n > 2 * kDtwPhaseRows && 2 * we + 1 <= kDtwGroupMaxC) path_c.push_back(4);
     const std::vector<int> fw_c{0, 4, 5, 6, 7, 8};
 
     // scratch sized for the largest candidate plan
     size_t ws_max = 0;
     for (int pc : parts_c)
         for (int sd : seeds_c)
-            for (int sg : seg_c) {
-                Tuning t{pc, sd, sg, 0.0f, 0, 0};
-                ws_max = std::max(ws_max, cascade_ws_bytes(plan_for(ix, b, we, k, qn, t)));
-            }
+            for (int sg : seg_c)
+                for (int dp : {0, 4}) {
+                    Tuning t{pc, sd, sg, 0.0f, dp, 0};
+                    ws_max = std::max(ws_max, cascade_ws_bytes(plan_for(ix, b, we, k, qn, t)));
+                }
     Carve cv0;
     cv0.take<int64_t>((size_t)qn * k);
     cv0.take<float>((size_t)qn * k);
@@ -927,7 +930,7 @@ dtw_status dtw_index_create(int32_t p, const dtw_options *opt, dtw_index **out) 
     if (!(o.slack >= 0.0f) || std::isinf(o.slack)) return ix_fail(DTW_ERR_INVALID_ARG, "slack must be finite and >= 0");
     if (o.seeds < 0) return ix_fail(DTW_ERR_INVALID_ARG, "seeds=%d must be >= 0", o.seeds);
     if (o.parts < -1) return ix_fail(DTW_ERR_INVALID_ARG, "parts=%d must be >= -1", o.parts);
-    if (o.dtw_path < 0 || o.dtw_path > 3) return ix_fail(DTW_ERR_INVALID_ARG, "dtw_path=%d outside [0, 3]", o.dtw_path);
+    if (o.dtw_path < 0 || o.dtw_path > 4) return ix_fail(DTW_ERR_INVALID_ARG, "dtw_path=%d outside [0, 4]", o.dtw_path);
     if (o.filter_path < 0 || o.filter_path > 2)
         return ix_fail(DTW_ERR_INVALID_ARG, "filter_path=%d outside [0, 2]", o.filter_path);
     auto *ix = new dtw_index();
@@ -1041,10 +1044,10 @@ dtw_status dtw_index_set_tuning(dtw_index *ix, int32_t n, int32_t w, int32_t k, 
     if (t->parts < -1 || t->parts > n || t->seeds < 0 || t->seeds > 32 ||
         (t->seg_len != 0 && t->seg_len != 512 && t->seg_len != 1024 && t->seg_len != 2048 && t->seg_len != 4096) ||
         t->dtw_path < 0 ||
-        t->dtw_path > 3 ||
+        t->dtw_path > 4 ||
         t->filter_warps < 0 || t->filter_warps > 8)
         return ix_fail(DTW_ERR_INVALID_ARG, "tuning out of range (parts in [-1, n], seeds in [0, 32], seg_len "
-                                            "0/512/1024/2048/4096, dtw_path 0-3, filter_warps 0-8)");
+                                            "0/512/1024/2048/4096, dtw_path 0-4, filter_warps 0-8)");
     if (w < 0 || k < 1 || k > DTW_MAX_K) return ix_fail(DTW_ERR_INVALID_ARG, "w or k out of range");
     std::lock_guard<std::mutex> lk(ix->mu);
     if (find_bucket(ix, n) < 0) return ix_fail(DTW_ERR_NO_BUCKET, "no bucket of length %d", n);

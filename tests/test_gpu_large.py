@@ -80,6 +80,10 @@ def test_random_walk_full_size_ten_neighbours(api):
         idx, dist = api.knn_search(cuda(db), cuda(qs), 25, p, 10)
         sample = np.array([0, 1, 500, 998, 999])
         check_rows(db, qs[sample], 25, p, 10, idx.cpu().numpy()[sample], dist.cpu().numpy()[sample])
+        # at this size the main DTW stage runs in row phases; every query's
+        # answer equals the one-launch thread path's bit for bit
+        ti, td = api.knn_search(cuda(db), cuda(qs), 25, p, 10, dtw_path=1)
+        assert torch.equal(idx, ti) and torch.equal(dist, td), p
 
 
 def test_index_long_buckets_graph_autotune(api):

@@ -330,6 +330,25 @@ def test_knn_warp_dtw_path(api, p, n, w, k):
         assert torch.equal(gi, ti) and torch.equal(gd, td)
 
 
+@pytest.mark.parametrize("p", [1, 2])
+@pytest.mark.parametrize("n,w,k", [(256, 25, 1), (256, 25, 10), (200, 6, 3), (301, 30, 1), (130, 12, 2)])
+def test_dtw_row_phases_equal_thread_path(api, p, n, w, k):
+    # the main DTW stage in row phases of 64 rows (pairs alive at a phase's
+    # end resumed by the next launch) gives the thread path's results bit
+    # for bit; compile-time and runtime band paddings, n % 4 != 0 and n not a
+    # multiple of the phase; counters still add up
+    db = synth.random_walks(6_000, n, seed=60 + n)
+    qs = synth.random_walks(40, n, seed=61 + n, stream=synth.STREAM_QUERY)
+    ti, td = api.knn_search(cuda(db), cuda(qs), w, p, k, dtw_path=1)
+    ri, rd, st = api.knn_search(cuda(db), cuda(qs), w, p, k, dtw_path=4, return_stats=True)
+    assert torch.equal(ri, ti) and torch.equal(rd, td)
+    pruned = st["pruned_summary"] + st["pruned_keogh"] + st["pruned_improved"]
+    assert st["seeds"] + pruned + st["dtw_computed"] == st["candidates"]
+    assert 0 < st["dtw_rows"] <= st["dtw_lane_rows"]
+    oi, od, _ = oracle.knn_cascade(db, qs[:6], w, p, k, mode=1, threads=8)
+    assert_knn(db, qs[:6], w, p, k, ti[:6], td[:6], oi, od)
+
+
 def test_knn_edge_cases(api):
     # k > N pads with -1 / +inf; N = 1; n = 1; odd n (scalar load path); w = 0; w >= n
     db = synth.random_walks(5, 33, seed=5)
