@@ -94,8 +94,9 @@ typedef struct {
                          3 one warp per two pairs (16-lane groups) where the band allows,
                          4 one thread per pair in launches of 64 rows (pairs still alive
                          at a launch's last row are resumed by the next one), where the
-                         band fits 64 register slots and n > 128; 0 uses 4 for runs of
-                         at least 2^24 (query, candidate) pairs */
+                         band fits one thread's registers (2w + 1 <= 64, or <= 208 for
+                         p = 1 and 2) and n > 128; 0 uses 4 for bands of up to 64
+                         slots in runs of at least 2^24 (query, candidate) pairs */
     int32_t filter_path; /* LB_Keogh / LB_Improved filter kernel: 0 chooses (batches of eight
                             pairs per warp for series of 128 or 256 elements with the
                             piecewise-sum pre-filter, else one warp per pair), 1 one warp

@@ -156,14 +156,17 @@ CascadePlan make_plan(int64_t N, int64_t Qmax, int n, int w, int p, int k, const
     // (2048 keeps enough CTAs on smaller ones), 1024 for longer series
     pl.seg_len = seg_len > 0 ? seg_len : (n <= 256 ? (N >= 65536 ? 4096 : 2048) : 1024);
     pl.dtw_path = o.dtw_path;
-    // The main DTW stage in row phases of 64 rows (k_dtw_reg4p): bands of up
-    // to 64 register slots, series longer than two phases; asked for
-    // (dtw_path 4) or, by default, for runs of at least 2^24 pairs, where the
-    // stage is long enough for the phases' state traffic and extra launches
-    // to pay (100,000 x 256, 1,000 queries: DTW stage 1.44 -> 1.37 ms).
-    const bool phase_ok = !pl.g.wide && pl.g.C <= kDtwGroupMaxC && n > 2 * kDtwPhaseRows &&
-                          pl.mode != DTW_MODE_NOPRUNE && N > 0;
-    const bool phase_big = o.dtw_path == 0 && Qc * N >= ((int64_t)1 << 24);
+    // The main DTW stage in row phases of 64 rows (k_dtw_reg4p, k_dtw_regp):
+    // bands on the register path (up to 64 slots, or 208 for p = 1 and 2),
+    // series longer than two phases.  Asked for by dtw_path 4; by default for
+    // bands of up to 64 slots in runs of at least 2^24 pairs, where the stage
+    // is long enough for the phases' state traffic and extra launches to pay
+    // (100,000 x 256, 1,000 queries: DTW stage 1.44 -> 1.37 ms).  Wider bands
+    // measured slower in phases (n = 1,024, w = 102: 12.9 -> 14.5 ms), their
+    // 209-slot states outweighing the lanes regained.
+    const bool phase_ok = !pl.g.wide && pl.g.C <= (p == 1 || p == 2 ? kDtwRegMaxC : kDtwGroupMaxC) &&
+                          n > 2 * kDtwPhaseRows && pl.mode != DTW_MODE_NOPRUNE && N > 0;
+    const bool phase_big = o.dtw_path == 0 && pl.g.C <= kDtwGroupMaxC && Qc * N >= ((int64_t)1 << 24);
     pl.dtw_phase = (phase_ok && (o.dtw_path == 4 || phase_big)) ? kDtwPhaseRows : 0;
     pl.lb_abandon = o.lb_abandon > 0 ? 1 : 0;
     // The DTW stage takes every query's lowest-bound pairs first (a multiple

@@ -87,6 +87,58 @@ __device__ __forceinline__ void dtw_cells_from(float (&D)[C], float xi, const fl
     }
 }
 
+// One row i of the register path: the band window of the query read from
+// the shifted copy that puts column i - wl on a 16-byte boundary, the row
+// entered at slot e (a jump on the uniform e).
+template <int C, int P>
+__device__ __forceinline__ void reg_row(float (&D)[C], float xi, const float *__restrict__ yc, int i, int e, int wl,
+                                        int padl, int ylen) {
+    const int a = i - wl + padl;
+    const int r = a & 3;
+    const float4 *yb = reinterpret_cast<const float4 *>(yc + r * ylen + (a - r));
+    const float4 h0 = __ldg(yb + 0), h1 = __ldg(yb + 1), h2 = __ldg(yb + 2), h3 = __ldg(yb + 3);
+    switch (e) {
+        case 0: DTW_CELL(0, h0.x) [[fallthrough]];
+        case 1: DTW_CELL(1, h0.y) [[fallthrough]];
+        case 2: DTW_CELL(2, h0.z) [[fallthrough]];
+        case 3: DTW_CELL(3, h0.w) [[fallthrough]];
+        case 4: DTW_CELL(4, h1.x) [[fallthrough]];
+        case 5: DTW_CELL(5, h1.y) [[fallthrough]];
+        case 6: DTW_CELL(6, h1.z) [[fallthrough]];
+        case 7: DTW_CELL(7, h1.w) [[fallthrough]];
+        case 8: DTW_CELL(8, h2.x) [[fallthrough]];
+        case 9: DTW_CELL(9, h2.y) [[fallthrough]];
+        case 10: DTW_CELL(10, h2.z) [[fallthrough]];
+        case 11: DTW_CELL(11, h2.w) [[fallthrough]];
+        case 12: DTW_CELL(12, h3.x) [[fallthrough]];
+        case 13: DTW_CELL(13, h3.y) [[fallthrough]];
+        case 14: DTW_CELL(14, h3.z) [[fallthrough]];
+        default: DTW_CELL(15, h3.w)
+    }
+    dtw_cells_from<16, C, P>(D, xi, yb);
+}
+
+// The abandon test after a row group (every 8 rows): the band's minimum, raised
+// by the LB_Keogh terms of the rows not yet reached (reading 6) when `tail`,
+// against the threshold.  fp32: the two LB_Keogh sums (different orders) each
+// carry at most n u relative error, and the path's remaining additions at
+// most (2n - 1) u; c covers both.
+__device__ __forceinline__ float raise_by_tail(float mn, int n, float lbk_total, float lbk_pre) {
+    const float c = (float)(2 * n + 2) * 5.9604645e-8f;
+    const float rest = fmaxf(0.0f, lbk_total - lbk_pre - c * lbk_total);
+    return fmaxf(mn, (mn + rest) * (1.0f - c));
+}
+
+template <int C>
+__device__ __forceinline__ bool reg4_abandons(const float (&D)[C], int n, bool tail, float lbk_total, float lbk_pre,
+                                              float thr) {
+    float mn = D[0];
+#pragma unroll
+    for (int k = 1; k < C; ++k) mn = fminf(mn, D[k]);
+    if (tail) mn = raise_by_tail(mn, n, lbk_total, lbk_pre);
+    return mn > thr;
+}
+
 // ---------------------------------------------------------------------------
 // Register path: one thread per pair, the whole band of C = round_up(2w+1, 16)
 // slots in registers.  The band occupies slots e..C-1 (e = C - (2w+1) < 16);
@@ -104,7 +156,8 @@ k_dtw_reg(DtwJob j, int e, int wl) {
     const int ylen = j.qc.ylen, padl = j.qc.padl;
     if (j.npairs_dev) j.npairs = (int64_t)*j.npairs_dev;
     const int wb = min(j.w, n - 1);
-    unsigned long long n_skip = 0, n_comp = 0, n_aband = 0, n_rows = 0, n_cells = 0;
+    const bool tail = (P == 1 || P == 2) && j.tU != nullptr && j.abandon;
+    unsigned long long n_skip = 0, n_comp = 0, n_aband = 0, n_rows = 0, n_lane_rows = 0, n_cells = 0;
     for (;;) {
         unsigned long long chunk = 0;
         if (lane == 0) chunk = atomicAdd(j.cursor, 1ull);
@@ -116,6 +169,7 @@ k_dtw_reg(DtwJob j, int e, int wl) {
         bool valid;
         fetch_pair(j, pi, q, c, valid);
         float thr = kInf;
+        int my_rows = 0;
         if (valid) {
             thr = j.bsf ? load_threshold(j.bsf + q) : j.fixed_thr;
             if (j.pair_lbi && j.pair_lbi[pi] > thr * (1.0f + j.slack)) {
@@ -128,6 +182,12 @@ k_dtw_reg(DtwJob j, int e, int wl) {
         ++n_comp;
         const float *x = j.db + (int64_t)c * n;
         const float *yc = j.qc.data + (int64_t)q * 4 * ylen;
+        // the cumulative LB_Keogh abandon bound (reading 6): the pair's result
+        // slot holds its LB_Keogh^p (read at each test, to spare registers),
+        // and the terms of the rows passed so far are summed here; the rest
+        // bounds the rows not yet reached
+        const int64_t toff = tail ? (int64_t)q * n : 0;
+        float lbk_pre = 0.0f;
         float D[C];
 #pragma unroll
         for (int k = 0; k < C; ++k) D[k] = sel_eq(k, wl, 0.0f, kInf);  // row -1: D(-1,-1) = 0
@@ -135,35 +195,12 @@ k_dtw_reg(DtwJob j, int e, int wl) {
         int rows = n;
         for (int i = 0; i < n; ++i) {
             const float xi = __ldg(x + i);
-            const int a = i - wl + padl;
-            const int r = a & 3;
-            const float4 *yb = reinterpret_cast<const float4 *>(yc + r * ylen + (a - r));
-            const float4 h0 = __ldg(yb + 0), h1 = __ldg(yb + 1), h2 = __ldg(yb + 2), h3 = __ldg(yb + 3);
-            switch (e) {
-                case 0: DTW_CELL(0, h0.x) [[fallthrough]];
-                case 1: DTW_CELL(1, h0.y) [[fallthrough]];
-                case 2: DTW_CELL(2, h0.z) [[fallthrough]];
-                case 3: DTW_CELL(3, h0.w) [[fallthrough]];
-                case 4: DTW_CELL(4, h1.x) [[fallthrough]];
-                case 5: DTW_CELL(5, h1.y) [[fallthrough]];
-                case 6: DTW_CELL(6, h1.z) [[fallthrough]];
-                case 7: DTW_CELL(7, h1.w) [[fallthrough]];
-                case 8: DTW_CELL(8, h2.x) [[fallthrough]];
-                case 9: DTW_CELL(9, h2.y) [[fallthrough]];
-                case 10: DTW_CELL(10, h2.z) [[fallthrough]];
-                case 11: DTW_CELL(11, h2.w) [[fallthrough]];
-                case 12: DTW_CELL(12, h3.x) [[fallthrough]];
-                case 13: DTW_CELL(13, h3.y) [[fallthrough]];
-                case 14: DTW_CELL(14, h3.z) [[fallthrough]];
-                default: DTW_CELL(15, h3.w)
-            }
-            dtw_cells_from<16, C, P>(D, xi, yb);
+            if (tail) lbk_pre = acc_dist<P>(lbk_pre, xi, __ldg(j.tL + toff + i), __ldg(j.tU + toff + i));
+            reg_row<C, P>(D, xi, yc, i, e, wl, padl, ylen);
             if (j.abandon && (i & 7) == 7 && i + 1 < n) {
-                float mn = D[0];
-#pragma unroll
-                for (int k = 1; k < C; ++k) mn = fminf(mn, D[k]);
                 if (j.bsf) thr = load_threshold(j.bsf + q);
-                if (mn > thr) {
+                const float lbk_total = tail ? j.res[pi] : 0.0f;
+                if (reg4_abandons<C>(D, n, tail, lbk_total, lbk_pre, thr)) {
                     abandoned = true;
                     rows = i + 1;
                     break;
@@ -171,6 +208,7 @@ k_dtw_reg(DtwJob j, int e, int wl) {
             }
         }
         n_rows += rows;
+        my_rows = rows;
         n_cells += (unsigned long long)band_cells(rows, n, wb);
         float d = kInf;
 #pragma unroll
@@ -183,6 +221,8 @@ k_dtw_reg(DtwJob j, int e, int wl) {
         j.res[pi] = j.root_out ? root_p(d, P) : d;
         if (!abandoned && j.bsf) update_threshold(j.bsf, j.gmin, j.k, q, c % j.k, d);
         }  // valid
+        // the warp steps until its longest pair ends
+        n_lane_rows += 32ull * __reduce_max_sync(0xffffffffu, (unsigned)my_rows);
     }
     if (j.counters) {
         // one atomic per warp and counter
@@ -197,6 +237,7 @@ k_dtw_reg(DtwJob j, int e, int wl) {
         for (int o = 16; o > 0; o >>= 1) n_cells += __shfl_xor_sync(0xffffffffu, n_cells, o);
         if (lane == 0) {
             if (rows_w) atomicAdd(j.counters + CNT_DTW_ROWS, rows_w);
+            if (n_lane_rows) atomicAdd(j.counters + CNT_DTW_LANE_ROWS, n_lane_rows);
             if (n_cells) atomicAdd(j.counters + CNT_DTW_CELLS, n_cells);
             if (n_skip) atomicAdd(j.counters + CNT_DTW_SKIP, n_skip);
             if (n_comp) atomicAdd(j.counters + CNT_DTW_COMPUTED, n_comp);
@@ -323,25 +364,6 @@ __device__ __forceinline__ void reg4_rows(float (&D)[C], const float *__restrict
         lbk_pre = acc_dist<P>(lbk_pre, x4.z, l4.z, u4.z);
         lbk_pre = acc_dist<P>(lbk_pre, x4.w, l4.w, u4.w);
     }
-}
-
-// The abandon test after a row group (every 8 rows): the band's minimum, raised
-// by the LB_Keogh terms of the rows not yet reached (reading 6) when `tail`,
-// against the threshold.  fp32: the two LB_Keogh sums (different orders) each
-// carry at most n u relative error, and the path's remaining additions at
-// most (2n - 1) u; c covers both.
-template <int C>
-__device__ __forceinline__ bool reg4_abandons(const float (&D)[C], int n, bool tail, float lbk_total, float lbk_pre,
-                                              float thr) {
-    float mn = D[0];
-#pragma unroll
-    for (int k = 1; k < C; ++k) mn = fminf(mn, D[k]);
-    if (tail) {
-        const float c = (float)(2 * n + 2) * 5.9604645e-8f;
-        const float rest = fmaxf(0.0f, lbk_total - lbk_pre - c * lbk_total);
-        mn = fmaxf(mn, (mn + rest) * (1.0f - c));
-    }
-    return mn > thr;
 }
 
 template <int C, int P, int E>
@@ -494,10 +516,16 @@ k_dtw_reg4p(DtwJob j, int e, int wl, bool xvec) {
         float thr = kInf;
         if (alive) {
             thr = j.bsf ? load_threshold(j.bsf + q) : j.fixed_thr;
-            if (!resume && j.pair_lbi && j.pair_lbi[pi] > thr * (1.0f + j.slack)) {
+            // a pair whose LB_Improved exceeds the threshold is skipped; a
+            // resumed one, checked again against the threshold as it has
+            // fallen since, is abandoned
+            if (j.pair_lbi && j.pair_lbi[pi] > thr * (1.0f + j.slack)) {
                 j.res[pi] = kInf;
                 alive = false;
-                ++n_skip;
+                if (resume)
+                    ++n_aband;
+                else
+                    ++n_skip;
             }
         }
         if (alive && !resume) ++n_comp;
@@ -568,6 +596,156 @@ k_dtw_reg4p(DtwJob j, int e, int wl, bool xvec) {
             j.res[pi] = kInf;
         } else if (alive) {
             // completed: the last row was evaluated
+            float d = kInf;
+#pragma unroll
+            for (int k = 0; k < C; ++k) d = sel_eq(k, wl, D[k], d);
+            if (!j.bsf && d > j.fixed_thr) d = kInf;
+            j.res[pi] = j.root_out ? root_p(d, P) : d;
+            if (j.bsf) update_threshold(j.bsf, j.gmin, j.k, q, c % j.k, d);
+        }
+    }
+    if (j.counters) {
+        n_skip = __reduce_add_sync(0xffffffffu, (unsigned)n_skip);
+        n_comp = __reduce_add_sync(0xffffffffu, (unsigned)n_comp);
+        n_aband = __reduce_add_sync(0xffffffffu, (unsigned)n_aband);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            n_rows += __shfl_xor_sync(0xffffffffu, n_rows, o);
+            n_cells += __shfl_xor_sync(0xffffffffu, n_cells, o);
+        }
+        if (lane == 0) {
+            if (n_rows) atomicAdd(j.counters + CNT_DTW_ROWS, n_rows);
+            if (n_cells) atomicAdd(j.counters + CNT_DTW_CELLS, n_cells);
+            if (n_skip) atomicAdd(j.counters + CNT_DTW_SKIP, n_skip);
+            if (n_comp) atomicAdd(j.counters + CNT_DTW_COMPUTED, n_comp);
+            if (n_aband) atomicAdd(j.counters + CNT_DTW_ABANDONED, n_aband);
+            if (n_lane_rows) atomicAdd(j.counters + CNT_DTW_LANE_ROWS, n_lane_rows);
+        }
+    }
+}
+
+// The register path of bands wider than 64 slots (k_dtw_reg's rows, one per
+// step, abandon test every 8 rows) in row phases, with the continuation
+// lists, leading region and deferral of k_dtw_reg4p.
+template <int C, int P>
+__global__ void __launch_bounds__(kDtwThreads, (C <= 112 ? 3 : 2))
+k_dtw_regp(DtwJob j, int e, int wl) {
+    const int lane = threadIdx.x & 31;
+    const int n = j.n;
+    const int ylen = j.qc.ylen, padl = j.qc.padl;
+    const int wb = min(j.w, n - 1);
+    const bool resume = j.ph.in_state != nullptr;
+    const int64_t cap = j.ph.cap;
+    int64_t npairs = j.npairs;
+    if (resume) {
+        const unsigned long long c_in = *j.ph.in_count;
+        npairs = (int64_t)(c_in < (unsigned long long)cap ? c_in : (unsigned long long)cap);
+    } else if (j.npairs_dev) {
+        npairs = (int64_t)*j.npairs_dev;
+    }
+    const int64_t lead = (!resume && j.ph.lead) ? (int64_t)*j.ph.lead : 0;
+    const int r0 = j.ph.row_begin;
+    const bool tail = (P == 1 || P == 2) && j.tU != nullptr && j.abandon;
+    const unsigned long long cells0 = (unsigned long long)band_cells(r0, n, wb);
+    unsigned long long n_skip = 0, n_comp = 0, n_aband = 0, n_rows = 0, n_lane_rows = 0, n_cells = 0;
+    for (;;) {
+        unsigned long long chunk = 0;
+        if (lane == 0) chunk = atomicAdd(j.cursor, 1ull);
+        chunk = __shfl_sync(0xffffffffu, chunk, 0);
+        const int64_t p0 = (int64_t)chunk * 32;
+        if (p0 >= npairs) break;
+        const int64_t t = p0 + lane;
+        bool alive = t < npairs;
+        int64_t pi = 0;
+        int q = 0, c = 0;
+        if (alive) {
+            pi = resume ? j.ph.in_pi[t] : t;
+            const Pair pr = j.pairs[pi];
+            q = pr.q;
+            c = pr.c;
+            if (c < 0) alive = false;
+        }
+        float thr = kInf;
+        if (alive) {
+            thr = j.bsf ? load_threshold(j.bsf + q) : j.fixed_thr;
+            // a pair whose LB_Improved exceeds the threshold is skipped; a
+            // resumed one, checked again against the threshold as it has
+            // fallen since, is abandoned
+            if (j.pair_lbi && j.pair_lbi[pi] > thr * (1.0f + j.slack)) {
+                j.res[pi] = kInf;
+                alive = false;
+                if (resume)
+                    ++n_aband;
+                else
+                    ++n_skip;
+            }
+        }
+        if (alive && !resume) ++n_comp;
+        int stop = (pi < lead || j.ph.row_end >= n) ? n : j.ph.row_end;
+        const float *x = j.db + (int64_t)c * n;
+        const float *yc = j.qc.data + (int64_t)q * 4 * ylen;
+        const int64_t toff = tail ? (int64_t)q * n : 0;
+        float D[C];
+        float lbk_pre = 0.0f;
+        if (resume) {
+#pragma unroll
+            for (int k = 0; k < C; ++k) D[k] = alive ? j.ph.in_state[(int64_t)k * cap + t] : kInf;
+            lbk_pre = alive ? j.ph.in_state[(int64_t)C * cap + t] : 0.0f;
+        } else {
+#pragma unroll
+            for (int k = 0; k < C; ++k) D[k] = sel_eq(k, wl, 0.0f, kInf);  // row -1: D(-1,-1) = 0
+        }
+        bool abandoned = false;
+        int i = r0;
+        for (;;) {
+            while (__any_sync(0xffffffffu, alive && i < stop)) {
+                if (alive && i < stop) {
+                    const float xi = __ldg(x + i);
+                    if (tail) lbk_pre = acc_dist<P>(lbk_pre, xi, __ldg(j.tL + toff + i), __ldg(j.tU + toff + i));
+                    reg_row<C, P>(D, xi, yc, i, e, wl, padl, ylen);
+                    if (j.abandon && (i & 7) == 7 && i + 1 < n) {
+                        if (j.bsf) thr = load_threshold(j.bsf + q);
+                        const float lbk_total = tail ? j.res[pi] : 0.0f;
+                        if (reg4_abandons<C>(D, n, tail, lbk_total, lbk_pre, thr)) {
+                            abandoned = true;
+                            alive = false;
+                        }
+                    }
+                    ++i;
+                }
+            }
+            // pairs alive at the end of the phase move to the out list
+            const bool want = alive && stop < n;
+            const unsigned m = __ballot_sync(0xffffffffu, want);
+            if (m == 0) break;
+            unsigned long long base = 0;
+            const int leader = __ffs(m) - 1;
+            if (lane == leader) base = atomicAdd(j.ph.out_count, (unsigned long long)__popc(m));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (want) {
+                const int64_t slot = (int64_t)base + __popc(m & ((1u << lane) - 1));
+                if (slot < cap) {
+#pragma unroll
+                    for (int k = 0; k < C; ++k) j.ph.out_state[(int64_t)k * cap + slot] = D[k];
+                    j.ph.out_state[(int64_t)C * cap + slot] = lbk_pre;
+                    j.ph.out_pi[slot] = pi;
+                    alive = false;
+                } else {
+                    stop = n;  // no room: this pair runs on here
+                }
+            }
+            if (!__any_sync(0xffffffffu, alive && i < stop)) break;
+        }
+        const int rows = min(i, n);
+        if (i > r0) {
+            n_rows += (unsigned long long)(rows - r0);
+            n_cells += (unsigned long long)band_cells(rows, n, wb) - cells0;
+        }
+        n_lane_rows += 32ull * __reduce_max_sync(0xffffffffu, (unsigned)(i > r0 ? rows - r0 : 0));
+        if (abandoned) {
+            ++n_aband;
+            j.res[pi] = kInf;
+        } else if (alive) {
             float d = kInf;
 #pragma unroll
             for (int k = 0; k < C; ++k) d = sel_eq(k, wl, D[k], d);

@@ -119,12 +119,33 @@ cudaError_t launch_dtw_pt(const DtwJob &j, const DtwGeom &g, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// The row-phase thread-per-pair kernel (k_dtw_reg4p) for one launch of
-// j.ph's rows; bands of up to 64 slots on the register path only.
+// The row-phase thread-per-pair kernels for one launch of j.ph's rows:
+// k_dtw_reg4p for bands of up to 64 slots, k_dtw_regp up to 208 (the
+// register path only).
 template <int P>
 cudaError_t launch_dtw_phase_pt(const DtwJob &j, const DtwGeom &g, cudaStream_t s) {
-    if (g.wide || g.C > kDtwGroupMaxC) return cudaErrorInvalidValue;
+    if (g.wide || g.C > kDtwRegMaxC) return cudaErrorInvalidValue;
     const int64_t warps = (j.npairs + 31) / 32;
+    if (g.C > kDtwGroupMaxC) {
+        // p = 1 and 2 only: the p = 4 and infinity variants of the widest
+        // bands spill registers
+        if constexpr (P == 1 || P == 2) {
+#define DTW_REGP_CASE(CC)                                                                             \
+    case CC: {                                                                                        \
+        auto kern = k_dtw_regp<CC, P>;                                                               \
+        kern<<<launch_detail::blocks_for(kern, warps), kDtwThreads, 0, s>>>(j, g.e, g.wl);            \
+        return cudaGetLastError();                                                                    \
+    }
+            switch (g.C) {
+                DTW_REGP_CASE(80) DTW_REGP_CASE(96) DTW_REGP_CASE(112) DTW_REGP_CASE(128)
+                DTW_REGP_CASE(144) DTW_REGP_CASE(160) DTW_REGP_CASE(176) DTW_REGP_CASE(192)
+                DTW_REGP_CASE(208)
+                default: break;
+            }
+#undef DTW_REGP_CASE
+        }
+        return cudaErrorInvalidValue;
+    }
     const bool xvec = (j.n % 4 == 0) && ((reinterpret_cast<uintptr_t>(j.db) & 15) == 0);
 #define DTW_REG4P_FIXED(CC, EE)                                                                       \
     if (g.C == CC && g.e == EE) {                                                                     \

@@ -331,12 +331,15 @@ def test_knn_warp_dtw_path(api, p, n, w, k):
 
 
 @pytest.mark.parametrize("p", [1, 2])
-@pytest.mark.parametrize("n,w,k", [(256, 25, 1), (256, 25, 10), (200, 6, 3), (301, 30, 1), (130, 12, 2)])
+@pytest.mark.parametrize("n,w,k", [(256, 25, 1), (256, 25, 10), (200, 6, 3), (301, 30, 1), (130, 12, 2),
+                                   (300, 40, 1), (517, 51, 3), (400, 102, 1), (260, 100, 5)])
 def test_dtw_row_phases_equal_thread_path(api, p, n, w, k):
     # the main DTW stage in row phases of 64 rows (pairs alive at a phase's
     # end resumed by the next launch) gives the thread path's results bit
     # for bit; compile-time and runtime band paddings, n % 4 != 0 and n not a
-    # multiple of the phase; counters still add up
+    # multiple of the phase, bands of 4-rows-per-load kernels (up to 64
+    # slots) and of the wider register kernels (96 to 208 slots); counters
+    # still add up
     db = synth.random_walks(6_000, n, seed=60 + n)
     qs = synth.random_walks(40, n, seed=61 + n, stream=synth.STREAM_QUERY)
     ti, td = api.knn_search(cuda(db), cuda(qs), w, p, k, dtw_path=1)
