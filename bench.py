@@ -72,6 +72,10 @@ def parse():
     ap.add_argument("--lb-abandon", type=int, default=0,
                     help="1: early abandoning inside the LB sums (streamed rows of series longer than 256)")
     ap.add_argument("--no-p2", action="store_true", help="skip the DTW_2 side measurement")
+    ap.add_argument("--shard", choices=["queries", "candidates"], default="queries",
+                    help="N > 1: every GPU holds the database and searches its own queries (weak scaling), "
+                         "or holds a candidate range and searches every query, with the seeds' thresholds "
+                         "exchanged and the top-k lists merged (strong scaling)")
     ap.add_argument("--no-extra", action="store_true",
                     help="default workload only: skip the bounded batched and serving runs added to its line")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU baseline sample")
@@ -116,7 +120,10 @@ def workload_config(a, world):
         "N": a.N, "n": a.n, "w": a.w, "queries_per_step_per_gpu": a.Q, "p": a.p, "k": a.k,
         "data": DATA[a.data][2], "seed": a.seed,
         "l2": "flushed between timed steps (256 MiB write)",
-        "parallelism": "queries sharded over %d GPU(s), database replicated" % world,
+        "parallelism": ("candidates sharded over %d GPU(s) (thresholds all-reduced after the seeds, top-k "
+                        "lists all-gathered and merged), every query on every GPU" % world
+                        if getattr(a, "shard", "queries") == "candidates" else
+                        "queries sharded over %d GPU(s), database replicated" % world),
     }
 
 
@@ -268,10 +275,12 @@ def filter_work(a, stats):
     return scanned, pd_surv, lbk_surv
 
 
-def stage_rates(prof, a, steps, peaks, stats):
+def stage_rates(prof, a, steps, peaks, stats, prefix_runs=1):
     """Achieved rate of each timed stage against the derived fp32 ALU peak, in
     the operation counts above: the piecewise-sum / LB_Keogh tile, the filter
-    and the DTW stages (cells are the in-band cells evaluated)."""
+    and the DTW stages (cells are the in-band cells evaluated).  prefix_runs:
+    runs of the bound tile and the seeds per step (2 when the seeds'
+    thresholds are exchanged before the search)."""
     alu_peak, _ = alu_peak_tops(peaks)
     out = {}
 
@@ -280,7 +289,7 @@ def stage_rates(prof, a, steps, peaks, stats):
 
     d = a.n // 8 if a.n >= 64 else a.n
     if prof["lb_keogh"]["launches"]:
-        t = a.Q * a.N * d * term_ops(a.p) / 1e12 / (ms("lb_keogh") / 1e3)
+        t = prefix_runs * a.Q * a.N * d * term_ops(a.p) / 1e12 / (ms("lb_keogh") / 1e3)
         out["lb_keogh_tile"] = {"ms": ms("lb_keogh"), "Top_s": t, "frac_alu": t / alu_peak}
     if prof["lb_improved"]["launches"] and stats.get("candidates"):
         scanned, pd_surv, lbk_surv = filter_work(a, stats)
@@ -296,13 +305,13 @@ def stage_rates(prof, a, steps, peaks, stats):
             # belonged to a live pair (a warp steps until its longest pair ends)
             out["dtw"]["lane_use"] = stats["dtw_rows"] / stats["dtw_lane_rows"]
     if prof["seed_dtw"]["launches"] and stats.get("seed_cells"):
-        cells = stats["seed_cells"] / (ms("seed_dtw") / 1e3)
+        cells = prefix_runs * stats["seed_cells"] / (ms("seed_dtw") / 1e3)
         out["seed_dtw"] = {"ms": ms("seed_dtw"), "cells_per_s": cells,
                            "frac_alu": cells * DTW_CELL_OPS / 1e12 / alu_peak}
     return out
 
 
-def roofline(prof, a, steps, peaks, stats):
+def roofline(prof, a, steps, peaks, stats, prefix_runs=1):
     """Roofline of the dominant stage (largest device time in the timed
     region), in the operation counts above; `instruction_mix` gives the same
     rate counted as the kernel's own fp32 instructions."""
@@ -319,12 +328,14 @@ def roofline(prof, a, steps, peaks, stats):
             "traffic_note": "no DRAM counter is read in the timed run; per-kernel DRAM bytes are in the ncu summaries"}
     if dom == "lb_keogh":
         d = a.n // 8 if a.n >= 64 else a.n
-        ops = a.Q * a.N * d * term_ops(a.p) / per_call
+        ops = prefix_runs * a.Q * a.N * d * term_ops(a.p) / per_call
         achieved = ops / 1e12 / (ms / 1e3)
         return dict(base, kernel="k_lbk_tile", achieved=achieved, frac=achieved / alu_peak,
                     instruction_mix={"ops_per_term": 4, "Top_s": achieved * 4 / term_ops(a.p)})
     if dom in ("dtw", "seed_dtw"):
         cells = stats.get("dtw_cells" if dom == "dtw" else "seed_cells", 0) / per_call
+        if dom == "seed_dtw":
+            cells *= prefix_runs
         achieved = cells * DTW_CELL_OPS / 1e12 / (ms / 1e3) if cells else None
         band = 2 * min(a.w, a.n - 1) + 1
         lanes = a.dtw_path == 2 or (a.dtw_path == 0 and band > 208)
@@ -371,9 +382,15 @@ def run_ours(a):
     from paper_0811_3301_gb300 import _native as N
     from paper_0811_3301_gb300 import api
 
+    from paper_0811_3301_gb300 import shard
+
+    cand = a.shard == "candidates"
     db_h = make_series(a, a.N, synth.STREAM_DB)
-    q_h = make_series(a, a.Q, synth.STREAM_QUERY + 16 * rank)
-    db = torch.from_numpy(db_h).to(dev)
+    # query sharding: each GPU its own queries; candidate sharding: every GPU
+    # the same queries against its own candidate range
+    q_h = make_series(a, a.Q, synth.STREAM_QUERY + (0 if cand else 16 * rank))
+    c0, c1 = shard.candidate_range(a.N, world, rank) if cand else (0, a.N)
+    db = torch.from_numpy(np.ascontiguousarray(db_h[c0:c1])).to(dev)
     qs = torch.from_numpy(q_h).to(dev)
     flush = torch.empty(256 * 2**20 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
@@ -387,8 +404,15 @@ def run_ours(a):
     kw = {"seeds": a.seeds, "parts": a.parts, "dtw_path": a.dtw_path, "filter_path": a.filter_path,
           "lb_abandon": a.lb_abandon}
 
-    def step(p):
-        return api.knn_search(db, qs, a.w, p, a.k, **kw)
+    skw = {key: kw[key] for key in ("seeds", "parts", "dtw_path", "filter_path")}
+
+    def step(p, queries=None):
+        queries = qs if queries is None else queries
+        if cand:
+            return shard.sharded_knn_search(db, c0, queries, a.w, p, a.k, **kw)
+        return api.knn_search(db, queries, a.w, p, a.k, **kw)
+
+    per_step_queries = a.Q if cand else world * a.Q  # whole-job queries per step
 
     # pruning report (untimed): LB_Keogh alone vs LB_Keogh + LB_Improved
     pruning = {}
@@ -425,11 +449,15 @@ def run_ours(a):
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     ms_max = float(t.item())
-    value = world * a.Q * a.steps / (ms_max / 1e3)
+    value = per_step_queries * a.steps / (ms_max / 1e3)
     clocks = sampler.summary(t_wall0, t_wall1) if sampler else None
 
     # DTW rows evaluated per step (for the DTW roofline): one extra stats run
-    _, _, st_main = api.knn_search(db, qs, a.w, a.p, a.k, return_stats=True, **kw)
+    if cand:
+        thr = shard.exchange_thresholds(api.seed_thresholds(db, qs, a.w, a.p, a.k, **skw))
+        _, _, st_main = api.knn_search(db, qs, a.w, a.p, a.k, thr_in=thr, return_stats=True, **kw)
+    else:
+        _, _, st_main = api.knn_search(db, qs, a.w, a.p, a.k, return_stats=True, **kw)
 
     # DTW_2 side measurement (same workload, same timing method)
     p2 = None
@@ -449,7 +477,7 @@ def run_ours(a):
         t2 = torch.tensor([ms2], dtype=torch.float64, device=dev)
         if world > 1:
             dist.all_reduce(t2, op=dist.ReduceOp.MAX)
-        p2 = {"p": other, "value": world * a.Q * a.steps / (float(t2.item()) / 1e3), "unit": "queries/s",
+        p2 = {"p": other, "value": per_step_queries * a.steps / (float(t2.item()) / 1e3), "unit": "queries/s",
               "ms_per_step": float(t2.item()) / a.steps}
 
     # end to end through the public API: queries from pinned host memory,
@@ -457,20 +485,30 @@ def run_ours(a):
     q_pin = torch.from_numpy(q_h).pin_memory()
     oi = torch.empty((a.Q, a.k), dtype=torch.int64).pin_memory()
     od = torch.empty((a.Q, a.k), dtype=torch.float32).pin_memory()
+    def e2e_step():
+        if cand:
+            # the collectives take device tensors: queries in, merged lists out
+            mi, md = step(a.p, q_pin.to(dev, non_blocking=True))
+            oi.copy_(mi)
+            od.copy_(md)
+            torch.cuda.synchronize()
+        else:
+            api.knn_search(db, q_pin, a.w, a.p, a.k, out_idx=oi, out_dist=od, **kw)  # synchronous (host outputs)
+
     for _ in range(a.warmup):
-        api.knn_search(db, q_pin, a.w, a.p, a.k, out_idx=oi, out_dist=od, **kw)
+        e2e_step()
     barrier()
     e2e_s = 0.0
     for i in range(a.steps):
         flush.fill_(float(i))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        api.knn_search(db, q_pin, a.w, a.p, a.k, out_idx=oi, out_dist=od, **kw)  # synchronous (host outputs)
+        e2e_step()
         e2e_s += time.perf_counter() - t0
     te = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
     if world > 1:
         dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e = {"value": world * a.Q * a.steps / float(te.item()), "unit": "queries/s",
+    e2e = {"value": per_step_queries * a.steps / float(te.item()), "unit": "queries/s",
            "h2d_bytes_per_step": a.Q * a.n * 4, "d2h_bytes_per_step": a.Q * a.k * (8 + 4)}
 
     if sampler:
@@ -482,7 +520,14 @@ def run_ours(a):
     except (OSError, ValueError):
         pass
     launches = sum(v["launches"] for v in prof.values())
-    roof = roofline(prof, a, a.steps, peaks, st_main)
+    if cand:
+        launches += a.steps  # the merge kernel, outside the stage timers
+    # the shard's own size in candidate mode; the bound tile and the seeds run
+    # twice per step there (once for the thresholds, once in the search)
+    ar = argparse.Namespace(**vars(a))
+    ar.N = c1 - c0
+    prefix_runs = 2 if cand else 1
+    roof = roofline(prof, ar, a.steps, peaks, st_main, prefix_runs)
 
     if rank != 0:
         return None
@@ -496,12 +541,13 @@ def run_ours(a):
         extra = extra_workloads(a)
     out = {
         "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": a.steps,
-        "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True, "scaling": "weak",
+        "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True,
+        "scaling": "strong" if cand else "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic (%s)" % DATA[a.data][1],
         "config": workload_config(a, world), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": launches, "clocks": clocks, "p2": p2, "pruning": pruning,
         "stages_ms_per_step": {k: v["ms"] / a.steps for k, v in prof.items()},
-        "stage_rates": stage_rates(prof, a, a.steps, peaks, st_main),
+        "stage_rates": stage_rates(prof, ar, a.steps, peaks, st_main, prefix_runs),
         "stats_per_step": st_main,
     }
     out.update(extra)

@@ -203,6 +203,48 @@ dtw_status knn_search_ex(const float *db, int64_t N, const float *queries, int64
                          dtw_stats *stats, void *stream);
 
 /*
+ * Candidate sharding (Sec. 7-8 problem statement: the candidates of a query
+ * are independent, so the database can be split by candidate range over
+ * several GPUs or processes, each searching every query in its own shard).
+ * A shard's own seeds give each query a threshold that is at least that
+ * shard's k-th smallest DTW, and the smallest of these over the shards is at
+ * least the k-th smallest over the whole database, so every shard may prune
+ * with it: a true neighbour never exceeds it.
+ *
+ * knn_seed_thresholds runs the first stages of knn_search_ex on this shard
+ * (query envelopes, the bound of every pair, the DTW of the lowest-bound
+ * seeds) and writes thr_out[q] [Q], the k-th smallest seed DTW of query q
+ * (+INF when the shard has fewer than k seeds), in the cascade's power units:
+ * DTW_p^p for p = 1, 2, 4 and DTW_inf for p = DTW_P_INF (no root taken).
+ *
+ * knn_search_bounded is knn_search_ex with query q's threshold lowered to
+ * thr_in[q] (same units; NaN and negative values are ignored) once its seeds
+ * are done.  The result lists only the shard's candidates whose DTW does not
+ * exceed the final threshold (the rest of a list is idx -1, +INF); when
+ * thr_in is the minimum of every shard's thr_out, merging the shards' lists
+ * by (distance, index) gives the exact k nearest neighbours of the whole
+ * database.  The shards' indices are their own (0-based in the shard).
+ *
+ * knn_merge_topk merges R lists per query: idx, dist [R][Q][k_in] (device;
+ * indices below 2^31, -1 / +INF for empty entries, distances >= 0) into
+ * out_idx, out_dist [Q][k] (device), the k smallest (distance, index) per
+ * query, padded with -1 / +INF.  Asynchronous on stream.
+ *
+ * thr_out and thr_in may be host or device memory (a host thr_out makes the
+ * call synchronous); other arguments as in knn_search_ex.
+ */
+dtw_status knn_seed_thresholds(const float *db, int64_t N, const float *queries, int64_t Q,
+                               int32_t n, int32_t w, int32_t p, int32_t k,
+                               const dtw_options *opt, float *thr_out, void *stream);
+dtw_status knn_search_bounded(const float *db, int64_t N, const float *queries, int64_t Q,
+                              int32_t n, int32_t w, int32_t p, int32_t k,
+                              const dtw_options *opt, const float *thr_in, int64_t *out_idx,
+                              float *out_dist, dtw_stats *stats, void *stream);
+dtw_status knn_merge_topk(const int64_t *idx, const float *dist, int32_t R, int64_t Q,
+                          int32_t k_in, int32_t k, int64_t *out_idx, float *out_dist,
+                          void *stream);
+
+/*
  * Stage timing.  While enabled, knn_search records a pair of CUDA events on
  * its stream around each stage (stage index: DTW_STAGE_*), so that the
  * device time of each kernel is measured on the stream it runs on.

@@ -132,6 +132,10 @@ SIGNATURES = {
     "dtw_profile_read": [ctypes.c_void_p, _i32],
     "knn_search_ex": [_vp, _i64, _vp, _i64, _i32, _i32, _i32, _i32, ctypes.POINTER(Options), _vp, _vp,
                       ctypes.POINTER(Stats), _vp],
+    "knn_seed_thresholds": [_vp, _i64, _vp, _i64, _i32, _i32, _i32, _i32, ctypes.POINTER(Options), _vp, _vp],
+    "knn_search_bounded": [_vp, _i64, _vp, _i64, _i32, _i32, _i32, _i32, ctypes.POINTER(Options), _vp, _vp, _vp,
+                           ctypes.POINTER(Stats), _vp],
+    "knn_merge_topk": [_vp, _vp, _i32, _i64, _i32, _i32, _vp, _vp, _vp],
     "dtw_index_create": [_i32, ctypes.POINTER(Options), ctypes.POINTER(_vp)],
     "dtw_index_add_bucket": [_vp, _vp, _i64, _i32],
     "dtw_index_tune": [_vp, _vp, _i64, _i32, _i32, _i32, ctypes.POINTER(Tuning)],

@@ -149,11 +149,26 @@ def dtw_triangle(x: torch.Tensor, y: torch.Tensor, z: torch.Tensor, w: int, p: i
     return (ratio, d3) if with_distances else ratio
 
 
+def _knn_args(db, queries, mode, slack, seeds, parts, dtw_path, filter_path, lb_abandon):
+    db = _f32(db, "db")
+    queries = _f32(queries, "queries")
+    if queries.dim() == 1:
+        queries = queries.unsqueeze(0)
+    if db.dim() != 2 or queries.dim() != 2 or db.shape[1] != queries.shape[1]:
+        raise ValueError("db [N, n] and queries [Q, n] must share n")
+    if mode not in _MODES:
+        raise ValueError("mode must be one of %s" % sorted(_MODES))
+    opt = N.Options(_MODES[mode], float(slack), int(seeds), int(parts), int(dtw_path), int(filter_path),
+                    int(lb_abandon))
+    return db, queries, opt
+
+
 def knn_search(db: torch.Tensor, queries: torch.Tensor, w: int, p: int, k: int = 1, *, mode: str = "improved",
                slack: float = 1e-6, seeds: int = 0, parts: int = 0, dtw_path: int = 0, filter_path: int = 0,
                lb_abandon: int = 0,
                out_idx: torch.Tensor | None = None,
-               out_dist: torch.Tensor | None = None, return_stats: bool = False):
+               out_dist: torch.Tensor | None = None, return_stats: bool = False,
+               thr_in: torch.Tensor | None = None):
     """Exact k nearest neighbours of each query row under DTW_p with band w (Sec. 7-8).
 
     db [N, n] and queries [Q, n] may live on the GPU or in host memory
@@ -161,30 +176,70 @@ def knn_search(db: torch.Tensor, queries: torch.Tensor, w: int, p: int, k: int =
     dist float32 [Q, k]) ordered by (distance, index); with return_stats
     also the cascade counters.  Outputs default to the device of `queries`
     when it is a CUDA tensor, else to host memory.
+
+    thr_in (float32 [Q], power units as seed_thresholds gives them) makes
+    this the search of one shard of a candidate-sharded database
+    (knn_search_bounded): each query's threshold is lowered to thr_in, and
+    only candidates within the final threshold are listed.
     """
-    db = _f32(db, "db")
-    queries = _f32(queries, "queries")
-    if queries.dim() == 1:
-        queries = queries.unsqueeze(0)
-    if db.dim() != 2 or queries.dim() != 2 or db.shape[1] != queries.shape[1]:
-        raise ValueError("db [N, n] and queries [Q, n] must share n")
+    db, queries, opt = _knn_args(db, queries, mode, slack, seeds, parts, dtw_path, filter_path, lb_abandon)
     Q, n = queries.shape
     dev = queries.device
     if out_idx is None:
         out_idx = torch.empty((Q, k), dtype=torch.int64, device=dev, pin_memory=not queries.is_cuda and torch.cuda.is_available())
     if out_dist is None:
         out_dist = torch.empty((Q, k), dtype=torch.float32, device=dev, pin_memory=not queries.is_cuda and torch.cuda.is_available())
-    if mode not in _MODES:
-        raise ValueError("mode must be one of %s" % sorted(_MODES))
-    opt = N.Options(_MODES[mode], float(slack), int(seeds), int(parts), int(dtw_path), int(filter_path),
-                    int(lb_abandon))
     st = N.Stats()
-    N.check(N.lib.knn_search_ex(_ptr(db), db.shape[0], _ptr(queries), Q, n, int(w), int(p), int(k),
-                                ctypes.byref(opt), _ptr(out_idx), _ptr(out_dist),
-                                ctypes.byref(st) if return_stats else None, _stream()))
+    stp = ctypes.byref(st) if return_stats else None
+    if thr_in is None:
+        N.check(N.lib.knn_search_ex(_ptr(db), db.shape[0], _ptr(queries), Q, n, int(w), int(p), int(k),
+                                    ctypes.byref(opt), _ptr(out_idx), _ptr(out_dist), stp, _stream()))
+    else:
+        thr_in = _f32(thr_in, "thr_in")
+        if thr_in.shape != (Q,):
+            raise ValueError("thr_in must be [Q]")
+        N.check(N.lib.knn_search_bounded(_ptr(db), db.shape[0], _ptr(queries), Q, n, int(w), int(p), int(k),
+                                         ctypes.byref(opt), _ptr(thr_in), _ptr(out_idx), _ptr(out_dist), stp,
+                                         _stream()))
     if return_stats:
         return out_idx, out_dist, st.as_dict()
     return out_idx, out_dist
+
+
+def seed_thresholds(db: torch.Tensor, queries: torch.Tensor, w: int, p: int, k: int = 1, *,
+                    mode: str = "improved", slack: float = 1e-6, seeds: int = 0, parts: int = 0,
+                    dtw_path: int = 0, filter_path: int = 0, out: torch.Tensor | None = None) -> torch.Tensor:
+    """Each query's k-th smallest seed DTW against this shard of a
+    candidate-sharded database (knn_seed_thresholds): float32 [Q] in the
+    cascade's power units (DTW_p^p; DTW_inf for p = infinity), +inf where the
+    shard has fewer than k seeds.  The minimum over the shards is a valid
+    threshold for every shard's knn_search(..., thr_in=...)."""
+    db, queries, opt = _knn_args(db, queries, mode, slack, seeds, parts, dtw_path, filter_path, 0)
+    Q, n = queries.shape
+    if out is None:
+        out = torch.empty(Q, dtype=torch.float32, device=queries.device,
+                          pin_memory=not queries.is_cuda and torch.cuda.is_available())
+    N.check(N.lib.knn_seed_thresholds(_ptr(db), db.shape[0], _ptr(queries), Q, n, int(w), int(p), int(k),
+                                      ctypes.byref(opt), _ptr(out), _stream()))
+    return out
+
+
+def merge_topk(idx: torch.Tensor, dist: torch.Tensor, k: int):
+    """The k smallest (distance, index) per query of R per-shard lists idx,
+    dist [R, Q, k_in] (CUDA tensors; global indices below 2^31, -1 / +inf for
+    empty entries): (idx int64 [Q, k], dist float32 [Q, k]), padded with
+    -1 / +inf (knn_merge_topk)."""
+    if not (idx.is_cuda and dist.is_cuda):
+        raise ValueError("merge_topk takes CUDA tensors")
+    if idx.dim() != 3 or idx.shape != dist.shape:
+        raise ValueError("idx and dist must both be [R, Q, k_in]")
+    idx = idx.to(torch.int64).contiguous()
+    dist = dist.to(torch.float32).contiguous()
+    R, Q, kin = idx.shape
+    oi = torch.empty((Q, k), dtype=torch.int64, device=idx.device)
+    od = torch.empty((Q, k), dtype=torch.float32, device=idx.device)
+    N.check(N.lib.knn_merge_topk(_ptr(idx), _ptr(dist), R, Q, kin, int(k), _ptr(oi), _ptr(od), _stream()))
+    return oi, od
 
 
 def _i32_host(v, Q: int, name: str) -> np.ndarray:

@@ -347,9 +347,14 @@ dtw_status dtw_triangle(const float *x, const float *y, const float *z, int64_t 
     return DTW_OK;
 }
 
-dtw_status knn_search_ex(const float *db, int64_t N, const float *queries, int64_t Q, int32_t n,
-                         int32_t w, int32_t p, int32_t k, const dtw_options *opt, int64_t *out_idx,
-                         float *out_dist, dtw_stats *stats, void *stream) {
+}  // extern "C"
+
+// knn_search_ex, with per-query thresholds from other shards of the database
+// (thr_in, lowered into each query's threshold after its seeds) and/or the
+// seeds' thresholds reported (thr_out); prefix_only stops after the seeds.
+static dtw_status knn_run(const float *db, int64_t N, const float *queries, int64_t Q, int32_t n, int32_t w,
+                          int32_t p, int32_t k, const dtw_options *opt, int64_t *out_idx, float *out_dist,
+                          dtw_stats *stats, void *stream, const float *thr_in, float *thr_out, bool prefix_only) {
     g_err[0] = 0;
     dtw_status st = check_common(n, w, p);
     if (st != DTW_OK) return st;
@@ -369,18 +374,22 @@ dtw_status knn_search_ex(const float *db, int64_t N, const float *queries, int64
         return fail(DTW_ERR_INVALID_ARG, "filter_path=%d outside [0, 2]", o.filter_path);
     if (stats) memset(stats, 0, sizeof(*stats));
     if (Q == 0) return DTW_OK;
-    if (!queries || !out_idx || !out_dist || (N > 0 && !db)) return fail(DTW_ERR_INVALID_ARG, "null pointer");
+    if (!queries || (N > 0 && !db)) return fail(DTW_ERR_INVALID_ARG, "null pointer");
+    if (!prefix_only && (!out_idx || !out_dist)) return fail(DTW_ERR_INVALID_ARG, "null pointer");
+    if (prefix_only && !thr_out) return fail(DTW_ERR_INVALID_ARG, "null pointer");
     cudaStream_t s = (cudaStream_t)stream;
 
     const CascadePlan pl = make_plan(N, Q, n, w, p, k, o);
     const bool db_dev = N == 0 || is_device_ptr(db);
     const bool q_dev = is_device_ptr(queries);
-    const bool oi_dev = is_device_ptr(out_idx);
-    const bool od_dev = is_device_ptr(out_dist);
+    const bool oi_dev = prefix_only || is_device_ptr(out_idx);
+    const bool od_dev = prefix_only || is_device_ptr(out_dist);
+    const bool ti_dev = !thr_in || is_device_ptr(thr_in);
+    const bool to_dev = !thr_out || is_device_ptr(thr_out);
     const int64_t Qc = pl.Qc;
 
     struct Extra {
-        float *db, *q, *PX, *XU, *XL, *out_dist;
+        float *db, *q, *PX, *XU, *XL, *out_dist, *thr_in, *thr_out;
         int64_t *out_idx;
         unsigned long long *counters, *xmax;
     };
@@ -394,6 +403,8 @@ dtw_status knn_search_ex(const float *db, int64_t N, const float *queries, int64
         x.xmax = cv.take<unsigned long long>(1);
         x.out_idx = oi_dev ? nullptr : cv.take<int64_t>((size_t)Q * k);
         x.out_dist = od_dev ? nullptr : cv.take<float>((size_t)Q * k);
+        x.thr_in = ti_dev ? nullptr : cv.take<float>((size_t)Q);
+        x.thr_out = to_dev ? nullptr : cv.take<float>((size_t)Q);
         return carve_ws(pl, cv);
     };
     Carve sizing;
@@ -412,6 +423,12 @@ dtw_status knn_search_ex(const float *db, int64_t N, const float *queries, int64
     }
     int64_t *oidx = oi_dev ? out_idx : x.out_idx;
     float *odist = od_dev ? out_dist : x.out_dist;
+    const float *tin = thr_in;
+    if (!ti_dev) {
+        CUDA_TRY(cudaMemcpyAsync(x.thr_in, thr_in, (size_t)Q * sizeof(float), cudaMemcpyHostToDevice, s));
+        tin = x.thr_in;
+    }
+    float *tout = to_dev ? thr_out : x.thr_out;
     CUDA_TRY(cudaMemsetAsync(x.counters, 0, CNT_ALLOC * sizeof(unsigned long long), s));
     unsigned *xmax_bits = reinterpret_cast<unsigned *>(x.xmax);
     // part sums and row envelopes of the database, once per call
@@ -426,14 +443,17 @@ dtw_status knn_search_ex(const float *db, int64_t N, const float *queries, int64
                                      cudaMemcpyHostToDevice, s));
             qd = x.q;
         }
-        CUDA_TRY(cascade_run(pl, ws, dbd, x.PX, xmax_bits, x.XU, x.XL, qd, qn, oidx + q0 * k, odist + q0 * k,
-                             x.counters, s));
+        CUDA_TRY(cascade_run(pl, ws, dbd, x.PX, xmax_bits, x.XU, x.XL, qd, qn, oidx ? oidx + q0 * k : nullptr,
+                             odist ? odist + q0 * k : nullptr, x.counters, s, tin ? tin + q0 : nullptr,
+                             tout ? tout + q0 : nullptr, prefix_only));
     }
+    if (!to_dev)
+        CUDA_TRY(cudaMemcpyAsync(thr_out, x.thr_out, (size_t)Q * sizeof(float), cudaMemcpyDeviceToHost, s));
     if (!oi_dev)
         CUDA_TRY(cudaMemcpyAsync(out_idx, x.out_idx, (size_t)Q * k * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     if (!od_dev)
         CUDA_TRY(cudaMemcpyAsync(out_dist, x.out_dist, (size_t)Q * k * sizeof(float), cudaMemcpyDeviceToHost, s));
-    if (stats || !oi_dev || !od_dev) {
+    if (stats || !oi_dev || !od_dev || !to_dev) {
         // a synchronising call also reports a bounded device-side wait that
         // gave up (the outputs are then not valid)
         unsigned long long h[CNT_ALLOC];
@@ -447,10 +467,48 @@ dtw_status knn_search_ex(const float *db, int64_t N, const float *queries, int64
     return DTW_OK;
 }
 
+extern "C" {
+
+dtw_status knn_search_ex(const float *db, int64_t N, const float *queries, int64_t Q, int32_t n,
+                         int32_t w, int32_t p, int32_t k, const dtw_options *opt, int64_t *out_idx,
+                         float *out_dist, dtw_stats *stats, void *stream) {
+    return knn_run(db, N, queries, Q, n, w, p, k, opt, out_idx, out_dist, stats, stream, nullptr, nullptr, false);
+}
+
 dtw_status knn_search(const float *db, int64_t N, const float *queries, int64_t Q, int32_t n, int32_t w,
                       int32_t p, int32_t k, int64_t *out_idx, float *out_dist, dtw_stats *stats,
                       void *stream) {
     return knn_search_ex(db, N, queries, Q, n, w, p, k, nullptr, out_idx, out_dist, stats, stream);
+}
+
+dtw_status knn_seed_thresholds(const float *db, int64_t N, const float *queries, int64_t Q, int32_t n,
+                               int32_t w, int32_t p, int32_t k, const dtw_options *opt, float *thr_out,
+                               void *stream) {
+    return knn_run(db, N, queries, Q, n, w, p, k, opt, nullptr, nullptr, nullptr, stream, nullptr, thr_out, true);
+}
+
+dtw_status knn_search_bounded(const float *db, int64_t N, const float *queries, int64_t Q, int32_t n,
+                              int32_t w, int32_t p, int32_t k, const dtw_options *opt, const float *thr_in,
+                              int64_t *out_idx, float *out_dist, dtw_stats *stats, void *stream) {
+    if (!thr_in && Q > 0) {
+        g_err[0] = 0;
+        return fail(DTW_ERR_INVALID_ARG, "null pointer");
+    }
+    return knn_run(db, N, queries, Q, n, w, p, k, opt, out_idx, out_dist, stats, stream, thr_in, nullptr, false);
+}
+
+dtw_status knn_merge_topk(const int64_t *idx, const float *dist, int32_t R, int64_t Q, int32_t k_in, int32_t k,
+                          int64_t *out_idx, float *out_dist, void *stream) {
+    g_err[0] = 0;
+    if (R < 1 || k_in < 1 || k < 1 || k > DTW_MAX_K || Q < 0 || Q > INT32_MAX / 2 ||
+        (int64_t)R * k_in > INT32_MAX / 2)
+        return fail(DTW_ERR_INVALID_ARG, "R=%d, k_in=%d, k=%d, Q=%lld out of range", R, k_in, k, (long long)Q);
+    if (Q == 0) return DTW_OK;
+    if (!idx || !dist || !out_idx || !out_dist) return fail(DTW_ERR_INVALID_ARG, "null pointer");
+    if (!is_device_ptr(idx) || !is_device_ptr(dist) || !is_device_ptr(out_idx) || !is_device_ptr(out_dist))
+        return fail(DTW_ERR_INVALID_ARG, "knn_merge_topk takes device buffers");
+    CUDA_TRY(launch_merge_topk(idx, dist, R, (int)Q, k_in, k, out_idx, out_dist, (cudaStream_t)stream));
+    return DTW_OK;
 }
 
 }  // extern "C"

@@ -198,6 +198,82 @@ cudaError_t launch_finalize(const CascadeBufs &b, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------------------
+// Thresholds shared between the shards of a candidate-sharded search: each
+// query's threshold lowered to an outside value (NaN and negative values are
+// ignored), and/or copied out.  Costs are non-negative, so the fp32 bits of
+// the thresholds order like their values.
+// ---------------------------------------------------------------------------
+__global__ void k_threshold_io(uint32_t *bsf, int Q, int has_db, const float *thr_in, float *thr_out) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= Q) return;
+    uint32_t v = has_db ? bsf[q] : 0x7f800000u;
+    if (thr_in) {
+        const float t = thr_in[q] + 0.0f;  // -0 -> +0
+        if (t >= 0.0f) {
+            const uint32_t tb = __float_as_uint(t);
+            v = tb < v ? tb : v;
+        }
+    }
+    if (has_db) bsf[q] = v;
+    if (thr_out) thr_out[q] = __uint_as_float(v);
+}
+
+cudaError_t launch_threshold_io(uint32_t *bsf, int Q, bool has_db, const float *thr_in, float *thr_out,
+                                cudaStream_t s) {
+    if (Q <= 0 || (!thr_in && !thr_out)) return cudaSuccess;
+    k_threshold_io<<<(Q + 255) / 256, 256, 0, s>>>(bsf, Q, has_db ? 1 : 0, thr_in, thr_out);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Merge of per-shard top-k lists (candidate sharding): one warp per query
+// takes the k smallest (distance, index) keys among the R lists of k_in
+// entries ([R][Q][k_in], global indices, -1 / +INF empty), k rounds of a
+// warp minimum over the keys above the previous round's.
+// ---------------------------------------------------------------------------
+__global__ void k_merge_topk(const int64_t *idx, const float *dist, int R, int Q, int k_in, int k,
+                             int64_t *out_idx, float *out_dist) {
+    const int q = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (q >= Q) return;
+    const int m = R * k_in;
+    unsigned long long last = 0;
+    bool first = true;
+    for (int r = 0; r < k; ++r) {
+        unsigned long long best = ~0ull;
+        for (int e = lane; e < m; e += 32) {
+            const int sh = e / k_in, t = e - sh * k_in;
+            const int64_t at = ((int64_t)sh * Q + q) * k_in + t;
+            const int64_t c = idx[at];
+            const float d = dist[at];
+            if (c < 0 || !(d < kInf)) continue;
+            const unsigned long long v = pack_key(d + 0.0f, (int)c);
+            if ((first || v > last) && v < best) best = v;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long other = __shfl_xor_sync(0xffffffffu, best, o);
+            best = other < best ? other : best;
+        }
+        const int64_t o = (int64_t)q * k + r;
+        if (lane == 0) {
+            out_idx[o] = best == ~0ull ? -1 : (int64_t)(best & 0xffffffffull);
+            out_dist[o] = best == ~0ull ? kInf : __uint_as_float((uint32_t)(best >> 32));
+        }
+        last = best;
+        first = false;
+    }
+}
+
+cudaError_t launch_merge_topk(const int64_t *idx, const float *dist, int R, int Q, int k_in, int k,
+                              int64_t *out_idx, float *out_dist, cudaStream_t s) {
+    if (Q <= 0) return cudaSuccess;
+    const int per = 4;
+    k_merge_topk<<<(Q + per - 1) / per, 32 * per, 0, s>>>(idx, dist, R, Q, k_in, k, out_idx, out_dist);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // Group the filter's survivors by query (a counting sort): exclusive scans of
 // the per-query counts give each query its output ranges, and one CTA per
 // query moves its sub-segments there.  The DTW stage then sees runs of pairs

@@ -369,10 +369,18 @@ cudaError_t cascade_prefix(const CascadePlan &pl, const CascadeWs &l, const Casc
 
 cudaError_t cascade_run(const CascadePlan &pl, const CascadeWs &l, const float *db, const float *PX,
                         const unsigned *xmax_bits, const float *XU, const float *XL, const float *q, int qn,
-                        int64_t *out_idx, float *out_dist, unsigned long long *counters, cudaStream_t s) {
+                        int64_t *out_idx, float *out_dist, unsigned long long *counters, cudaStream_t s,
+                        const float *thr_in, float *thr_out, bool prefix_only) {
     const CascadeBufs b = cascade_bufs(pl, l, db, XU, XL, q, qn, out_idx, out_dist, counters);
     RUN_TRY(cascade_prefix(pl, l, b, PX, xmax_bits, s));
     const int64_t N = pl.N;
+    if (thr_in || thr_out) {
+        // thresholds exchanged with other shards of the database: lowered
+        // before the filter, and/or reported after the seeds
+        StageTimer tm(DTW_STAGE_SEED_KTH, s);
+        RUN_TRY(launch_threshold_io(b.bsf, qn, N > 0, thr_in, thr_out, s));
+    }
+    if (prefix_only) return cudaSuccess;
     if (N > 0) {
         {
             StageTimer tm(DTW_STAGE_LB_IMPROVED, s);

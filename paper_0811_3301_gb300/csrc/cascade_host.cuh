@@ -74,7 +74,8 @@ size_t cascade_ws_bytes(const CascadePlan &pl);
 // out_idx/out_dist [qn][k] (device).  Asynchronous on s; allocates nothing.
 cudaError_t cascade_run(const CascadePlan &pl, const CascadeWs &ws, const float *db, const float *PX,
                         const unsigned *xmax_bits, const float *XU, const float *XL, const float *q, int qn,
-                        int64_t *out_idx, float *out_dist, unsigned long long *counters, cudaStream_t s);
+                        int64_t *out_idx, float *out_dist, unsigned long long *counters, cudaStream_t s,
+                        const float *thr_in = nullptr, float *thr_out = nullptr, bool prefix_only = false);
 
 // The device buffers of one run (cascade_run's view of ws and its
 // arguments), for callers that launch stages themselves.

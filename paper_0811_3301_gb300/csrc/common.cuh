@@ -275,6 +275,14 @@ int lbi_filter_warps(int n, int w, int S, int seg_len, int p, int want = 0);
 // with the piecewise-sum pre-filter and LB_Improved on.
 bool lbi_batch_applies(int n, bool summary, bool lbi_inline);
 cudaError_t launch_finalize(const CascadeBufs &b, cudaStream_t s);
+// bsf[q] = min(bsf[q], thr_in[q]) (thr_in nullable; has_db false: no
+// database, the threshold is +INF and bsf is not touched), then thr_out[q] =
+// bsf[q] (nullable); Q thresholds, power space.
+cudaError_t launch_threshold_io(uint32_t *bsf, int Q, bool has_db, const float *thr_in, float *thr_out,
+                                cudaStream_t s);
+// The k smallest (distance, index) of R per-shard lists [R][Q][k_in] per query.
+cudaError_t launch_merge_topk(const int64_t *idx, const float *dist, int R, int Q, int k_in, int k,
+                              int64_t *out_idx, float *out_dist, cudaStream_t s);
 cudaError_t launch_group_by_query(const CascadeBufs &b, cudaStream_t s);
 
 

@@ -698,8 +698,9 @@ dtw_status tune_group(dtw_index *ix, int b, int w, int k, const float *qdev, int
         path_c.push_back(2);
         if (2 * we + 1 <= 512) path_c.push_back(3);
     }
-    if (n > 2 * kDtwPhaseRows && 2 * we + 1 <= (ix->p == 1 || ix->p == 2 ? kDtwRegMaxC : kDtwGroupMaxC))
-        path_c.push_back(4);
+    // row phases only for the bands of up to 64 slots: wider ones measured
+    // slower in phases
+    if (n > 2 * kDtwPhaseRows && 2 * we + 1 <= kDtwGroupMaxC) path_c.push_back(4);
     const std::vector<int> fw_c{0, 4, 5, 6, 7, 8};
 
     // scratch sized for the largest candidate plan

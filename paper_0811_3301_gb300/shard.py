@@ -12,8 +12,14 @@ statement), so the search shards two ways:
   and ordering by (distance, index) keeps the lower index first on ties, as
   the single-GPU search does.
 
-The collective is torch.distributed's all_gather over the caller's process
-group (NCCL between GPUs, gloo on CPU).
+  Before the bounds, the ranks exchange thresholds: each rank's seeds give
+  every query a threshold at least that rank's k-th smallest DTW, and their
+  minimum (an all-reduce) is at least the k-th smallest over the whole
+  database, so every rank prunes with the tightest one and still keeps every
+  true neighbour.
+
+The collectives are torch.distributed's all_reduce and all_gather over the
+caller's process group (NCCL between GPUs, gloo on CPU).
 """
 
 from __future__ import annotations
@@ -55,30 +61,58 @@ def merge_topk(idx: np.ndarray, dist: np.ndarray, k: int) -> tuple[np.ndarray, n
     return out_i, out_d
 
 
+def exchange_thresholds(thr, group=None):
+    """Every rank's per-query thresholds [Q] (torch tensor) replaced, in
+    place, by their minimum over the ranks of the group; returned."""
+    import torch.distributed as dist
+
+    if dist.is_initialized() and dist.get_world_size(group) > 1:
+        dist.all_reduce(thr, op=dist.ReduceOp.MIN, group=group)
+    return thr
+
+
 def gather_merge(local_idx, local_dist, k: int, group=None):
     """All-gathers every rank's [Q][k] top-k (torch tensors with global indices)
-    and returns the merged exact top-k on every rank (same device as input)."""
+    and returns the merged exact top-k on every rank (same device as input):
+    on the GPU by the library's merge kernel, for host tensors (ranks
+    without a GPU) by merge_topk above."""
     import torch
     import torch.distributed as dist
 
-    world = dist.get_world_size(group)
+    world = dist.get_world_size(group) if dist.is_initialized() else 1
     gi = [torch.empty_like(local_idx) for _ in range(world)]
     gd = [torch.empty_like(local_dist) for _ in range(world)]
-    dist.all_gather(gi, local_idx.contiguous(), group=group)
-    dist.all_gather(gd, local_dist.contiguous(), group=group)
-    idx = np.stack([t.cpu().numpy() for t in gi])
-    dd = np.stack([t.cpu().numpy() for t in gd])
+    if world > 1:
+        dist.all_gather(gi, local_idx.contiguous(), group=group)
+        dist.all_gather(gd, local_dist.contiguous(), group=group)
+    else:
+        gi, gd = [local_idx.contiguous()], [local_dist.contiguous()]
+    if local_idx.is_cuda:
+        from . import api
+
+        return api.merge_topk(torch.stack(gi), torch.stack(gd), k)
+    idx = np.stack([t.numpy() for t in gi])
+    dd = np.stack([t.numpy() for t in gd])
     mi, md = merge_topk(idx, dd, k)
-    return (torch.from_numpy(mi).to(local_idx.device), torch.from_numpy(md).to(local_dist.device))
+    return torch.from_numpy(mi), torch.from_numpy(md)
 
 
-def sharded_knn_search(db_shard, offset: int, queries, w: int, p: int, k: int, group=None, **kw):
+def sharded_knn_search(db_shard, offset: int, queries, w: int, p: int, k: int, group=None, exchange: bool = True,
+                       **kw):
     """knn_search over this rank's candidate range (db_shard = rows
-    [offset, offset + len)), then the exact global top-k by gather_merge."""
+    [offset, offset + len)), then the exact global top-k by gather_merge.
+    With exchange, the ranks first share their seeds' thresholds
+    (seed_thresholds, exchange_thresholds) and every rank searches with the
+    tightest (knn_search(..., thr_in=...))."""
     import torch
 
     from . import api
 
-    idx, dd = api.knn_search(db_shard, queries, w, p, k, **kw)
+    if exchange:
+        skw = {key: v for key, v in kw.items() if key in ("mode", "slack", "seeds", "parts", "dtw_path", "filter_path")}
+        thr = exchange_thresholds(api.seed_thresholds(db_shard, queries, w, p, k, **skw), group)
+        idx, dd = api.knn_search(db_shard, queries, w, p, k, thr_in=thr, **kw)
+    else:
+        idx, dd = api.knn_search(db_shard, queries, w, p, k, **kw)
     idx = torch.where(idx >= 0, idx + int(offset), idx)
     return gather_merge(idx, dd, k, group=group)

@@ -81,3 +81,56 @@ def test_candidate_sharding_over_two_gloo_ranks_equals_the_full_search():
     ri, rd = oracle.knn_bruteforce(db, qs, 4, 1, 6)
     np.testing.assert_array_equal(mi, ri)
     np.testing.assert_allclose(md, rd.astype(np.float32), rtol=0, atol=0)
+
+
+def _rank_exchange_main(rank, world, port, out_path):
+    # each rank: a stand-in for its seeds' threshold (the k-th smallest DTW
+    # of its first 20 candidates, by the oracle), the all-reduce minimum over
+    # the ranks, then its range's top-k restricted to that threshold (what
+    # the bounded GPU search lists), and the merge
+    import torch.distributed as dist
+
+    from paper_0811_3301_gb300 import shard
+
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        db = synth.random_walks(601, 48, seed=45)
+        qs = synth.random_walks(5, 48, seed=45, stream=synth.STREAM_QUERY)
+        w, p, k = 4, 2, 6
+        a, b = shard.candidate_range(db.shape[0], world, rank)
+        seeds = np.array([[oracle.dtw(db[a + c], q, w, p) for c in range(20)] for q in qs])
+        kth = np.sort(seeds, axis=1)[:, k - 1]
+        t32 = kth.astype(np.float32)
+        t32 = np.where(t32.astype(np.float64) < kth, np.nextafter(t32, np.float32(np.inf)), t32)  # round up
+        thr = torch.from_numpy(t32)
+        mine = thr.clone()
+        shard.exchange_thresholds(thr)
+        li, ld = oracle.knn_bruteforce(db[a:b], qs, w, p, k)
+        cut = ld > thr.numpy()[:, None].astype(np.float64)
+        li = np.where(cut | (li < 0), -1, li + a)
+        ld = np.where(cut, np.inf, ld)
+        mi, md = shard.gather_merge(torch.from_numpy(li), torch.from_numpy(ld.astype(np.float32)), k)
+        if rank == 0:
+            np.savez(out_path, idx=mi.numpy(), dist=md.numpy(), thr=thr.numpy(), mine=mine.numpy())
+    finally:
+        dist.destroy_process_group()
+
+
+def test_threshold_exchange_over_two_gloo_ranks_keeps_the_exact_result():
+    import torch.multiprocessing as mp
+
+    port = 31500 + (os.getpid() % 2000)
+    with tempfile.TemporaryDirectory() as d:
+        out = os.path.join(d, "merged.npz")
+        mp.spawn(_rank_exchange_main, args=(2, port, out), nprocs=2, join=True)
+        r = np.load(out)
+    db = synth.random_walks(601, 48, seed=45)
+    qs = synth.random_walks(5, 48, seed=45, stream=synth.STREAM_QUERY)
+    ri, rd = oracle.knn_bruteforce(db, qs, 4, 2, 6)
+    np.testing.assert_array_equal(r["idx"], ri)
+    np.testing.assert_allclose(r["dist"], rd.astype(np.float32), rtol=0, atol=0)
+    # the exchanged threshold is the smaller one, and bounds the true k-th
+    assert (r["thr"] <= r["mine"]).all()
+    assert (r["thr"].astype(np.float64) >= rd[:, -1].astype(np.float32)).all()
