@@ -118,6 +118,44 @@ __device__ __forceinline__ void reg_row(float (&D)[C], float xi, const float *__
     dtw_cells_from<16, C, P>(D, xi, yb);
 }
 
+__device__ __forceinline__ float f4_at(const float4 &v, int c) {
+    return c == 0 ? v.x : (c == 1 ? v.y : (c == 2 ? v.z : v.w));
+}
+
+// Rows i and i + 1 of the register path for a compile-time bottom padding E,
+// skewed by one slot: row i's slot K + 1 and row i + 1's slot K are the same
+// column, so one query value serves both, and the two rows' chains (each cell
+// waits on the one below it) run side by side instead of one after the
+// other.  Each cell takes the operands of the one-row order, so the values
+// are bit-identical to two calls of reg_row.  Reads the query window of row
+// i up to slot C + 3 (row i + 1's last slot and the rest of its 16-byte
+// piece), which the copies' right padding holds.
+template <int C, int P, int E>
+__device__ __forceinline__ void reg_rows2(float (&D)[C], float x0, float x1, const float *__restrict__ yc, int i,
+                                          int wl, int padl, int ylen) {
+    static_assert(E >= 0 && E < 16 && C % 16 == 0, "bottom padding below 16, C a multiple of 16");
+    const int a = i - wl + padl;
+    const int r = a & 3;
+    const float4 *yb = reinterpret_cast<const float4 *>(yc + r * ylen + (a - r));
+    float4 ch = __ldg(yb + (E >> 2));
+    float a_k = dtw_cost<P>(x0 - f4_at(ch, E & 3), min3f(D[E], (E + 1 < C) ? D[(E + 1 < C) ? E + 1 : E] : kInf, kInf));
+    float b_prev = kInf;
+#pragma unroll
+    for (int K = E; K < C; ++K) {
+        if (((K + 1) & 3) == 0) ch = __ldg(yb + ((K + 1) >> 2));
+        const float yv = f4_at(ch, (K + 1) & 3);
+        float a_next = kInf;
+        if (K + 1 < C) {
+            const float up = (K + 2 < C) ? D[(K + 2 < C) ? K + 2 : K] : kInf;
+            a_next = dtw_cost<P>(x0 - yv, min3f(D[(K + 1 < C) ? K + 1 : K], up, a_k));
+        }
+        const float b_k = dtw_cost<P>(x1 - yv, min3f(a_k, a_next, b_prev));
+        D[K] = b_k;
+        b_prev = b_k;
+        a_k = a_next;
+    }
+}
+
 // The abandon test after a row group (every 8 rows): the band's minimum, raised
 // by the LB_Keogh terms of the rows not yet reached (reading 6) when `tail`,
 // against the threshold.  fp32: the two LB_Keogh sums (different orders) each
@@ -148,7 +186,7 @@ __device__ __forceinline__ bool reg4_abandons(const float (&D)[C], int n, bool t
 // when the 32 lanes of a warp share a query these are broadcasts.
 // Pairs are taken 32 at a time from a global cursor (persistent grid).
 // ---------------------------------------------------------------------------
-template <int C, int P>
+template <int C, int P, int E>
 __global__ void __launch_bounds__(kDtwThreads)
 k_dtw_reg(DtwJob j, int e, int wl) {
     const int lane = threadIdx.x & 31;
@@ -193,7 +231,28 @@ k_dtw_reg(DtwJob j, int e, int wl) {
         for (int k = 0; k < C; ++k) D[k] = sel_eq(k, wl, 0.0f, kInf);  // row -1: D(-1,-1) = 0
         bool abandoned = false;
         int rows = n;
-        for (int i = 0; i < n; ++i) {
+        int i = 0;
+        if constexpr (E >= 0) {
+            // two rows per step (reg_rows2), the abandon test after the same rows
+            for (; i + 1 < n; i += 2) {
+                const float x0 = __ldg(x + i), x1 = __ldg(x + i + 1);
+                if (tail) {
+                    lbk_pre = acc_dist<P>(lbk_pre, x0, __ldg(j.tL + toff + i), __ldg(j.tU + toff + i));
+                    lbk_pre = acc_dist<P>(lbk_pre, x1, __ldg(j.tL + toff + i + 1), __ldg(j.tU + toff + i + 1));
+                }
+                reg_rows2<C, P, E>(D, x0, x1, yc, i, wl, padl, ylen);
+                if (j.abandon && ((i + 1) & 7) == 7 && i + 2 < n) {
+                    if (j.bsf) thr = load_threshold(j.bsf + q);
+                    const float lbk_total = tail ? j.res[pi] : 0.0f;
+                    if (reg4_abandons<C>(D, n, tail, lbk_total, lbk_pre, thr)) {
+                        abandoned = true;
+                        rows = i + 2;
+                        break;
+                    }
+                }
+            }
+        }
+        for (; !abandoned && i < n; ++i) {
             const float xi = __ldg(x + i);
             if (tail) lbk_pre = acc_dist<P>(lbk_pre, xi, __ldg(j.tL + toff + i), __ldg(j.tU + toff + i));
             reg_row<C, P>(D, xi, yc, i, e, wl, padl, ylen);
@@ -464,7 +523,8 @@ k_dtw_reg4(DtwJob j, int e, int wl, bool xvec) {
 // Register path in row phases (C <= 64): the rows, cells, abandon test and
 // results of k_dtw_reg4, but one launch evaluates only rows
 // [row_begin, row_end) of its pairs.  A pair still alive at row_end (< n) is
-// deferred: its band (C slots) and LB_Keogh prefix are written to the out
+// deferred: its band (the slots from e up; those below e are +INF padding)
+// and LB_Keogh prefix are written to the out
 // list, 32 consecutive pairs of a warp to consecutive entries, and the next
 // launch resumes it from there.  A warp thus steps only until the longest of
 // its pairs ends within the phase, and the next phase's warps are full again
@@ -493,6 +553,7 @@ k_dtw_reg4p(DtwJob j, int e, int wl, bool xvec) {
     }
     const int64_t lead = (!resume && j.ph.lead) ? (int64_t)*j.ph.lead : 0;
     const int r0 = j.ph.row_begin;
+    const int elo = E >= 0 ? E : e;  // lowest band slot
     const bool tail = (P == 1 || P == 2) && j.tU != nullptr && j.abandon;
     const unsigned long long cells0 = (unsigned long long)band_cells(r0, n, wb);
     unsigned long long n_skip = 0, n_comp = 0, n_aband = 0, n_rows = 0, n_lane_rows = 0, n_cells = 0;
@@ -540,7 +601,8 @@ k_dtw_reg4p(DtwJob j, int e, int wl, bool xvec) {
         float lbk_pre = 0.0f;
         if (resume) {
 #pragma unroll
-            for (int k = 0; k < C; ++k) D[k] = alive ? j.ph.in_state[(int64_t)k * cap + t] : kInf;
+            for (int k = 0; k < C; ++k)  // the padding slots below e stay +INF and are not stored
+                D[k] = (alive && k >= elo) ? j.ph.in_state[(int64_t)k * cap + t] : kInf;
             lbk_pre = alive ? j.ph.in_state[(int64_t)C * cap + t] : 0.0f;
         } else {
 #pragma unroll
@@ -574,7 +636,8 @@ k_dtw_reg4p(DtwJob j, int e, int wl, bool xvec) {
                 const int64_t slot = (int64_t)base + __popc(m & ((1u << lane) - 1));
                 if (slot < cap) {
 #pragma unroll
-                    for (int k = 0; k < C; ++k) j.ph.out_state[(int64_t)k * cap + slot] = D[k];
+                    for (int k = 0; k < C; ++k)
+                        if (k >= elo) j.ph.out_state[(int64_t)k * cap + slot] = D[k];
                     j.ph.out_state[(int64_t)C * cap + slot] = lbk_pre;
                     j.ph.out_pi[slot] = pi;
                     deferred = true;
@@ -645,6 +708,7 @@ k_dtw_regp(DtwJob j, int e, int wl) {
     }
     const int64_t lead = (!resume && j.ph.lead) ? (int64_t)*j.ph.lead : 0;
     const int r0 = j.ph.row_begin;
+    const int elo = e;  // lowest band slot
     const bool tail = (P == 1 || P == 2) && j.tU != nullptr && j.abandon;
     const unsigned long long cells0 = (unsigned long long)band_cells(r0, n, wb);
     unsigned long long n_skip = 0, n_comp = 0, n_aband = 0, n_rows = 0, n_lane_rows = 0, n_cells = 0;
@@ -689,7 +753,8 @@ k_dtw_regp(DtwJob j, int e, int wl) {
         float lbk_pre = 0.0f;
         if (resume) {
 #pragma unroll
-            for (int k = 0; k < C; ++k) D[k] = alive ? j.ph.in_state[(int64_t)k * cap + t] : kInf;
+            for (int k = 0; k < C; ++k)  // the padding slots below e stay +INF and are not stored
+                D[k] = (alive && k >= elo) ? j.ph.in_state[(int64_t)k * cap + t] : kInf;
             lbk_pre = alive ? j.ph.in_state[(int64_t)C * cap + t] : 0.0f;
         } else {
 #pragma unroll
@@ -726,7 +791,8 @@ k_dtw_regp(DtwJob j, int e, int wl) {
                 const int64_t slot = (int64_t)base + __popc(m & ((1u << lane) - 1));
                 if (slot < cap) {
 #pragma unroll
-                    for (int k = 0; k < C; ++k) j.ph.out_state[(int64_t)k * cap + slot] = D[k];
+                    for (int k = 0; k < C; ++k)
+                        if (k >= elo) j.ph.out_state[(int64_t)k * cap + slot] = D[k];
                     j.ph.out_state[(int64_t)C * cap + slot] = lbk_pre;
                     j.ph.out_pi[slot] = pi;
                     alive = false;

@@ -88,9 +88,20 @@ cudaError_t launch_dtw_pt(const DtwJob &j, const DtwGeom &g, cudaStream_t s) {
 #undef DTW_REG4_CASE
     } else if (!g.wide) {
         const int64_t warps = (j.npairs + 31) / 32;
+        // bands of 10 % of the bucket lengths 724 ... 1448 get a compile-time
+        // bottom padding and two rows per step: (C, e) = (80, 7) w = 36,
+        // (112, 9) w = 51, (160, 15) w = 72, (208, 3) w = 102
+#define DTW_REG_FIXED(CC, EE)                                                         \
+    if (g.C == CC && g.e == EE) {                                                     \
+        auto kern = k_dtw_reg<CC, P, EE>;                                            \
+        kern<<<launch_detail::blocks_for(kern, warps), kDtwThreads, 0, s>>>(j, g.e, g.wl);           \
+        return cudaGetLastError();                                                    \
+    }
+        DTW_REG_FIXED(80, 7) DTW_REG_FIXED(112, 9) DTW_REG_FIXED(160, 15) DTW_REG_FIXED(208, 3)
+#undef DTW_REG_FIXED
 #define DTW_REG_CASE(CC)                                                              \
     case CC: {                                                                        \
-        auto kern = k_dtw_reg<CC, P>;                                                \
+        auto kern = k_dtw_reg<CC, P, -1>;                                            \
         kern<<<launch_detail::blocks_for(kern, warps), kDtwThreads, 0, s>>>(j, g.e, g.wl);           \
         break;                                                                        \
     }
