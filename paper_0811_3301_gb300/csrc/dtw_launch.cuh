@@ -4,14 +4,46 @@
 // units (dtw_p*.cu, dtw_lanes_p*.cu) so that they compile in parallel.
 #pragma once
 #include "dtw_lanes.cuh"
+#include "dtw_wave.cuh"
 
 namespace dtwk {
+
+namespace launch_detail {
+template <typename K>
+int blocks_for(K kernel, int64_t warps_needed) {
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kDtwThreads, 0);
+    if (per_sm < 1) per_sm = 1;
+    int64_t full = (int64_t)per_sm * device_sm_count();
+    int64_t need = (warps_needed + (kDtwThreads / 32) - 1) / (kDtwThreads / 32);
+    if (need < 1) need = 1;
+    return (int)(need < full ? need : full);
+}
+}  // namespace launch_detail
 
 template <int P>
 cudaError_t launch_dtw_lanes_pt(const DtwJob &j, const DtwGeom &g, LanesShape ls, cudaStream_t s) {
     if (j.npairs <= 0) return cudaSuccess;
     const int n = j.n;
     const int w = j.w < n - 1 ? j.w : n - 1;
+    // bands of 10 % of 1448 and of 20 % (or 10 % of 2048): the one-row-per-step
+    // wavefront (dtw_wave.cuh), one pair per 32 lanes, compile-time padding;
+    // lanes == 2 (two 16-lane groups per warp) keeps the two-steps-per-row kernel
+    if (j.lanes != 2) {
+        const int bw = 2 * w + 1;
+#define DTW_WAVE_CASE(CC, GG, EE)                                                                 \
+    if (bw + (EE) == (CC) * (GG)) {                                                               \
+        const int wl = w + (EE);                                                                  \
+        /* query-copy indices read: padl - wl (row 0, slot 0) .. padl + n - 1 + w */             \
+        if (g.padl < wl || (int64_t)g.padl + n + w > (int64_t)j.qc.ylen) return cudaErrorInvalidValue; \
+        auto kern = k_dtw_wave<CC, GG, P, EE>;                                                    \
+        const int64_t warps = (j.npairs + (32 / (GG)) - 1) / (32 / (GG));                         \
+        kern<<<launch_detail::blocks_for(kern, warps), kDtwThreads, 0, s>>>(j);                   \
+        return cudaGetLastError();                                                                \
+    }
+        DTW_WAVE_CASE(13, 32, 7) DTW_WAVE_CASE(10, 32, 31)
+#undef DTW_WAVE_CASE
+    }
     // every query-copy index the lanes read: padl - w >= 0 (row 0, slot 0) up to
     // padl + n - 1 + w + cl - 1 (row n-1, top slot of the band's last lane)
     if (g.padl < w || (int64_t)g.padl + n + w + ls.cl > (int64_t)j.qc.ylen || 2 * w + 1 > ls.g * ls.cl)
@@ -40,18 +72,7 @@ cudaError_t launch_dtw_lanes_pt(const DtwJob &j, const DtwGeom &g, LanesShape ls
 }
 
 
-namespace launch_detail {
-template <typename K>
-int blocks_for(K kernel, int64_t warps_needed) {
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kDtwThreads, 0);
-    if (per_sm < 1) per_sm = 1;
-    int64_t full = (int64_t)per_sm * device_sm_count();
-    int64_t need = (warps_needed + (kDtwThreads / 32) - 1) / (kDtwThreads / 32);
-    if (need < 1) need = 1;
-    return (int)(need < full ? need : full);
-}
-}  // namespace launch_detail
+
 
 template <int P>
 cudaError_t launch_dtw_pt(const DtwJob &j, const DtwGeom &g, cudaStream_t s) {

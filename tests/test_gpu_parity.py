@@ -309,15 +309,20 @@ def test_knn_seed_count(api, seeds):
 
 
 WARP_CASES = [(1, 0, 3), (33, 0, 1), (40, 3, 2), (96, 9, 1), (128, 12, 10), (256, 25, 1), (512, 51, 3),
-              (1024, 102, 1), (700, 150, 2), (1024, 204, 1), (900, 400, 1)]
+              (1024, 102, 1), (700, 150, 2), (1024, 204, 1), (900, 400, 1),
+              # the one-row-per-step wavefront's bands (409 and 289 slots)
+              (2048, 204, 3), (1448, 144, 2), (300, 144, 1), (230, 204, 4)]
 
 
 @pytest.mark.parametrize("p", [1, 2])
 @pytest.mark.parametrize("n,w,k", WARP_CASES)
 def test_knn_warp_dtw_path(api, p, n, w, k):
-    # one warp per pair (two pairs per warp, wavefront abandoning) for every
+    # one warp per pair (the one-row-per-step wavefront for bands of 409 and
+    # 289 slots, else two pairs per warp; wavefront abandoning) for every
     # DTW stage; the thread-per-pair kernels evaluate the same cells with the
-    # same fp32 operations, so both paths give identical results
+    # same fp32 operations, so both paths give identical results (bands
+    # wider than 208 slots: the wavefront against the two-steps-per-row
+    # kernel of dtw_path 3)
     N = 400 if n >= 512 else 900
     db = synth.random_walks(N, n, seed=30 + n)
     qs = synth.random_walks(4, n, seed=30 + n, stream=synth.STREAM_QUERY)
