@@ -27,6 +27,8 @@ sample of the same workload.
 from __future__ import annotations
 
 import argparse
+import contextlib
+import gc
 import json
 import math
 import os
@@ -111,6 +113,20 @@ DATA = {  # workload label, short description, description for the config
 def make_series(a, count, stream):
     gen = synth.shapes if a.data == "shapes" else synth.random_walks
     return gen(count, a.n, seed=a.seed, stream=stream)
+
+
+@contextlib.contextmanager
+def no_gc():
+    """Host-timed loops run with Python's garbage collector paused, so that a
+    collection does not land inside one step's wall time."""
+    was = gc.isenabled()
+    gc.collect()
+    gc.disable()
+    try:
+        yield
+    finally:
+        if was:
+            gc.enable()
 
 
 def workload_config(a, world):
@@ -499,17 +515,21 @@ def run_ours(a):
         e2e_step()
     barrier()
     e2e_s = 0.0
-    for i in range(a.steps):
-        flush.fill_(float(i))
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        e2e_step()
-        e2e_s += time.perf_counter() - t0
+    e2e_steps = []
+    with no_gc():
+        for i in range(a.steps):
+            flush.fill_(float(i))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            e2e_step()
+            e2e_steps.append(time.perf_counter() - t0)
+            e2e_s += e2e_steps[-1]
     te = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
     if world > 1:
         dist.all_reduce(te, op=dist.ReduceOp.MAX)
     e2e = {"value": per_step_queries * a.steps / float(te.item()), "unit": "queries/s",
-           "h2d_bytes_per_step": a.Q * a.n * 4, "d2h_bytes_per_step": a.Q * a.k * (8 + 4)}
+           "h2d_bytes_per_step": a.Q * a.n * 4, "d2h_bytes_per_step": a.Q * a.k * (8 + 4),
+           "step_ms_median": float(np.median(e2e_steps)) * 1e3, "step_ms_max": max(e2e_steps) * 1e3}
 
     if sampler:
         sampler.stop()
@@ -666,12 +686,13 @@ def run_batched(a):
         for _ in range(a.warmup):
             ix.search_flat(fpin, lens, ws, k, graph=True, out_idx=oi_h, out_dist=od_h)
         e2e_s = 0.0
-        for i in range(a.steps):
-            flush.fill_(float(i))
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            ix.search_flat(fpin, lens, ws, k, graph=True, out_idx=oi_h, out_dist=od_h)
-            e2e_s += time.perf_counter() - t0
+        with no_gc():
+            for i in range(a.steps):
+                flush.fill_(float(i))
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                ix.search_flat(fpin, lens, ws, k, graph=True, out_idx=oi_h, out_dist=od_h)
+                e2e_s += time.perf_counter() - t0
         _, _, st = ix.search_flat(flat, lens, ws, k, return_stats=True)
         tuning = {int(n): ix.get_tuning(int(n), int(n) // 10, k) for n in buckets}
         per_k[k] = {"arms": arms, "autotune_seconds": tune_s, "tuning": tuning, "stats": st,
