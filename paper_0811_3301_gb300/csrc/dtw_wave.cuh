@@ -23,6 +23,9 @@
 // never feed the band: one register per row is reset as the window slides.  Pairs start at block boundaries (every CL steps, one
 // compile-time rotation of the window registers per step).
 //
+// Each lane's next two rows' x values and new window values are in flight
+// while it computes the current one (one row ahead left the loads exposed).
+//
 // Abandoning: after each block, the group's wavefront (each lane's last row
 // of the current pair; the row -1 values for lanes that have not reached it)
 // is a cut that every warping path crosses: within a row a path moves to
@@ -65,7 +68,8 @@ __global__ void __launch_bounds__(kDtwThreads, 4) k_dtw_wave(DtwJob j) {
         yw[u] = 0.0f;
     }
     float last = kInf;         // this lane's last slot of its latest row (for lane l + 1)
-    float nx = 0.0f, ny = 0.0f;  // the next row's x value and new window value
+    float nx = 0.0f, ny = 0.0f;    // the next row's x value and new window value
+    float nx2 = 0.0f, ny2 = 0.0f;  // the row after it
     const float *xr = j.db, *yr = j.qc.data;  // the pair this lane steps
     int64_t mpi = -1;                          // its pair index
     int T = kIdle;                             // the step of its row 0
@@ -166,6 +170,10 @@ __global__ void __launch_bounds__(kDtwThreads, 4) k_dtw_wave(DtwJob j) {
                 yw[(u + (R)) % CL] = (u < kPadCells && part_lane) ? kInf : __ldg(yr + (k0 + u - wl));         \
             nx = __ldg(xr);                                                                                   \
             ny = __ldg(yr + (k0 + CL - 1 - wl));                                                              \
+            if (n > 1) {                                                                                      \
+                nx2 = __ldg(xr + 1);                                                                          \
+                ny2 = __ldg(yr + (1 + k0 + CL - 1 - wl));                                                     \
+            }                                                                                                 \
         }                                                                                                     \
         const int r = ts - T;                                                                                 \
         const bool due = !pad_lane && r >= 0 && r < n;                                                        \
@@ -177,9 +185,11 @@ __global__ void __launch_bounds__(kDtwThreads, 4) k_dtw_wave(DtwJob j) {
             /* the padding slot just below the band: a +INF window value makes its cells +INF */             \
             if (kPadCells > 0 && part_lane) yw[(kPadCells - 1 + (R)) % CL] = kInf;                            \
             xi = nx;                                                                                          \
-            if (r + 1 < n) {                                                                                  \
-                nx = __ldg(xr + r + 1);                                                                       \
-                ny = __ldg(yr + (r + 1 - wl + k0 + CL - 1));                                                  \
+            nx = nx2;                                                                                         \
+            ny = ny2;                                                                                         \
+            if (r + 2 < n) {                                                                                  \
+                nx2 = __ldg(xr + r + 2);                                                                      \
+                ny2 = __ldg(yr + (r + 2 - wl + k0 + CL - 1));                                                 \
             }                                                                                                 \
             const float c0 = dtw_cost<P>(xi - yw[(R) % CL], min3f(D[0], D[1], left));                       \
             D[0] = c0;                                                                                        \
