@@ -133,12 +133,138 @@ k_envelope_rows(const float *__restrict__ y, int64_t count, int n, int w, float 
     }
 }
 
+// Many rows with windows at least as long as a lane's run of outputs: one
+// warp per row, the row in shared memory (one padding word per 32 so that
+// the lanes' strided reads fall in distinct banks).  Lane l takes the MT
+// consecutive outputs [s, e), s = l MT.  Every one of their windows holds the
+// common span [max(0, e-1-w), min(n-1, s+w)] (2w + 1 >= MT); the output i
+// adds the elements of its own window left of the span (one more per step
+// from e-1 down to s) and right of it (one more per step from s up), so a
+// lane reads 2w + MT elements for MT outputs instead of a table per level.
+// Min and max do not round: the values are the definition's.
+__device__ __forceinline__ int env_pad(int i) { return i + (i >> 5); }
+
+template <int MT>
+__global__ void __launch_bounds__(kEnvWarps * 32)
+k_envelope_runs(const float *__restrict__ y, int64_t count, int n, int w, float *__restrict__ U,
+                float *__restrict__ L, bool vec) {
+    extern __shared__ float sm[];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t row = (int64_t)blockIdx.x * kEnvWarps + wid;
+    if (row >= count) return;
+    float *xs = sm + (size_t)wid * (n + (n >> 5) + 1);
+    const float *yr = y + row * (int64_t)n;
+    if (vec) {
+        for (int i = 4 * lane; i < n; i += 128) {
+            const float4 v = __ldg(reinterpret_cast<const float4 *>(yr + i));
+            xs[env_pad(i)] = v.x;
+            xs[env_pad(i + 1)] = v.y;
+            xs[env_pad(i + 2)] = v.z;
+            xs[env_pad(i + 3)] = v.w;
+        }
+    } else {
+        for (int i = lane; i < n; i += 32) xs[env_pad(i)] = __ldg(yr + i);
+    }
+    __syncwarp();
+    const int s0 = lane * MT;
+    if (s0 < n) {
+        const int e = min(s0 + MT, n);
+        const int lo = max(0, e - 1 - w), hi = min(n - 1, s0 + w);
+        float cx = -kInf, cn = kInf;
+        int k = lo;
+        for (; k + 1 <= hi; k += 2) {
+            const float a = xs[env_pad(k)], b = xs[env_pad(k + 1)];
+            cx = max3f(cx, a, b);
+            cn = min3f(cn, a, b);
+        }
+        if (k <= hi) {
+            const float a = xs[env_pad(k)];
+            cx = fmaxf(cx, a);
+            cn = fminf(cn, a);
+        }
+        float ux[MT], ln[MT];
+        // right of the span: x[s0 + w + 1 .. i + w]
+        float rx = -kInf, rn = kInf;
+#pragma unroll
+        for (int m = 0; m < MT; ++m) {
+            const int j = s0 + m + w;
+            if (m > 0 && j <= n - 1) {
+                const float v = xs[env_pad(j)];
+                rx = fmaxf(rx, v);
+                rn = fminf(rn, v);
+            }
+            ux[m] = fmaxf(cx, rx);
+            ln[m] = fminf(cn, rn);
+        }
+        // left of the span: x[i - w .. e - 2 - w]
+        float lx = -kInf, lnn = kInf;
+#pragma unroll
+        for (int m = MT - 1; m >= 0; --m) {
+            const int i = s0 + m;
+            if (i < e - 1 && i - w >= 0) {
+                const float v = xs[env_pad(i - w)];
+                lx = fmaxf(lx, v);
+                lnn = fminf(lnn, v);
+            }
+            ux[m] = fmaxf(ux[m], lx);
+            ln[m] = fminf(ln[m], lnn);
+        }
+        float *Ur = U + row * (int64_t)n + s0, *Lr = L + row * (int64_t)n + s0;
+        if (vec && e - s0 == MT && MT >= 4) {
+#pragma unroll
+            for (int m = 0; m < MT; m += 4) {
+                *reinterpret_cast<float4 *>(Ur + m) = make_float4(ux[m], ux[m + 1], ux[m + 2], ux[m + 3]);
+                *reinterpret_cast<float4 *>(Lr + m) = make_float4(ln[m], ln[m + 1], ln[m + 2], ln[m + 3]);
+            }
+        } else {
+#pragma unroll
+            for (int m = 0; m < MT; ++m)
+                if (s0 + m < e) {
+                    Ur[m] = ux[m];
+                    Lr[m] = ln[m];
+                }
+        }
+    }
+}
+
+template <int MT>
+static cudaError_t envelope_runs_go(const float *y, int64_t count, int n, int w, float *U, float *L, bool vec,
+                                    cudaStream_t s) {
+    const size_t smem = (size_t)kEnvWarps * (n + (n >> 5) + 1) * sizeof(float);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_envelope_runs<MT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kEnvWarps * (kEnvWarpMaxN + kEnvWarpMaxN / 32 + 1) * (int)sizeof(float));
+        attr = true;
+    }
+    const int64_t blocks = (count + kEnvWarps - 1) / kEnvWarps;
+    k_envelope_runs<MT><<<(unsigned)blocks, kEnvWarps * 32, smem, s>>>(y, count, n, w, U, L, vec);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_envelope(const float *y, int64_t count, int n, int w, float *U, float *L,
                             QueryCopies qc, int copies_padl, cudaStream_t s, float *UL, float *LU) {
     if (count <= 0) return cudaSuccess;
     if ((UL == nullptr) != (LU == nullptr)) return cudaErrorInvalidValue;
     w = min(w, n - 1);
     if (qc.data == nullptr && UL == nullptr && n <= kEnvWarpMaxN && count >= 4096) {
+        // a lane's run of MT outputs (the power of two >= n / 32)
+        int mt = 1;
+        while (32 * mt < n) mt *= 2;
+        if (2 * w + 1 >= mt) {
+            const bool vec = (n % 4 == 0) && ((reinterpret_cast<uintptr_t>(y) & 15) == 0) &&
+                             ((reinterpret_cast<uintptr_t>(U) & 15) == 0) &&
+                             ((reinterpret_cast<uintptr_t>(L) & 15) == 0);
+            switch (mt) {
+                case 1: return envelope_runs_go<1>(y, count, n, w, U, L, vec, s);
+                case 2: return envelope_runs_go<2>(y, count, n, w, U, L, vec, s);
+                case 4: return envelope_runs_go<4>(y, count, n, w, U, L, vec, s);
+                case 8: return envelope_runs_go<8>(y, count, n, w, U, L, vec, s);
+                case 16: return envelope_runs_go<16>(y, count, n, w, U, L, vec, s);
+                case 32: return envelope_runs_go<32>(y, count, n, w, U, L, vec, s);
+                default: break;
+            }
+        }
         const size_t smem = (size_t)kEnvWarps * 4 * n * sizeof(float);
         static bool rows_attr = false;
         if (!rows_attr) {

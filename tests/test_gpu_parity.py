@@ -84,15 +84,17 @@ def test_envelope_bit_exact(api, n):
             assert np.array_equal(L[r].astype(np.float64), Lr), (n, w, r)
 
 
-@pytest.mark.parametrize("n", [33, 256, 1000])
+@pytest.mark.parametrize("n", [33, 97, 256, 724, 1000, 1024])
 def test_envelope_many_rows_bit_exact(api, n):
-    # 4,096 rows or more take the warp-per-row kernel (the database rows'
-    # envelopes of every knn_search call); sampled rows against the oracle
+    # 4,096 rows or more take the warp-per-row kernels (the database rows'
+    # envelopes of every knn_search call): lanes over runs of outputs when
+    # 2w + 1 covers a lane's run (w >= 4 at n = 256, >= 16 at n = 1,000),
+    # else the doubling table; sampled rows against the oracle
     count = 4500
     rng = np.random.default_rng(n + 1)
     Y = synth.random_walks(count, n, seed=n + 3)
     Y[::7] = rng.integers(-2, 3, size=Y[::7].shape).astype(np.float32)  # ties
-    for w in sorted({0, 2, n // 10, n - 1}):
+    for w in sorted({0, 2, 3, 4, 15, 16, n // 10, n // 2, n - 1}):
         U, L = api.dtw_envelope(cuda(Y), w)
         U, L = U.cpu().numpy(), L.cpu().numpy()
         for r in list(range(0, count, 97)) + [count - 1]:
