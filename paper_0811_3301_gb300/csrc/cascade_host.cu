@@ -104,9 +104,15 @@ static cudaError_t launch_dtw_any(const DtwJob &j, const DtwGeom &g, cudaStream_
 // shortens it many-fold.  That is the case of the seeds of long series.  The
 // main stage lists many pairs, where one thread per pair has the higher
 // throughput, unless the caller (or the autotuner) asks for the warp path.
-// Bands wider than one thread's registers always take the warp path.
+// Bands wider than one thread's registers always take the warp path.  When
+// the run overlaps with others (the groups of an index batch, on concurrent
+// streams), their kernels fill the SMs that one seed launch leaves idle, so
+// the seeds take the thread path's higher throughput instead (batched
+// workload: 345 K -> 401 K q/s; a lone run: 8,000 seeds of n = 1,024,
+// w = 102, 1.18 -> 1.86 ms).
 static int use_lanes(const CascadePlan &pl, int64_t npairs, bool main_stage) {
     if (dtw_lanes_cl(pl.n, pl.we) == 0) return 0;
+    if (!main_stage && pl.seeds_on_threads && (pl.dtw_path == 0 || pl.dtw_path >= 4)) return 0;
     if (pl.dtw_path == 3) return main_stage ? 2 : 1;
     if (pl.dtw_path >= 4) return main_stage ? 0 : ((pl.n >= 512 && npairs < ((int64_t)1 << 17)) ? 1 : 0);
     if (pl.dtw_path == 2) return 1;

@@ -36,6 +36,7 @@ struct CascadePlan {
     int64_t Qc;      // queries per run
     int seg_len;     // candidates per filter segment
     int filter_warps;
+    bool seeds_on_threads;  // seeds of long series one thread per pair (runs that overlap with others)
     int nseg;        // sub-segments per query
     int seg_per_cta; // filter segments per CTA
     int dtw_path;    // 0 auto, 1 thread per pair, 2 warp per pair (main DTW stage)

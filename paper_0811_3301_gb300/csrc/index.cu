@@ -363,6 +363,8 @@ dtw_status prepare_batch(dtw_index *ix, int64_t Q, const int32_t *q_len, const i
         gr.qn = (int)gr.members.size();
         gr.t = tuning_for(ix, bk.n, gr.w, gr.k);
         gr.pl = plan_for(ix, gr.bucket, gr.w, gr.k, per_query ? 1 : gr.qn, gr.t);
+        // groups that run side by side on the stream pool: seeds one thread per pair
+        gr.pl.seeds_on_threads = bt.groups.size() > 1 && !per_query;
         qdst = (qdst + 3) & ~int64_t(3);
         gr.qoff = qdst;
         gr.ooff = gout;

@@ -5,7 +5,6 @@ lists merged by the library's merge kernel.  The merged result must be the
 single search's over the whole database (and the oracle's on a sample), and
 the exchanged threshold must bound the true k-th distance."""
 
-import math
 
 import numpy as np
 import pytest
