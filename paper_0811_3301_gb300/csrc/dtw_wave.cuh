@@ -156,10 +156,11 @@ __global__ void __launch_bounds__(kDtwThreads, 4) k_dtw_wave(DtwJob j) {
     // of its groups has rows left
     while (__any_sync(0xffffffffu, t < t_end)) {
         // one block of CL steps; step R uses window rotation R
+        const int t_switch = g_act ? g_T0 + gl : -1;  // the step this lane starts the group's pair
 #define WAVE_STEP(R)                                                                                          \
     {                                                                                                         \
         const int ts = t + (R);                                                                               \
-        if (g_act && ts == g_T0 + gl) {                                                                       \
+        if (ts == t_switch) {                                                                                 \
             /* this lane starts the group's current pair: row -1 values, the window of row 0 */              \
             xr = j.db + (int64_t)g_c * n;                                                                     \
             yr = j.qc.data + (int64_t)g_q * qstride + j.qc.padl;                                              \
@@ -176,7 +177,7 @@ __global__ void __launch_bounds__(kDtwThreads, 4) k_dtw_wave(DtwJob j) {
             }                                                                                                 \
         }                                                                                                     \
         const int r = ts - T;                                                                                 \
-        const bool due = !pad_lane && r >= 0 && r < n;                                                        \
+        const bool due = !pad_lane && (unsigned)r < (unsigned)n;                                              \
         float left = __shfl_up_sync(gmask, last, 1, G);                                                       \
         if (gl == 0) left = kInf;                                                                             \
         float xi = 0.0f;                                                                                      \

@@ -848,10 +848,14 @@ __device__ __forceinline__ void query_load_packed(QueryPacked<MT> &Q, const Casc
 }
 
 // This lane's parts of LB_Keogh^p (s1) and of the second sum (s2) of one pair.
+// Each sum is split over two accumulators (even and odd t) so that the adds
+// form two short chains instead of one long one; any order of these
+// non-negative terms is covered by the slack of the pruning tests.
 template <int P, int MT>
 __device__ __forceinline__ void pair_sums(const QueryPacked<MT> &Q, const RowsPacked<MT> &r, float &s1, float &s2) {
     const float2 m1 = make_float2(-1.0f, -1.0f);
-    float2 a1 = make_float2(0.0f, 0.0f), a2 = make_float2(0.0f, 0.0f);
+    float2 a1[2] = {make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f)};
+    float2 a2[2] = {make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f)};
 #pragma unroll
     for (int j = 0; j < MT / 4; ++j)
 #pragma unroll
@@ -863,15 +867,16 @@ __device__ __forceinline__ void pair_sums(const QueryPacked<MT> &Q, const RowsPa
             const float2 d1 = __ffma2_rn(Q.u[t], m1, x);  // x - U
             const float2 d2 = __ffma2_rn(x, m1, Q.l[t]);  // L - x
             const float2 k = make_float2(max3f(d1.x, d2.x, 0.0f), max3f(d1.y, d2.y, 0.0f));
-            a1 = (P == 1) ? __fadd2_rn(a1, k) : __ffma2_rn(k, k, a1);
+            a1[h] = (P == 1) ? __fadd2_rn(a1[h], k) : __ffma2_rn(k, k, a1[h]);
             const float2 e1 = __ffma2_rn(xu, m1, Q.y[t]);  // y - XU
             const float2 e2 = __ffma2_rn(Q.y[t], m1, xl);  // XL - y
             const float2 g = make_float2(max3f(fminf(e1.x, Q.a[t].x), fminf(e2.x, Q.b[t].x), 0.0f),
                                          max3f(fminf(e1.y, Q.a[t].y), fminf(e2.y, Q.b[t].y), 0.0f));
-            a2 = (P == 1) ? __fadd2_rn(a2, g) : __ffma2_rn(g, g, a2);
+            a2[h] = (P == 1) ? __fadd2_rn(a2[h], g) : __ffma2_rn(g, g, a2[h]);
         }
-    s1 = a1.x + a1.y;
-    s2 = a2.x + a2.y;
+    const float2 b1 = __fadd2_rn(a1[0], a1[1]), b2 = __fadd2_rn(a2[0], a2[1]);
+    s1 = b1.x + b1.y;
+    s2 = b2.x + b2.y;
 }
 
 // ---------------------------------------------------------------------------
@@ -922,6 +927,7 @@ __global__ void __launch_bounds__(256, 2) k_lbi_batch(CascadeBufs b) {
             if (e < cnt1) env_issue<MT, true>(ring, e, b, surv_c[e], true, true);
             cp_async_commit();
         }
+        int st = 0;  // stage of pair e (e % kEnvStages), kept by increments
         for (int e0 = 0; e0 < cnt1; e0 += kLbiBatch) {
             float v[16];
 #pragma unroll
@@ -929,13 +935,16 @@ __global__ void __launch_bounds__(256, 2) k_lbi_batch(CascadeBufs b) {
                 const int e = e0 + u;
                 float a1 = 0.0f, a2 = 0.0f;
                 if (e < cnt1) {
-                    // the stage refilled here was read (and used) by pair e - 1
+                    // the stage refilled here, (e + 2) % 3, was read (and used) by pair e - 1
+                    static_assert(kEnvStages == 3, "stage arithmetic below");
                     const int ahead = e + kEnvStages - 1;
-                    if (ahead < cnt1) env_issue<MT, true>(ring, ahead % kEnvStages, b, surv_c[ahead], true, true);
+                    const int st_ahead = st == 0 ? 2 : st - 1;
+                    if (ahead < cnt1) env_issue<MT, true>(ring, st_ahead, b, surv_c[ahead], true, true);
                     cp_async_commit();
                     cp_async_wait<kEnvStages - 1>();
                     RowsPacked<MT> R;
-                    const float *stage = ring + (size_t)(e % kEnvStages) * 3 * 32 * MT;
+                    const float *stage = ring + (size_t)st * 3 * 32 * MT;
+                    st = st == 2 ? 0 : st + 1;
 #pragma unroll
                     for (int jj = 0; jj < MT / 4; ++jj) {
                         R.x[jj] = *reinterpret_cast<const float4 *>(stage + 4 * (lane + 32 * jj));
