@@ -157,7 +157,9 @@ __device__ __forceinline__ void reg_rows2(float (&D)[C], float x0, float x1, con
 }
 
 // The abandon test after a row group (every 8 rows): the band's minimum, raised
-// by the LB_Keogh terms of the rows not yet reached (reading 6) when `tail`,
+// by the LB_Keogh terms of the rows not yet reached when `tail` (every path
+// from the current row still crosses each later row i, at a cost of at least
+// x_i's distance to the query envelope there, Sec. 7),
 // against the threshold.  fp32: the two LB_Keogh sums (different orders) each
 // carry at most n u relative error, and the path's remaining additions at
 // most (2n - 1) u; c covers both.
@@ -220,7 +222,8 @@ k_dtw_reg(DtwJob j, int e, int wl) {
         ++n_comp;
         const float *x = j.db + (int64_t)c * n;
         const float *yc = j.qc.data + (int64_t)q * 4 * ylen;
-        // the cumulative LB_Keogh abandon bound (reading 6): the pair's result
+        // the cumulative LB_Keogh abandon bound (Sec. 3 early abandoning with
+        // the Sec. 7 terms of the rows still ahead): the pair's result
         // slot holds its LB_Keogh^p (read at each test, to spare registers),
         // and the terms of the rows passed so far are summed here; the rest
         // bounds the rows not yet reached
@@ -368,7 +371,7 @@ __device__ __forceinline__ void dtw_row_win(float (&D)[C], float xi, const float
 // window load: the query window of the group read from copy 0 (y0 + i) with
 // aligned 128-bit loads, x_i .. x_{i+3} with one (xvec) or four loads.  With
 // `tail`, the LB_Keogh terms of these rows are added to lbk_pre when rows
-// remain after them (the cumulative abandon bound, reading 6).
+// remain after them (the cumulative abandon bound of reg4_abandons).
 template <int C, int P, int E>
 __device__ __forceinline__ void reg4_rows(float (&D)[C], const float *__restrict__ x, const float *__restrict__ y0,
                                           int i, int n, int e, bool xvec, bool tail, const float *tu,
