@@ -20,17 +20,20 @@ __device__ __forceinline__ unsigned long long pack_key(float d, int c) {
 // databases (N <= 8192) the S smallest bounds overall.  Their exact DTW
 // is computed first so that the threshold is close to its final value before
 // the bulk of the candidates is filtered; this is the GPU counterpart of
-// visiting candidates in order of their lower bound.  One CTA per query;
-// each thread keeps a sorted list of its kSeedMax best keys, then S rounds of
-// a block-wide minimum pop the global best.  The seed of rank s of query q is
-// stored at s * Q + q, so the k best-bounded seeds of every query come first.
-// Also resets the query's thresholds to +INF.
+// visiting candidates in order of their lower bound.  One warp per query:
+// each lane keeps a sorted list of its kSeedMax best keys, then S rounds of a
+// warp minimum pop the global best (no block barriers).  The seed of rank s
+// of query q is stored at s * Q + q, so the k best-bounded seeds of every
+// query come first.  Also resets the query's thresholds to +INF.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_seed_select(CascadeBufs b) {
-    const int q = blockIdx.x;
-    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
-    if (t == 0) b.bsf[q] = 0x7f800000u;
-    for (int g = t; g < b.k; g += blockDim.x) b.gmin[(int64_t)q * b.k + g] = 0x7f800000u;
+constexpr int kSeedWarps = 4;
+
+__global__ void __launch_bounds__(kSeedWarps * 32) k_seed_select(CascadeBufs b) {
+    const int q = blockIdx.x * kSeedWarps + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (q >= b.Q) return;
+    if (lane == 0) b.bsf[q] = 0x7f800000u;
+    for (int g = lane; g < b.k; g += 32) b.gmin[(int64_t)q * b.k + g] = 0x7f800000u;
     unsigned long long key[kSeedMax];
 #pragma unroll
     for (int s = 0; s < kSeedMax; ++s) key[s] = ~0ull;
@@ -39,7 +42,7 @@ __global__ void __launch_bounds__(256) k_seed_select(CascadeBufs b) {
     const int cnt = full ? b.N : b.ntiles;
     const float *lbrow = b.lb + (int64_t)q * b.N;
     const unsigned long long *row = b.tile_min + (int64_t)q * b.ntiles;
-    for (int c = t; c < cnt; c += blockDim.x) {
+    for (int c = lane; c < cnt; c += 32) {
         unsigned long long v = full ? pack_key(lbrow[c], c) : row[c];
         if (v < key[kSeedMax - 1]) {
             // insertion into the sorted list
@@ -52,8 +55,8 @@ __global__ void __launch_bounds__(256) k_seed_select(CascadeBufs b) {
             key[0] = v < key[0] ? v : key[0];
         }
     }
-    __shared__ unsigned long long wmin[8];
-    __shared__ unsigned long long winner;
+    // every lane has read its bounds before the seeds' entries become NaN
+    __syncwarp();
     for (int s = 0; s < b.S; ++s) {
         unsigned long long m = key[0];
 #pragma unroll
@@ -61,34 +64,26 @@ __global__ void __launch_bounds__(256) k_seed_select(CascadeBufs b) {
             unsigned long long other = __shfl_xor_sync(0xffffffffu, m, o);
             m = other < m ? other : m;
         }
-        if (lane == 0) wmin[wid] = m;
-        __syncthreads();
-        if (t == 0) {
-            unsigned long long best = wmin[0];
-            for (int v = 1; v < (int)(blockDim.x >> 5); ++v) best = wmin[v] < best ? wmin[v] : best;
-            winner = best;
-            int c = (best == ~0ull) ? -1 : (int)(unsigned)(best & 0xffffffffull);
+        if (lane == 0) {
+            const int c = (m == ~0ull) ? -1 : (int)(unsigned)(m & 0xffffffffull);
             b.seed_pairs[(int64_t)s * b.Q + q] = Pair{q, c};
             b.seed_res[(int64_t)s * b.Q + q] = kInf;
             // the seed's matrix entry becomes NaN, which no bound test passes:
-            // the filter then skips seeds without looking them up (every
-            // thread finished reading the row before the first barrier above)
+            // the filter then skips seeds without looking them up
             if (c >= 0) b.lb[(int64_t)q * b.N + c] = __int_as_float(0x7fc00000);
         }
-        __syncthreads();
-        if (key[0] == winner && winner != ~0ull) {
+        if (key[0] == m && m != ~0ull) {
             // pop: only the owner holds this (unique) key
 #pragma unroll
             for (int u = 0; u + 1 < kSeedMax; ++u) key[u] = key[u + 1];
             key[kSeedMax - 1] = ~0ull;
         }
-        __syncthreads();
     }
 }
 
 cudaError_t launch_seed_select(const CascadeBufs &b, cudaStream_t s) {
     if (b.Q <= 0) return cudaSuccess;
-    k_seed_select<<<b.Q, 256, 0, s>>>(b);
+    k_seed_select<<<(b.Q + kSeedWarps - 1) / kSeedWarps, kSeedWarps * 32, 0, s>>>(b);
     return cudaGetLastError();
 }
 
