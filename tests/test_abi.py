@@ -170,3 +170,32 @@ def test_header_compiles_as_c99_and_cxx(tmp_path):
                  "-x", "c++", str(src)]):
         r = subprocess.run(cmd, capture_output=True, text=True)
         assert r.returncode == 0, r.stderr
+
+
+def test_shard_entry_points_validate_on_host(native):
+    # candidate sharding: the threshold export / bounded search / merge calls
+    # reject bad arguments before any device work
+    buf = (ctypes.c_float * 16)()
+    idx = (ctypes.c_int64 * 16)()
+    lib = native.lib
+    # merge: R, k_in, k out of range; host buffers refused; no queries is no work
+    assert _status(native, lambda: lib.knn_merge_topk(idx, buf, 0, 1, 1, 1, idx, buf, None))[0] == 1
+    assert _status(native, lambda: lib.knn_merge_topk(idx, buf, 2, 1, 0, 1, idx, buf, None))[0] == 1
+    st, text = _status(native, lambda: lib.knn_merge_topk(idx, buf, 2, 1, 4, 1000, idx, buf, None))
+    assert st == 1 and "k=1000" in text
+    st, text = _status(native, lambda: lib.knn_merge_topk(idx, buf, 2, 1, 4, 4, idx, buf, None))
+    assert st == 1 and "device" in text
+    assert lib.knn_merge_topk(idx, buf, 2, 0, 4, 4, idx, buf, None) == 0
+    # thresholds out: the usual argument checks, and an output buffer
+    st, text = _status(native, lambda: lib.knn_seed_thresholds(buf, 1, buf, 1, 16, 1, 3, 1, None, buf, None))
+    assert st == 1 and "p=3" in text
+    st, text = _status(native, lambda: lib.knn_seed_thresholds(buf, 1, buf, 1, 16, 1, 1, 1, None, None, None))
+    assert st == 1 and "null" in text
+    assert lib.knn_seed_thresholds(buf, 1, buf, 0, 16, 1, 1, 1, None, buf, None) == 0  # Q = 0
+    # bounded search: a threshold array is required when there are queries
+    st, text = _status(native, lambda: lib.knn_search_bounded(buf, 1, buf, 1, 16, 1, 1, 1, None, None, idx, buf,
+                                                              None, None))
+    assert st == 1 and "null" in text
+    st, text = _status(native, lambda: lib.knn_search_bounded(buf, 1, buf, 1, 16, 1, 1, 0, None, buf, idx, buf,
+                                                              None, None))
+    assert st == 1 and "k=0" in text
