@@ -51,3 +51,45 @@ def test_latency_summary():
     assert abs(s["throughput_qps"] - 998 / 1.000) < 1e-6
     none = bench.latency_summary([dict(comp[0], status=4)])
     assert none["succeeded"] == 0 and none["throughput_qps"] == 0.0 and none["p50_ms"] is None
+
+
+def test_candidate_mode_config_and_prefix_accounting(monkeypatch):
+    # the line's parallelism names the sharding; in candidate mode the bound
+    # tile and the seeds run twice per step (once for the thresholds), and the
+    # rates count that work twice over the shard's own candidates
+    import argparse
+
+    sys.path.insert(0, ROOT)
+    import bench
+
+    a = argparse.Namespace(data="random_walk", k=1, N=100_000, n=256, w=25, Q=1000, p=1, seed=2, dtw_path=0,
+                           shard="candidates")
+    assert "candidates sharded over 4 GPU(s)" in bench.workload_config(a, 4)["parallelism"]
+    a.shard = "queries"
+    assert "queries sharded over 4 GPU(s)" in bench.workload_config(a, 4)["parallelism"]
+    monkeypatch.setattr(bench, "alu_peak_tops", lambda peaks: (40.0, "derived"))
+    stages = ("lb_keogh", "lb_improved", "dtw", "seed_dtw")
+    prof = {s: {"ms": 0.0, "launches": 0} for s in stages}
+    prof["lb_keogh"] = {"ms": 2.0, "launches": 4}  # 2 steps x 2 runs, 0.5 ms each
+    prof["seed_dtw"] = {"ms": 0.2, "launches": 4}
+    stats = {"seed_cells": 1e9}
+    one = bench.stage_rates(prof, a, 2, {}, stats, prefix_runs=1)
+    two = bench.stage_rates(prof, a, 2, {}, stats, prefix_runs=2)
+    assert abs(two["lb_keogh_tile"]["Top_s"] - 2 * one["lb_keogh_tile"]["Top_s"]) < 1e-9
+    assert abs(two["seed_dtw"]["cells_per_s"] - 2 * one["seed_dtw"]["cells_per_s"]) < 1e-3
+    roof = bench.roofline(prof, a, 2, {}, stats, prefix_runs=2)
+    # per launch: Q N d terms of 3 ops (d = n / 8) in 0.5 ms
+    assert roof["kernel"] == "k_lbk_tile"
+    assert abs(roof["achieved"] - 1000 * 100_000 * 32 * 3 / 1e12 / 0.5e-3) < 1e-6
+
+
+def test_no_gc_pauses_and_restores_the_collector():
+    import gc
+
+    sys.path.insert(0, ROOT)
+    import bench
+
+    assert gc.isenabled()
+    with bench.no_gc():
+        assert not gc.isenabled()
+    assert gc.isenabled()
