@@ -470,8 +470,8 @@ def run_ours(a):
 
     # DTW rows evaluated per step (for the DTW roofline): one extra stats run
     if cand:
-        thr = shard.exchange_thresholds(api.seed_thresholds(db, qs, a.w, a.p, a.k, **skw))
-        _, _, st_main = api.knn_search(db, qs, a.w, a.p, a.k, thr_in=thr, return_stats=True, **kw)
+        thr = shard.exchange_thresholds(api.knn_seed_thresholds(db, qs, a.w, a.p, a.k, **skw))
+        _, _, st_main = api.knn_search_bounded(db, qs, a.w, a.p, a.k, thr, return_stats=True, **kw)
     else:
         _, _, st_main = api.knn_search(db, qs, a.w, a.p, a.k, return_stats=True, **kw)
 

@@ -177,10 +177,10 @@ def knn_search(db: torch.Tensor, queries: torch.Tensor, w: int, p: int, k: int =
     also the cascade counters.  Outputs default to the device of `queries`
     when it is a CUDA tensor, else to host memory.
 
-    thr_in (float32 [Q], power units as seed_thresholds gives them) makes
-    this the search of one shard of a candidate-sharded database
-    (knn_search_bounded): each query's threshold is lowered to thr_in, and
-    only candidates within the final threshold are listed.
+    thr_in (float32 [Q], power units as knn_seed_thresholds gives them)
+    makes this the search of one shard of a candidate-sharded database (the
+    C call knn_search_bounded): each query's threshold is lowered to thr_in,
+    and only candidates within the final threshold are listed.
     """
     db, queries, opt = _knn_args(db, queries, mode, slack, seeds, parts, dtw_path, filter_path, lb_abandon)
     Q, n = queries.shape
@@ -206,14 +206,23 @@ def knn_search(db: torch.Tensor, queries: torch.Tensor, w: int, p: int, k: int =
     return out_idx, out_dist
 
 
-def seed_thresholds(db: torch.Tensor, queries: torch.Tensor, w: int, p: int, k: int = 1, *,
+def knn_search_bounded(db: torch.Tensor, queries: torch.Tensor, w: int, p: int, k: int, thr_in: torch.Tensor,
+                       **kw):
+    """knn_search of one shard of a candidate-sharded database with every
+    query's threshold lowered to thr_in (float32 [Q], power units, e.g. the
+    minimum over the shards of knn_seed_thresholds); keyword arguments as in
+    knn_search."""
+    return knn_search(db, queries, w, p, k, thr_in=thr_in, **kw)
+
+
+def knn_seed_thresholds(db: torch.Tensor, queries: torch.Tensor, w: int, p: int, k: int = 1, *,
                     mode: str = "improved", slack: float = 1e-6, seeds: int = 0, parts: int = 0,
                     dtw_path: int = 0, filter_path: int = 0, out: torch.Tensor | None = None) -> torch.Tensor:
     """Each query's k-th smallest seed DTW against this shard of a
-    candidate-sharded database (knn_seed_thresholds): float32 [Q] in the
+    candidate-sharded database: float32 [Q] in the
     cascade's power units (DTW_p^p; DTW_inf for p = infinity), +inf where the
     shard has fewer than k seeds.  The minimum over the shards is a valid
-    threshold for every shard's knn_search(..., thr_in=...)."""
+    threshold for every shard's knn_search_bounded."""
     db, queries, opt = _knn_args(db, queries, mode, slack, seeds, parts, dtw_path, filter_path, 0)
     Q, n = queries.shape
     if out is None:
@@ -224,13 +233,13 @@ def seed_thresholds(db: torch.Tensor, queries: torch.Tensor, w: int, p: int, k: 
     return out
 
 
-def merge_topk(idx: torch.Tensor, dist: torch.Tensor, k: int):
+def knn_merge_topk(idx: torch.Tensor, dist: torch.Tensor, k: int):
     """The k smallest (distance, index) per query of R per-shard lists idx,
     dist [R, Q, k_in] (CUDA tensors; global indices below 2^31, -1 / +inf for
     empty entries): (idx int64 [Q, k], dist float32 [Q, k]), padded with
-    -1 / +inf (knn_merge_topk)."""
+    -1 / +inf."""
     if not (idx.is_cuda and dist.is_cuda):
-        raise ValueError("merge_topk takes CUDA tensors")
+        raise ValueError("knn_merge_topk takes CUDA tensors")
     if idx.dim() != 3 or idx.shape != dist.shape:
         raise ValueError("idx and dist must both be [R, Q, k_in]")
     idx = idx.to(torch.int64).contiguous()

@@ -90,7 +90,7 @@ def gather_merge(local_idx, local_dist, k: int, group=None):
     if local_idx.is_cuda:
         from . import api
 
-        return api.merge_topk(torch.stack(gi), torch.stack(gd), k)
+        return api.knn_merge_topk(torch.stack(gi), torch.stack(gd), k)
     idx = np.stack([t.numpy() for t in gi])
     dd = np.stack([t.numpy() for t in gd])
     mi, md = merge_topk(idx, dd, k)
@@ -102,16 +102,16 @@ def sharded_knn_search(db_shard, offset: int, queries, w: int, p: int, k: int, g
     """knn_search over this rank's candidate range (db_shard = rows
     [offset, offset + len)), then the exact global top-k by gather_merge.
     With exchange, the ranks first share their seeds' thresholds
-    (seed_thresholds, exchange_thresholds) and every rank searches with the
-    tightest (knn_search(..., thr_in=...))."""
+    (knn_seed_thresholds, exchange_thresholds) and every rank searches with
+    the tightest (knn_search_bounded)."""
     import torch
 
     from . import api
 
     if exchange:
         skw = {key: v for key, v in kw.items() if key in ("mode", "slack", "seeds", "parts", "dtw_path", "filter_path")}
-        thr = exchange_thresholds(api.seed_thresholds(db_shard, queries, w, p, k, **skw), group)
-        idx, dd = api.knn_search(db_shard, queries, w, p, k, thr_in=thr, **kw)
+        thr = exchange_thresholds(api.knn_seed_thresholds(db_shard, queries, w, p, k, **skw), group)
+        idx, dd = api.knn_search_bounded(db_shard, queries, w, p, k, thr, **kw)
     else:
         idx, dd = api.knn_search(db_shard, queries, w, p, k, **kw)
     idx = torch.where(idx >= 0, idx + int(offset), idx)

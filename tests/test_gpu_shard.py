@@ -35,15 +35,16 @@ def _sharded(api, db, qs, w, p, k, cuts, exchange=True):
     shards = list(zip([0] + cuts, cuts + [db.shape[0]]))
     thr = None
     if exchange:
-        ts = [api.seed_thresholds(cuda(db[a:b]), cuda(qs), w, p, k) for a, b in shards]
+        ts = [api.knn_seed_thresholds(cuda(db[a:b]), cuda(qs), w, p, k) for a, b in shards]
         thr = torch.stack(ts).min(dim=0).values
     lists_i, lists_d, stats = [], [], []
     for a, b in shards:
-        i, d, st = api.knn_search(cuda(db[a:b]), cuda(qs), w, p, k, thr_in=thr, return_stats=True)
+        i, d, st = (api.knn_search_bounded(cuda(db[a:b]), cuda(qs), w, p, k, thr, return_stats=True) if exchange
+                     else api.knn_search(cuda(db[a:b]), cuda(qs), w, p, k, return_stats=True))
         lists_i.append(torch.where(i >= 0, i + a, i))
         lists_d.append(d)
         stats.append(st)
-    mi, md = api.merge_topk(torch.stack(lists_i), torch.stack(lists_d), k)
+    mi, md = api.knn_merge_topk(torch.stack(lists_i), torch.stack(lists_d), k)
     return mi, md, thr, stats
 
 
@@ -99,28 +100,28 @@ def test_merge_kernel_matches_the_host_merge(api):
     idx[empty] = -1
     dist[empty] = np.inf
     hi, hd = shard.merge_topk(idx, dist, k)
-    gi, gd = api.merge_topk(torch.from_numpy(idx).cuda(), torch.from_numpy(dist).cuda(), k)
+    gi, gd = api.knn_merge_topk(torch.from_numpy(idx).cuda(), torch.from_numpy(dist).cuda(), k)
     np.testing.assert_array_equal(gi.cpu().numpy(), hi)
     np.testing.assert_array_equal(gd.cpu().numpy(), hd)
 
 
 def test_thresholds_of_an_empty_shard_and_host_buffers(api):
     qs = synth.random_walks(6, 64, seed=77, stream=synth.STREAM_QUERY)
-    t = api.seed_thresholds(cuda(np.zeros((0, 64))), cuda(qs), 6, 2, 2)
+    t = api.knn_seed_thresholds(cuda(np.zeros((0, 64))), cuda(qs), 6, 2, 2)
     assert bool(torch.isinf(t).all())
     db = synth.random_walks(3_000, 64, seed=78)
-    td = api.seed_thresholds(cuda(db), cuda(qs), 6, 2, 2)
-    th = api.seed_thresholds(torch.from_numpy(db), torch.from_numpy(qs), 6, 2, 2)  # host in, host out
+    td = api.knn_seed_thresholds(cuda(db), cuda(qs), 6, 2, 2)
+    th = api.knn_seed_thresholds(torch.from_numpy(db), torch.from_numpy(qs), 6, 2, 2)  # host in, host out
     assert not th.is_cuda and torch.equal(th, td.cpu())
     # a host thr_in, NaN and negative entries ignored (the query's own threshold stays)
     tin = th.clone()
     tin[0] = float("nan")
     tin[1] = -1.0
     ri, rd = api.knn_search(cuda(db), cuda(qs), 6, 2, 2)
-    bi, bd = api.knn_search(cuda(db), cuda(qs), 6, 2, 2, thr_in=tin)
+    bi, bd = api.knn_search_bounded(cuda(db), cuda(qs), 6, 2, 2, tin)
     assert torch.equal(bi, ri) and torch.equal(bd, rd)
     # a threshold below every distance leaves nothing to list
-    zi, zd = api.knn_search(cuda(db), cuda(qs), 6, 2, 2, thr_in=torch.zeros(6).cuda())
+    zi, zd = api.knn_search_bounded(cuda(db), cuda(qs), 6, 2, 2, torch.zeros(6).cuda())
     assert bool((zi == -1).all()) and bool(torch.isinf(zd).all())
 
 
