@@ -89,8 +89,11 @@ typedef struct {
                       the default (n / 8 when n >= 64, else off), -1 disables it (LB_Keogh
                       of every pair), otherwise 1 <= d <= n */
     int32_t dtw_path; /* DTW kernel of the cascade's DTW stages: 0 chooses (one warp per
-                         pair for long series or wide bands, else one thread per pair),
-                         1 one thread per pair where the band fits, 2 one warp per pair,
+                         pair for bands wider than 208 slots and for the few seeds of
+                         long series, else one thread per pair),
+                         1 one thread per pair where the band fits, 2 one warp per pair
+                         (one row per lane and step for bands of 409 and 289 slots, two
+                         pairs per warp otherwise),
                          3 one warp per two pairs (16-lane groups) where the band allows,
                          4 one thread per pair in launches of 64 rows (pairs still alive
                          at a launch's last row are resumed by the next one), where the
